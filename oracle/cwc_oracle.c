@@ -1,0 +1,703 @@
+/*
+ * cwc_oracle.c -- plain, sequential CPU oracle for Gillespie direct-method
+ * simulation of restricted CWC rewrite systems (flat mass-action networks are
+ * the one-compartment case), run over replicas x parameter-sweep points.
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this file.  It shares no code, header,
+ * table or constant generator with the CUDA library, and the CUDA library
+ * never loads it.
+ *
+ * It is deliberately slow and literal: every step re-matches every rule in
+ * every compartment and rebuilds the whole propensity tree, in the order of
+ * the simulation step of Sec. 5.1 (Fig. "CWC simulator pseudo-code": Match,
+ * Resolve = Gillespie + stochastic choice of the context, Update, clock).
+ *
+ * Build (see build.py): gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math.
+ * With contraction off, every floating-point expression below is evaluated
+ * as separate IEEE-754 double operations rounded to nearest-even, in the
+ * order written.
+ *
+ * Parity is pinned per function by the tests (tests/test_oracle_*.py):
+ *   philox4x32_10   statistical tests on the CPU; cuRAND's Philox4_32_10 on
+ *                   the GPU (library routine).
+ *   u52             exhaustive boundary words, exactness.
+ *   log_spec        <= 2 ulp against the C library log on 10^6 points + edges.
+ *   tree_sum        error bound against an exactly rounded sum (math.fsum).
+ *   select_rule     never picks a zero entry; frequencies vs a_j / a0.
+ *   propensities    Sec. 2.2 worked example (rate 4k); brute-force counting
+ *                   of distinct reactant tuples on small terms.
+ *   simulate        closed-form laws (birth-death Poisson / binomial mixture,
+ *                   isomerisation binomial), chemical master equation via
+ *                   matrix exponential, conservation invariants.
+ *   sensitivities   analytic birth-death gradient; central finite
+ *                   differences with common random numbers.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Status codes of one trajectory.                                          */
+/* ------------------------------------------------------------------------ */
+enum {
+  ST_OK = 0,             /* reached the end of the grid                     */
+  ST_ABSORBED = 1,       /* total propensity became zero (not an error)     */
+  ST_INT_OVERFLOW = 2,   /* a count would exceed INT32_MAX; event not applied */
+  ST_PROP_OVERFLOW = 3,  /* an int64 combinatorial count overflowed, or a0 = inf */
+  ST_CAPACITY = 4,       /* CREATE found no free compartment slot           */
+  ST_EVENT_LIMIT = 5,    /* max_events events were applied                  */
+  ST_BAD_INPUT = 6       /* rates, initial term or grid invalid             */
+};
+
+enum { K_LOCAL = 0, K_PARENT_CHILD = 1, K_CREATE = 2, K_DISSOLVE = 3 };
+
+typedef struct {
+  int32_t S, L, C, M;
+  const int32_t *kind, *ctx_label, *child_label;
+  const int32_t *lhs; /* [M][3][S]: context content, child wrap, child content */
+  const int32_t *rhs; /* [M][3][S] */
+} oracle_model;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications,    */
+/* a key schedule bumped by two Weyl constants between rounds.               */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; round++) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Draw for event n, purpose (0: tau and rule, 1: context), replica r, point p. */
+static void draw(uint64_t seed, uint32_t n, uint32_t purpose, uint32_t r, uint32_t p,
+                 uint32_t out[4]) {
+  uint32_t ctr[4] = {n, purpose, r, p};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  oracle_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uniform in (0,1): 52 random bits k, u = (k + 1/2) 2^-52.  Exact.          */
+/* ------------------------------------------------------------------------ */
+double oracle_u52(uint32_t wa, uint32_t wb) {
+  uint64_t k = ((uint64_t)(wa >> 6) << 26) | (uint64_t)(wb >> 6);
+  return ((double)k + 0.5) * 0x1p-52;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Natural logarithm for u in (0,1), fixed sequence of double operations:    */
+/* u = f 2^E, f in [1,2); if f >= sqrt2 then m = f/2, e = E+1 else m = f,     */
+/* e = E; s = (m-1)/(m+1); ln m = 2 atanh(s) = 2 (s + s^3/3 + ... + s^21/21)  */
+/* (series of Abramowitz & Stegun 4.1.27 with x = m); ln u = e ln2 + ln m.    */
+/* ------------------------------------------------------------------------ */
+static double coef[22]; /* coef[k] = 1/k for odd k, IEEE-divided */
+static int coef_ready = 0;
+
+static void init_coef(void) {
+  if (coef_ready) return;
+  for (int k = 3; k <= 21; k += 2) coef[k] = 1.0 / (double)k;
+  coef_ready = 1;
+}
+
+double oracle_log_spec(double u) {
+  const double SQRT2 = 1.4142135623730951;  /* the double nearest sqrt(2) */
+  const double LN2 = 0.6931471805599453;    /* the double nearest ln(2)   */
+  init_coef();
+  uint64_t bits;
+  memcpy(&bits, &u, 8);
+  int E = (int)((bits >> 52) & 0x7ff) - 1023;
+  uint64_t fbits = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+  double f;
+  memcpy(&f, &fbits, 8);
+  double m;
+  int e;
+  if (f >= SQRT2) {
+    m = f * 0.5;
+    e = E + 1;
+  } else {
+    m = f;
+    e = E;
+  }
+  double s = (m - 1.0) / (m + 1.0);
+  double z = s * s;
+  double p = coef[21];
+  for (int k = 19; k >= 3; k -= 2) p = p * z + coef[k];
+  double r = 2.0 * (s + s * (z * p));
+  return (double)e * LN2 + r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 32-lane blocked tree over a[0..M-1]: block size B = ceil(M/32); leaf l is */
+/* the left-to-right sum of a[lB .. min((l+1)B, M)-1] (empty: +0); then five */
+/* levels of pairwise sums, node(k,i) = node(k-1,2i) + node(k-1,2i+1).       */
+/* nodes[0..31] = leaves, [32..47] level 1, [48..55] level 2, [56..59]       */
+/* level 3, [60..61] level 4, [62] root.                                      */
+/* ------------------------------------------------------------------------ */
+static const int LEVEL_BASE[6] = {0, 32, 48, 56, 60, 62};
+
+static void build_tree(const double* a, int M, double nodes[63]) {
+  int B = (M + 31) / 32;
+  for (int l = 0; l < 32; l++) {
+    double s = 0.0;
+    for (int j = l * B; j < (l + 1) * B && j < M; j++) s = s + a[j];
+    nodes[l] = s;
+  }
+  for (int k = 1; k <= 5; k++) {
+    int width = 32 >> k;
+    for (int i = 0; i < width; i++)
+      nodes[LEVEL_BASE[k] + i] = nodes[LEVEL_BASE[k - 1] + 2 * i] + nodes[LEVEL_BASE[k - 1] + 2 * i + 1];
+  }
+}
+
+double oracle_tree_sum(const double* a, int32_t M) {
+  double nodes[63];
+  build_tree(a, M, nodes);
+  return nodes[62];
+}
+
+/* Guarded descent: at a node go left if x < S_left or S_right == 0, else    */
+/* x -= S_left and go right; in the leaf pick the first j whose running sum  */
+/* exceeds x, else the last positive entry.  Never returns a zero entry.     */
+int32_t oracle_select(const double* a, int32_t M, double x) {
+  double nodes[63];
+  build_tree(a, M, nodes);
+  int B = (M + 31) / 32;
+  int i = 0; /* index within the level */
+  for (int k = 5; k >= 1; k--) {
+    double SL = nodes[LEVEL_BASE[k - 1] + 2 * i];
+    double SR = nodes[LEVEL_BASE[k - 1] + 2 * i + 1];
+    if (x < SL || SR == 0.0) {
+      i = 2 * i;
+    } else {
+      x = x - SL;
+      i = 2 * i + 1;
+    }
+  }
+  double s = 0.0;
+  int last = -1;
+  for (int j = i * B; j < (i + 1) * B && j < M; j++) {
+    if (a[j] > 0.0) {
+      last = j;
+      s = s + a[j];
+      if (x < s) return j;
+    }
+  }
+  return last;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Terms: per trajectory, C compartment slots.                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t S, C;
+  int32_t* alive;   /* [C] */
+  int32_t* label;   /* [C] */
+  int32_t* parent;  /* [C] */
+  int32_t* wrap;    /* [C][S] */
+  int32_t* content; /* [C][S] */
+} term_t;
+
+/* binomial(n, k) for k in {0,1,2}, n >= 0; the Match_Populations count. */
+static int binom(int64_t n, int32_t k, int64_t* out) {
+  if (k == 0) { *out = 1; return 0; }
+  if (n < k) { *out = 0; return 0; }
+  if (k == 1) { *out = n; return 0; }
+  /* k == 2: n (n-1) / 2, exact in int64 for n < 2^31 */
+  *out = n * (n - 1) / 2;
+  return 0;
+}
+
+/* product of binomials of one pattern over one multiset; -1 on int64 overflow */
+static int pattern_count(const int32_t* pattern, const int32_t* multiset, int32_t S, int64_t* acc) {
+  for (int x = 0; x < S; x++) {
+    if (pattern[x] == 0) continue;
+    int64_t b;
+    binom(multiset[x], pattern[x], &b);
+    int64_t prod;
+    if (__builtin_mul_overflow(*acc, b, &prod)) return -1;
+    *acc = prod;
+  }
+  return 0;
+}
+
+/* Is slot c a context of rule j?  LOCAL/CREATE: slot of the rule's label.    */
+/* PARENT_CHILD/DISSOLVE: a child slot of label child_label whose parent has  */
+/* the rule's label.                                                          */
+static int is_context(const oracle_model* m, const term_t* t, int j, int c) {
+  if (!t->alive[c]) return 0;
+  int kind = m->kind[j];
+  if (kind == K_LOCAL || kind == K_CREATE) return t->label[c] == m->ctx_label[j];
+  if (c == 0) return 0;
+  int q = t->parent[c];
+  return t->label[c] == m->child_label[j] && t->label[q] == m->ctx_label[j];
+}
+
+/* Match(rule, term, context): number of distinct reactant combinations of   */
+/* rule j at context c (Sec. 2.2).  -1 on overflow.                           */
+static int match_count(const oracle_model* m, const term_t* t, int j, int c, int64_t* h) {
+  const int32_t S = m->S;
+  const int32_t* lhs = m->lhs + (size_t)j * 3 * S;
+  int kind = m->kind[j];
+  int64_t acc = 1;
+  if (kind == K_LOCAL || kind == K_CREATE) {
+    if (pattern_count(lhs, t->content + (size_t)c * S, S, &acc)) return -1;
+  } else {
+    int q = t->parent[c];
+    if (pattern_count(lhs, t->content + (size_t)q * S, S, &acc)) return -1;
+    if (pattern_count(lhs + S, t->wrap + (size_t)c * S, S, &acc)) return -1;
+    if (pattern_count(lhs + 2 * S, t->content + (size_t)c * S, S, &acc)) return -1;
+  }
+  *h = acc;
+  return 0;
+}
+
+/* H_j = sum over contexts of the combinatorial counts (int64, -1 overflow). */
+static int rule_total(const oracle_model* m, const term_t* t, int j, int64_t* H) {
+  int64_t total = 0;
+  for (int c = 0; c < t->C; c++) {
+    if (!is_context(m, t, j, c)) continue;
+    int64_t h;
+    if (match_count(m, t, j, c, &h)) return -1;
+    int64_t s;
+    if (__builtin_add_overflow(total, h, &s)) return -1;
+    total = s;
+  }
+  *H = total;
+  return 0;
+}
+
+/* Observables: flat models give the root content; otherwise content totals  */
+/* per label [L][S], wrap totals per label 1..L-1 [L-1][S], alive count per  */
+/* label [L].  Totals are summed in int64 and saturate at INT32_MAX.         */
+static int num_obs(const oracle_model* m) {
+  if (m->L == 1 && m->C == 1) return m->S;
+  return m->L * m->S + (m->L - 1) * m->S + m->L;
+}
+
+static void observe(const oracle_model* m, const term_t* t, int32_t* out) {
+  const int S = m->S, L = m->L;
+  if (L == 1 && m->C == 1) {
+    for (int x = 0; x < S; x++) out[x] = t->content[x];
+    return;
+  }
+  int O = num_obs(m);
+  int64_t tot[4096];
+  int64_t* acc = O <= 4096 ? tot : malloc(sizeof(int64_t) * O);
+  for (int o = 0; o < O; o++) acc[o] = 0;
+  for (int c = 0; c < t->C; c++) {
+    if (!t->alive[c]) continue;
+    int l = t->label[c];
+    for (int x = 0; x < S; x++) acc[l * S + x] += t->content[(size_t)c * S + x];
+    if (l > 0)
+      for (int x = 0; x < S; x++) acc[L * S + (l - 1) * S + x] += t->wrap[(size_t)c * S + x];
+    acc[L * S + (L - 1) * S + l] += 1;
+  }
+  for (int o = 0; o < O; o++) out[o] = acc[o] > 2147483647LL ? 2147483647 : (int32_t)acc[o];
+  if (acc != tot) free(acc);
+}
+
+/* Check that a new value fits int32. */
+static int fits(int64_t v) { return v >= 0 && v <= 2147483647LL; }
+
+/* Update step: delete P sigma and add O sigma at the chosen context.        */
+/* Returns ST_OK, ST_CAPACITY or ST_INT_OVERFLOW (then nothing changed).     */
+static int apply_rule(const oracle_model* m, term_t* t, int j, int c) {
+  const int S = m->S;
+  const int32_t* lhs = m->lhs + (size_t)j * 3 * S;
+  const int32_t* rhs = m->rhs + (size_t)j * 3 * S;
+  int kind = m->kind[j];
+  if (kind == K_LOCAL) {
+    int32_t* x = t->content + (size_t)c * S;
+    for (int s = 0; s < S; s++)
+      if (!fits((int64_t)x[s] + rhs[s] - lhs[s])) return ST_INT_OVERFLOW;
+    for (int s = 0; s < S; s++) x[s] = x[s] + rhs[s] - lhs[s];
+    return ST_OK;
+  }
+  if (kind == K_PARENT_CHILD) {
+    int q = t->parent[c];
+    int32_t* xp = t->content + (size_t)q * S;
+    int32_t* w = t->wrap + (size_t)c * S;
+    int32_t* xc = t->content + (size_t)c * S;
+    for (int s = 0; s < S; s++) {
+      if (!fits((int64_t)xp[s] + rhs[s] - lhs[s])) return ST_INT_OVERFLOW;
+      if (!fits((int64_t)w[s] + rhs[S + s] - lhs[S + s])) return ST_INT_OVERFLOW;
+      if (!fits((int64_t)xc[s] + rhs[2 * S + s] - lhs[2 * S + s])) return ST_INT_OVERFLOW;
+    }
+    for (int s = 0; s < S; s++) {
+      xp[s] = xp[s] + rhs[s] - lhs[s];
+      w[s] = w[s] + rhs[S + s] - lhs[S + s];
+      xc[s] = xc[s] + rhs[2 * S + s] - lhs[2 * S + s];
+    }
+    return ST_OK;
+  }
+  if (kind == K_CREATE) {
+    int e = -1;
+    for (int d = 1; d < t->C; d++)
+      if (!t->alive[d]) { e = d; break; }
+    if (e < 0) return ST_CAPACITY;
+    int32_t* x = t->content + (size_t)c * S;
+    for (int s = 0; s < S; s++)
+      if (!fits((int64_t)x[s] + rhs[s] - lhs[s])) return ST_INT_OVERFLOW;
+    for (int s = 0; s < S; s++) x[s] = x[s] + rhs[s] - lhs[s];
+    t->alive[e] = 1;
+    t->label[e] = m->child_label[j];
+    t->parent[e] = c;
+    for (int s = 0; s < S; s++) {
+      t->wrap[(size_t)e * S + s] = rhs[S + s];
+      t->content[(size_t)e * S + s] = rhs[2 * S + s];
+    }
+    return ST_OK;
+  }
+  /* K_DISSOLVE */
+  {
+    int q = t->parent[c];
+    int32_t* xp = t->content + (size_t)q * S;
+    int32_t* w = t->wrap + (size_t)c * S;
+    int32_t* xc = t->content + (size_t)c * S;
+    for (int s = 0; s < S; s++) {
+      int64_t v = (int64_t)xp[s] + rhs[s] - lhs[s] + ((int64_t)w[s] - lhs[S + s]) +
+                  ((int64_t)xc[s] - lhs[2 * S + s]);
+      if (!fits(v)) return ST_INT_OVERFLOW;
+    }
+    for (int s = 0; s < S; s++)
+      xp[s] = xp[s] + rhs[s] - lhs[s] + (w[s] - lhs[S + s]) + (xc[s] - lhs[2 * S + s]);
+    for (int d = 0; d < t->C; d++)
+      if (t->alive[d] && d != c && t->parent[d] == c) t->parent[d] = q;
+    t->alive[c] = 0;
+    t->label[c] = 0;
+    t->parent[c] = -1;
+    for (int s = 0; s < S; s++) {
+      w[s] = 0;
+      xc[s] = 0;
+    }
+    return ST_OK;
+  }
+}
+
+/* FNV-1a 64-bit over the little-endian bytes of (uint32 rule, uint32 slot). */
+static uint64_t fnv_event(uint64_t h, uint32_t rule, uint32_t slot) {
+  uint8_t bytes[8];
+  for (int i = 0; i < 4; i++) bytes[i] = (uint8_t)(rule >> (8 * i));
+  for (int i = 0; i < 4; i++) bytes[4 + i] = (uint8_t)(slot >> (8 * i));
+  for (int i = 0; i < 8; i++) {
+    h ^= bytes[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+/* Load the initial term for sweep point p; returns 0 if valid.              */
+static int load_init(const oracle_model* m, const int32_t* init, int p, int Pi, term_t* t) {
+  const int S = m->S, C = m->C;
+  int ip = Pi == 1 ? 0 : p;
+  for (int c = 0; c < C; c++) {
+    t->alive[c] = 0;
+    t->label[c] = 0;
+    t->parent[c] = -1;
+  }
+  memset(t->wrap, 0, sizeof(int32_t) * (size_t)C * S);
+  memset(t->content, 0, sizeof(int32_t) * (size_t)C * S);
+  if (m->L == 1 && C == 1) {
+    const int32_t* x = init + (size_t)ip * S;
+    t->alive[0] = 1;
+    for (int s = 0; s < S; s++) {
+      if (x[s] < 0) return -1;
+      t->content[s] = x[s];
+    }
+    return 0;
+  }
+  const int W = 3 + 2 * S;
+  const int32_t* img = init + (size_t)ip * C * W;
+  for (int c = 0; c < C; c++) {
+    const int32_t* row = img + (size_t)c * W;
+    if (row[0] != 0 && row[0] != 1) return -1;
+    t->alive[c] = row[0];
+    if (!row[0]) continue;
+    t->label[c] = row[1];
+    t->parent[c] = row[2];
+    for (int s = 0; s < S; s++) {
+      t->wrap[(size_t)c * S + s] = row[3 + s];
+      t->content[(size_t)c * S + s] = row[3 + S + s];
+      if (row[3 + s] < 0 || row[3 + S + s] < 0) return -1;
+    }
+  }
+  /* the root: slot 0, alive, label 0, no parent, empty wrap */
+  if (!t->alive[0] || t->label[0] != 0 || t->parent[0] != -1) return -1;
+  for (int s = 0; s < S; s++)
+    if (t->wrap[s] != 0) return -1;
+  for (int c = 1; c < C; c++) {
+    if (!t->alive[c]) continue;
+    if (t->label[c] < 1 || t->label[c] >= m->L) return -1;
+    /* the parent chain must reach the root through alive slots */
+    int q = c, steps = 0;
+    while (q != 0) {
+      q = t->parent[q];
+      if (q < 0 || q >= C || !t->alive[q] || ++steps > C) return -1;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One trajectory.  The score part (partials != NULL) follows the same path  */
+/* and accumulates, per grid point g, c(g) * S_j(g) with                      */
+/*   c(g)   = sum_o grad_means[g][o] * (X_o(g) - means[g][o])                */
+/*   S_j(g) = N_j(g) / k_j - I_j(g),  I_j(g) = int_0^{g} H_j(X(s)) ds        */
+/* (the likelihood-ratio score of a CTMC path, a_j = k_j H_j).               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const oracle_model* m;
+  const double* k;
+  const double* grid;
+  int G, O, M;
+  int32_t* states;        /* [G][O] or NULL */
+  const double* means;    /* [G][O] or NULL */
+  const double* gmeans;   /* [G][O] or NULL */
+  double* partial;        /* [M] or NULL */
+  int64_t* N;             /* [M] */
+  double* I;              /* [M] */
+  int64_t* H;             /* [M] */
+  int32_t* obs;           /* [O] */
+} traj_ctx;
+
+static void record(traj_ctx* x, const term_t* t, int g, double now) {
+  observe(x->m, t, x->obs);
+  if (x->states) memcpy(x->states + (size_t)g * x->O, x->obs, sizeof(int32_t) * x->O);
+  if (x->partial) {
+    double cg = 0.0;
+    for (int o = 0; o < x->O; o++)
+      cg = cg + x->gmeans[(size_t)g * x->O + o] * ((double)x->obs[o] - x->means[(size_t)g * x->O + o]);
+    double dt = x->grid[g] - now;
+    for (int j = 0; j < x->M; j++) {
+      double Ig = x->I[j] + (double)x->H[j] * dt;
+      double Sj = (double)x->N[j] / x->k[j] - Ig;
+      x->partial[j] = x->partial[j] + cg * Sj;
+    }
+  }
+}
+
+static int valid_grid(const double* grid, int G) {
+  if (G < 1) return 0;
+  if (!(grid[0] >= 0.0) || !isfinite(grid[0])) return 0;
+  for (int g = 1; g < G; g++)
+    if (!(grid[g] > grid[g - 1]) || !isfinite(grid[g])) return 0;
+  return 1;
+}
+
+int32_t oracle_num_observables(const oracle_model* m) { return num_obs(m); }
+
+/*
+ * Simulate trajectories q in [q_begin, q_end), q = p*R + r.
+ * Output arrays are indexed by (q - q_begin); any of them may be NULL.
+ *   states   [nq][G][O] int32     status [nq] int32    events [nq] int64
+ *   hash     [nq] uint64          final_t [nq] double
+ *   log_*    [nq][log_cap]: rule, slot and time of the first log_cap events
+ *   means/grad_means [P][G][O], partials [nq][M]: score accumulation
+ * Returns 0, or -1 if the model is malformed.
+ */
+int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32_t R,
+                    const int32_t* init, int32_t Pi, const double* grid, int32_t G,
+                    uint64_t seed, int64_t max_events, int64_t q_begin, int64_t q_end,
+                    int32_t* states, int32_t* status, int64_t* events, uint64_t* hash,
+                    double* final_t, int32_t log_cap, int32_t* log_rule, int32_t* log_slot,
+                    double* log_t, const double* means, const double* grad_means,
+                    double* partials) {
+  const int S = m->S, C = m->C, M = m->M, O = num_obs(m);
+  if (S < 1 || C < 1 || M < 1 || m->L < 1) return -1;
+  for (int j = 0; j < M; j++) {
+    if (m->kind[j] < 0 || m->kind[j] > 3) return -1;
+    if (m->ctx_label[j] < 0 || m->ctx_label[j] >= m->L) return -1;
+    if (m->kind[j] != K_LOCAL && (m->child_label[j] < 1 || m->child_label[j] >= m->L)) return -1;
+  }
+  term_t t;
+  t.S = S;
+  t.C = C;
+  t.alive = malloc(sizeof(int32_t) * C);
+  t.label = malloc(sizeof(int32_t) * C);
+  t.parent = malloc(sizeof(int32_t) * C);
+  t.wrap = malloc(sizeof(int32_t) * (size_t)C * S);
+  t.content = malloc(sizeof(int32_t) * (size_t)C * S);
+  double* a = malloc(sizeof(double) * M);
+  traj_ctx x;
+  x.m = m;
+  x.grid = grid;
+  x.G = G;
+  x.O = O;
+  x.M = M;
+  x.N = malloc(sizeof(int64_t) * M);
+  x.I = malloc(sizeof(double) * M);
+  x.H = malloc(sizeof(int64_t) * M);
+  x.obs = malloc(sizeof(int32_t) * O);
+  const double T = grid[G - 1];
+  const int grid_ok = valid_grid(grid, G);
+
+  for (int64_t q = q_begin; q < q_end; q++) {
+    const int64_t lq = q - q_begin;
+    const int p = (int)(q / R), r = (int)(q % R);
+    x.k = rates + (size_t)p * M;
+    x.states = states ? states + (size_t)lq * G * O : NULL;
+    x.means = means ? means + (size_t)p * G * O : NULL;
+    x.gmeans = grad_means ? grad_means + (size_t)p * G * O : NULL;
+    x.partial = partials ? partials + (size_t)lq * M : NULL;
+    for (int j = 0; j < M; j++) {
+      x.N[j] = 0;
+      x.I[j] = 0.0;
+      x.H[j] = 0;
+      if (x.partial) x.partial[j] = 0.0;
+    }
+    double tnow = 0.0;
+    int64_t n = 0;
+    uint64_t h = 0xcbf29ce484222325ull;
+    int st = ST_OK;
+    int gi = 0;
+    int rates_ok = 1;
+    for (int j = 0; j < M; j++)
+      if (!(x.k[j] > 0.0) || !isfinite(x.k[j])) rates_ok = 0;
+    if (!rates_ok || !grid_ok || load_init(m, init, p, Pi, &t) != 0) {
+      st = ST_BAD_INPUT;
+      if (x.states) memset(x.states, 0, sizeof(int32_t) * (size_t)G * O);
+      goto done;
+    }
+    for (;;) {
+      /* 1. Match: every rule at every compartment. */
+      int overflow = 0;
+      for (int j = 0; j < M; j++) {
+        if (rule_total(m, &t, j, &x.H[j])) { overflow = 1; break; }
+        a[j] = x.k[j] * (double)x.H[j];
+      }
+      double a0 = 0.0;
+      if (!overflow) {
+        a0 = oracle_tree_sum(a, M);
+        if (!isfinite(a0)) overflow = 1;
+      }
+      if (overflow) {
+        /* H of the current term is unusable: record states, keep the score unchanged */
+        st = ST_PROP_OVERFLOW;
+        for (int j = 0; j < M; j++) x.H[j] = 0;
+        for (; gi < G; gi++) record(&x, &t, gi, tnow);
+        break;
+      }
+      if (n == max_events) {
+        st = ST_EVENT_LIMIT;
+        for (; gi < G; gi++) record(&x, &t, gi, tnow);
+        break;
+      }
+      if (a0 == 0.0) {
+        st = ST_ABSORBED;
+        for (; gi < G; gi++) record(&x, &t, gi, tnow);
+        break;
+      }
+      /* 2. Resolve: tau ~ Exp(a0), rule j with probability a_j / a0. */
+      uint32_t w[4];
+      draw(seed, (uint32_t)n, 0, (uint32_t)r, (uint32_t)p, w);
+      double u_tau = oracle_u52(w[0], w[1]);
+      double u_sel = oracle_u52(w[2], w[3]);
+      double tau = (-oracle_log_spec(u_tau)) / a0;
+      double tnext = tnow + tau;
+      while (gi < G && grid[gi] < tnext) {
+        record(&x, &t, gi, tnow);
+        gi++;
+      }
+      if (tnext > T) break; /* the event falls past the horizon: not applied */
+      int j = oracle_select(a, M, u_sel * a0);
+      /* stochastic choice of the context within rule j: x in [0, H_j) */
+      uint32_t wc[4];
+      draw(seed, (uint32_t)n, 1, (uint32_t)r, (uint32_t)p, wc);
+      uint64_t W = (uint64_t)wc[0] | ((uint64_t)wc[1] << 32);
+      uint64_t xc = (uint64_t)(((unsigned __int128)W * (unsigned __int128)(uint64_t)x.H[j]) >> 64);
+      int ctx = -1;
+      uint64_t cum = 0;
+      for (int c = 0; c < C; c++) {
+        if (!is_context(m, &t, j, c)) continue;
+        int64_t hc;
+        match_count(m, &t, j, c, &hc);
+        cum += (uint64_t)hc;
+        if (xc < cum) { ctx = c; break; }
+      }
+      /* 3. Update. */
+      int ast = apply_rule(m, &t, j, ctx);
+      if (ast != ST_OK) {
+        st = ast;
+        for (; gi < G; gi++) record(&x, &t, gi, tnow);
+        break;
+      }
+      if (x.partial) {
+        for (int i = 0; i < M; i++) x.I[i] = x.I[i] + (double)x.H[i] * (tnext - tnow);
+        x.N[j] += 1;
+      }
+      if (log_cap > 0 && n < log_cap) {
+        if (log_rule) log_rule[lq * log_cap + n] = j;
+        if (log_slot) log_slot[lq * log_cap + n] = ctx;
+        if (log_t) log_t[lq * log_cap + n] = tnext;
+      }
+      tnow = tnext;
+      n = n + 1;
+      h = fnv_event(h, (uint32_t)j, (uint32_t)ctx);
+    }
+  done:
+    if (status) status[lq] = st;
+    if (events) events[lq] = n;
+    if (hash) hash[lq] = h;
+    if (final_t) final_t[lq] = tnow;
+  }
+  free(t.alive);
+  free(t.label);
+  free(t.parent);
+  free(t.wrap);
+  free(t.content);
+  free(a);
+  free(x.N);
+  free(x.I);
+  free(x.H);
+  free(x.obs);
+  return 0;
+}
+
+/* Combinatorial count H_j of every rule at a given term (for the pins).     */
+/* term: flat counts [S] or slot image [C][3+2S].  Returns -1 on overflow or */
+/* invalid term.                                                              */
+int oracle_rule_totals(const oracle_model* m, const int32_t* init, int64_t* H_out) {
+  const int S = m->S, C = m->C;
+  term_t t;
+  t.S = S;
+  t.C = C;
+  t.alive = malloc(sizeof(int32_t) * C);
+  t.label = malloc(sizeof(int32_t) * C);
+  t.parent = malloc(sizeof(int32_t) * C);
+  t.wrap = malloc(sizeof(int32_t) * (size_t)C * S);
+  t.content = malloc(sizeof(int32_t) * (size_t)C * S);
+  int rc = load_init(m, init, 0, 1, &t);
+  for (int j = 0; rc == 0 && j < m->M; j++)
+    if (rule_total(m, &t, j, &H_out[j])) rc = -1;
+  free(t.alive);
+  free(t.label);
+  free(t.parent);
+  free(t.wrap);
+  free(t.content);
+  return rc;
+}
+
+/* Vector helpers for the pins (plain loops over the scalar routines). */
+void oracle_log_spec_array(const double* u, double* out, int64_t n) {
+  for (int64_t i = 0; i < n; i++) out[i] = oracle_log_spec(u[i]);
+}
+
+void oracle_philox_array(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int64_t n) {
+  for (int64_t i = 0; i < n; i++) oracle_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}

@@ -1,0 +1,407 @@
+"""Seeded synthetic inputs for the batched CWC / Gillespie simulator.
+
+This module is the single place where inputs are generated; both the CUDA path
+and the CPU oracle receive what it builds.  It contains no simulation
+arithmetic: no propensities, no random streams of the method, no time
+advance.  Random choices here use SplitMix64 (Steele, Lea, Flood, "Fast
+splittable pseudorandom number generators", OOPSLA 2014), written out in pure
+Python so that every machine builds identical models from the same seed.
+
+Model representation (the restricted CWC rule language of Sec. 2.1-2.2):
+
+* ``S`` atoms (species) ``0..S-1``; ``L`` compartment labels, label 0 is the
+  top level (the root compartment, which has no wrap); ``C`` compartment
+  slots per trajectory, slot 0 is the root.
+* Rule ``j`` has a ``kind``:
+  ``LOCAL``        ``l: p X -> p' X`` rewrites the content of a compartment of
+                   label ``l`` (the paper's example ``l: a b X -> c X``);
+  ``PARENT_CHILD`` ``l: p X (w x | q Y)^l' -> p' X (w' x | q' Y)^l'`` rewrites
+                   a parent content of label ``l`` together with the wrap and
+                   content of one child compartment of label ``l'`` (binding
+                   to a wrap, transport in and out);
+  ``CREATE``       ``l: p X -> p' X (w' | q')^l'`` makes a new compartment;
+  ``DISSOLVE``     ``l: p X (w x | q Y)^l' -> p' X x Y`` removes a child and
+                   releases its remaining wrap and content into the parent.
+* ``lhs[j, 0/1/2, :]`` are the multiplicities of the parent (context)
+  content, child wrap and child content patterns; ``rhs`` the same for the
+  right-hand side.
+
+Flat mass-action networks are the special case ``L = 1``, ``C = 1`` and only
+``LOCAL`` rules on label 0.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import math
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+LOCAL, PARENT_CHILD, CREATE, DISSOLVE = 0, 1, 2, 3
+KIND_NAMES = {LOCAL: "LOCAL", PARENT_CHILD: "PARENT_CHILD", CREATE: "CREATE", DISSOLVE: "DISSOLVE"}
+
+_MASK64 = (1 << 64) - 1
+
+# Horizons T of the synthetic workloads, chosen so that the mean number of
+# events per trajectory is near each workload's target (file written by
+# oracle/calibrate_horizons.py).
+HORIZONS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workload_horizons.json")
+
+
+def calibrated_horizon(name: str) -> Optional[float]:
+    try:
+        with open(HORIZONS_PATH) as f:
+            return float(json.load(f)[name])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class SplitMix64:
+    """SplitMix64 generator (input generation only)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        """Double in [0, 1) with 53 random bits."""
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Integer uniform on [lo, hi] (inclusive); modulo bias is irrelevant here."""
+        return lo + self.next_u64() % (hi - lo + 1)
+
+    def log_uniform(self, lo_exp: float, hi_exp: float) -> float:
+        return 10.0 ** (lo_exp + (hi_exp - lo_exp) * self.uniform())
+
+    def choice_distinct(self, n: int, k: int) -> List[int]:
+        pool = list(range(n))
+        out = []
+        for _ in range(k):
+            i = self.randint(0, len(pool) - 1)
+            out.append(pool.pop(i))
+        return out
+
+
+@dataclasses.dataclass
+class Model:
+    n_species: int
+    n_labels: int
+    max_compartments: int
+    kind: np.ndarray          # int32 [M]
+    ctx_label: np.ndarray     # int32 [M]
+    child_label: np.ndarray   # int32 [M]  (-1 for LOCAL)
+    lhs: np.ndarray           # int32 [M, 3, S]
+    rhs: np.ndarray           # int32 [M, 3, S]
+    name: str = ""
+
+    @property
+    def n_rules(self) -> int:
+        return int(self.kind.shape[0])
+
+    @property
+    def is_flat(self) -> bool:
+        return self.n_labels == 1 and self.max_compartments == 1
+
+    @property
+    def n_observables(self) -> int:
+        S, L = self.n_species, self.n_labels
+        if self.is_flat:
+            return S
+        return L * S + (L - 1) * S + L
+
+    def contiguous(self) -> "Model":
+        return dataclasses.replace(
+            self,
+            kind=np.ascontiguousarray(self.kind, dtype=np.int32),
+            ctx_label=np.ascontiguousarray(self.ctx_label, dtype=np.int32),
+            child_label=np.ascontiguousarray(self.child_label, dtype=np.int32),
+            lhs=np.ascontiguousarray(self.lhs, dtype=np.int32),
+            rhs=np.ascontiguousarray(self.rhs, dtype=np.int32),
+        )
+
+
+Reaction = Tuple[Dict[int, int], Dict[int, int]]
+
+
+def flat_model(n_species: int, reactions: Sequence[Reaction], name: str = "") -> Model:
+    """Flat mass-action network: every reaction is a LOCAL rule of the root."""
+    M = len(reactions)
+    lhs = np.zeros((M, 3, n_species), np.int32)
+    rhs = np.zeros((M, 3, n_species), np.int32)
+    for j, (reac, prod) in enumerate(reactions):
+        for s, c in reac.items():
+            lhs[j, 0, s] += c
+        for s, c in prod.items():
+            rhs[j, 0, s] += c
+    return Model(n_species, 1, 1, np.zeros(M, np.int32), np.zeros(M, np.int32),
+                 np.full(M, -1, np.int32), lhs, rhs, name)
+
+
+@dataclasses.dataclass
+class RuleSpec:
+    kind: int
+    ctx_label: int
+    child_label: int = -1
+    lhs_ctx: Dict[int, int] = dataclasses.field(default_factory=dict)
+    lhs_wrap: Dict[int, int] = dataclasses.field(default_factory=dict)
+    lhs_child: Dict[int, int] = dataclasses.field(default_factory=dict)
+    rhs_ctx: Dict[int, int] = dataclasses.field(default_factory=dict)
+    rhs_wrap: Dict[int, int] = dataclasses.field(default_factory=dict)
+    rhs_child: Dict[int, int] = dataclasses.field(default_factory=dict)
+
+
+def cwc_model(n_species: int, n_labels: int, max_compartments: int,
+              rules: Sequence[RuleSpec], name: str = "") -> Model:
+    M = len(rules)
+    lhs = np.zeros((M, 3, n_species), np.int32)
+    rhs = np.zeros((M, 3, n_species), np.int32)
+    kind = np.zeros(M, np.int32)
+    ctx = np.zeros(M, np.int32)
+    child = np.full(M, -1, np.int32)
+    for j, r in enumerate(rules):
+        kind[j], ctx[j], child[j] = r.kind, r.ctx_label, r.child_label
+        for k, d in enumerate((r.lhs_ctx, r.lhs_wrap, r.lhs_child)):
+            for s, c in d.items():
+                lhs[j, k, s] += c
+        for k, d in enumerate((r.rhs_ctx, r.rhs_wrap, r.rhs_child)):
+            for s, c in d.items():
+                rhs[j, k, s] += c
+    return Model(n_species, n_labels, max_compartments, kind, ctx, child, lhs, rhs, name)
+
+
+# ----------------------------------------------------------------------------
+# Initial terms.  A flat model takes counts [S]; a compartmentalised model takes
+# a slot image [C, 3 + 2S]: (alive, label, parent, wrap[S], content[S]).
+# ----------------------------------------------------------------------------
+
+def slot_image_width(n_species: int) -> int:
+    return 3 + 2 * n_species
+
+
+def empty_slot_image(model: Model) -> np.ndarray:
+    S, C = model.n_species, model.max_compartments
+    img = np.zeros((C, slot_image_width(S)), np.int32)
+    img[:, 2] = -1
+    img[0, 0] = 1  # root alive, label 0, parent -1
+    return img
+
+
+# ----------------------------------------------------------------------------
+# Batches
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Batch:
+    """One call's inputs: P sweep points x R replicas on a time grid."""
+    model: Model
+    rates: np.ndarray     # float64 [P, M]
+    init: np.ndarray      # int32 [Pi, S] (flat) or [Pi, C, 3+2S]; Pi in {1, P}
+    grid: np.ndarray      # float64 [G], 0 <= g0 < g1 < ...
+    R: int
+    seed: int
+    max_events: int = (1 << 32) - 1
+    name: str = ""
+
+    @property
+    def P(self) -> int:
+        return int(self.rates.shape[0])
+
+    @property
+    def G(self) -> int:
+        return int(self.grid.shape[0])
+
+    @property
+    def n_traj(self) -> int:
+        return self.P * self.R
+
+
+def uniform_grid(T: float, G: int) -> np.ndarray:
+    """g_i = i*T/(G-1), i = 0..G-1 (g_0 = 0 records the initial term)."""
+    if G == 1:
+        return np.array([T], np.float64)
+    return np.array([T * i / (G - 1) for i in range(G)], np.float64)
+
+
+def crude_rate(model: Model, rates: np.ndarray, counts: np.ndarray) -> float:
+    """Rough total event rate of a flat model at ``counts``: sum_j k_j prod_x n_x^nu.
+
+    Used only to pick a time horizon that gives roughly the wanted number of
+    events; it deliberately ignores the exact combinatorial count.
+    """
+    total = 0.0
+    for j in range(model.n_rules):
+        term = float(rates[j])
+        for s in range(model.n_species):
+            nu = int(model.lhs[j, 0, s])
+            if nu:
+                term *= float(counts[s]) ** nu
+        total += term
+    return total
+
+
+def random_flat_network(rng: SplitMix64, S: int, n_order1: int, n_order2: int,
+                        n_inflow_pairs: int = 0, name: str = "") -> Model:
+    """Random mass-action network without sink species.
+
+    * ``n_inflow_pairs`` pairs (0 -> X_i, X_i -> 0) on distinct species;
+    * ``n_order1`` unimolecular conversions ``A -> B``; the first ``S`` of them
+      form one directed cycle through all species (a random permutation), so
+      every species has an outgoing reaction and molecules never pile up in a
+      sink; the rest are random (B != A);
+    * ``n_order2`` bimolecular reactions ``A + B -> C + D`` (alternately A != B
+      and ``2A``), products drawn independently (``2C`` is possible).
+    Apart from the inflow/outflow pairs every reaction conserves the molecule
+    count.  The reaction order is shuffled with the same seeded stream.
+    """
+    if n_order1 < S:
+        raise ValueError("need at least S unimolecular reactions for the cycle")
+    reactions: List[Reaction] = []
+    inflow_species = rng.choice_distinct(S, n_inflow_pairs)
+    for s in inflow_species:
+        reactions.append(({}, {s: 1}))
+        reactions.append(({s: 1}, {}))
+    perm = rng.choice_distinct(S, S)
+    body: List[Reaction] = []
+    for i in range(S):
+        body.append(({perm[i]: 1}, {perm[(i + 1) % S]: 1}))
+    for _ in range(n_order1 - S):
+        a = rng.randint(0, S - 1)
+        b = (a + rng.randint(1, S - 1)) % S
+        body.append(({a: 1}, {b: 1}))
+    for i in range(n_order2):
+        if i % 2 == 0:
+            a, b = rng.choice_distinct(S, 2)
+            reac = {a: 1, b: 1}
+        else:
+            a = rng.randint(0, S - 1)
+            reac = {a: 2}
+        c = rng.randint(0, S - 1)
+        d = rng.randint(0, S - 1)
+        prod: Dict[int, int] = {}
+        prod[c] = prod.get(c, 0) + 1
+        prod[d] = prod.get(d, 0) + 1
+        body.append((reac, prod))
+    for i in range(len(body) - 1, 0, -1):
+        k = rng.randint(0, i)
+        body[i], body[k] = body[k], body[i]
+    reactions.extend(body)
+    return flat_model(S, reactions, name)
+
+
+def reaction_order(model: Model, j: int) -> int:
+    return int(model.lhs[j, 0].sum())
+
+
+def _flat_batch(model: Model, rng: SplitMix64, P: int, R: int, G: int, x_lo: int, x_hi: int,
+                target_events: float, seed: int, rate_decades: Tuple[float, float] = (-3.0, 0.0),
+                name: str = "", use_calibrated: bool = True) -> Batch:
+    """Rates, initial counts and horizon for a flat network.
+
+    Rate constants are log-uniform over ``rate_decades`` in concentration
+    units and converted to stochastic constants for a system of size
+    Omega = (x_lo + x_hi) / 2 molecules (order 0: k*Omega, order 1: k,
+    order 2: k/Omega), the usual volume scaling of mass-action kinetics.  The
+    horizon is the calibrated one for ``name`` when available (and the
+    default target), else T = target_events / crude_rate(x0).
+    """
+    M, S = model.n_rules, model.n_species
+    omega = 0.5 * (x_lo + x_hi)
+    base = np.empty(M, np.float64)
+    for j in range(M):
+        k = rng.log_uniform(*rate_decades)
+        base[j] = k * omega ** (1 - reaction_order(model, j))
+    x0 = np.array([rng.randint(x_lo, x_hi) for _ in range(S)], np.int32)
+    T = target_events / crude_rate(model, base, x0)
+    if use_calibrated:
+        Tc = calibrated_horizon(name)
+        if Tc is not None:
+            T = Tc
+    rates = np.tile(base, (P, 1))
+    return Batch(model, rates, x0[None, :].copy(), uniform_grid(T, G), R, seed, name=name)
+
+
+# ----------------------------------------------------------------------------
+# The five benchmark workloads (shapes of the paper's multi-instance runs,
+# Sec. 5.2: replicas and parameter sweeps of mass-action / CWC models).
+# ----------------------------------------------------------------------------
+
+def flat8x12(R: int = 64, G: int = 100, use_calibrated: bool = True) -> Batch:
+    """8 species, 12 reactions (8-cycle of conversions + 4 bimolecular), 64 replicas,
+    ~1e4 events, 100-point grid."""
+    rng = SplitMix64(1)
+    model = random_flat_network(rng, 8, 8, 4, 0, "flat8x12")
+    return _flat_batch(model, rng, 1, R, G, 50, 500, 1e4, seed=101, name="flat8x12",
+                       use_calibrated=use_calibrated)
+
+
+def flat32x64(R: int = 65536, G: int = 1000, use_calibrated: bool = True) -> Batch:
+    """32 species, 64 reactions (8 inflow/outflow pairs, 32 order-1, 16 order-2)."""
+    rng = SplitMix64(2)
+    model = random_flat_network(rng, 32, 32, 16, 8, "flat32x64")
+    return _flat_batch(model, rng, 1, R, G, 100, 5000, 1e5, seed=102, name="flat32x64",
+                       use_calibrated=use_calibrated)
+
+
+def sweep256x256(P: int = 256, R: int = 256, G: int = 1000) -> Batch:
+    """flat32x64's network under P rate vectors, R replicas each.
+
+    Sweep point p scales every rate by a common factor 10^U(-1,1) (two
+    decades, so trajectory lengths vary about 100x across points) times a
+    per-rate jitter 10^U(-1/4,1/4) (so the vectors also differ in shape).
+    """
+    rng = SplitMix64(2)
+    model = random_flat_network(rng, 32, 32, 16, 8, "flat32x64")
+    b = _flat_batch(model, rng, 1, R, G, 100, 5000, 1e5, seed=104, name="flat32x64")
+    srng = SplitMix64(204)
+    rates = np.empty((P, model.n_rules), np.float64)
+    for p in range(P):
+        common = srng.log_uniform(-1.0, 1.0)
+        rates[p] = b.rates[0] * common * np.array(
+            [srng.log_uniform(-0.25, 0.25) for _ in range(model.n_rules)])
+    return Batch(model, rates, b.init, b.grid, R, 104, name="sweep256x256")
+
+
+def flat16x24(R: int = 131072, G: int = 100, use_calibrated: bool = True) -> Batch:
+    """16 species, 24 reactions (2 inflow/outflow pairs, 16 order-1, 4 order-2)."""
+    rng = SplitMix64(5)
+    model = random_flat_network(rng, 16, 16, 4, 2, "flat16x24")
+    return _flat_batch(model, rng, 1, R, G, 50, 500, 1e4, seed=105, name="flat16x24",
+                       use_calibrated=use_calibrated)
+
+
+# ----------------------------------------------------------------------------
+# Small models with known laws (used to pin the oracle)
+# ----------------------------------------------------------------------------
+
+def birth_death() -> Model:
+    """0 -> A (k1), A -> 0 (k2)."""
+    return flat_model(1, [({}, {0: 1}), ({0: 1}, {})], "birth_death")
+
+
+def isomerisation() -> Model:
+    """A -> B (kf), B -> A (kb)."""
+    return flat_model(2, [({0: 1}, {1: 1}), ({1: 1}, {0: 1})], "isomerisation")
+
+
+def dimerisation() -> Model:
+    """2A -> B (k1), B -> 2A (k2)."""
+    return flat_model(2, [({0: 2}, {1: 1}), ({1: 1}, {0: 2})], "dimerisation")
+
+
+def heterodimer() -> Model:
+    """A + B -> C (k1), C -> A + B (k2)."""
+    return flat_model(3, [({0: 1, 1: 1}, {2: 1}), ({2: 1}, {0: 1, 1: 1})], "heterodimer")
+
+
+def paper_example_rule() -> Model:
+    """The worked example of Sec. 2.2: l: a b X -> c X (species a=0, b=1, c=2)."""
+    return flat_model(3, [({0: 1, 1: 1}, {2: 1})], "paper_example")
