@@ -1,0 +1,340 @@
+"""Benchmark: SSA events per second of the batched direct method on GB300.
+
+Workload (one "step"): the 32-species / 64-reaction flat network, 65,536
+replicas x ~1e5 events each, sampled on a 1,000-point grid (int32 states
+[65536, 1000, 32] = 8.4 GB written per step), FP64 propensities and time.
+A step is one cwc_simulate call over the whole batch; events = applied
+reactions summed over trajectories.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank simulates its own shard of replicas
+(replica_offset = rank * R, so the shards are distinct trajectories of one
+larger batch; no collective on the data path) and rank 0 prints one JSON line
+with the events of all ranks over the slowest rank's time ("weak" scaling).
+``--impl reference`` times the CPU oracle (the reference arm) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "flat32x64"
+WORKLOAD_DESC = ("flat mass-action network, 32 species, 64 reactions (8 inflow/outflow pairs, 32 conversions, "
+                 "16 bimolecular), 65536 replicas x ~1e5 events, 1000-point grid, int32 states, FP64 propensities/time")
+METRIC = "SSA events/sec"
+UNIT = "events/s"
+KERNEL_SOURCES = ["paper_1010_2438_gb300/csrc/flat_ssa.cu", "paper_1010_2438_gb300/csrc/ssa_device.cuh",
+                  "paper_1010_2438_gb300/csrc/cwc_internal.h"]
+# FP64 pipe of one GB300: 152 SMs x 2 FP64 lanes per clock x 2.07 GHz (the
+# nominal 1.25 TFLOP/s dense FP64 counts an FMA as two flops).  A DADD/DMUL/
+# DFMA stream measured 5.0e11 op/s on the GB300s.
+FP64_PEAK_OPS = 152 * 2 * 2.07e9
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def fp64_ops_per_event(model) -> float:
+    """Algorithmic FP64 arithmetic operations of one event of the method
+    (written specification), averaged uniformly over the rules fired:
+      log: m-1, m+1, one division, s*s, 9 Horner steps (18 ops), z*p, s*(.), s+(.),
+           e*ln2 + r                                                    = 26
+      tau = -L / a0 (1), t + tau (1), x = u_sel * a0 (1)                 =  3
+      tree descent: one subtraction per level (5) + leaf scan (B-1)
+      update: one k_i * H_i per dependent, (B-1) adds per dirty leaf, one add
+      per dirty internal node.
+    Integer work (Philox, uniforms, counts, comparisons of doubles as bit
+    patterns, hashing) is not counted."""
+    from paper_1010_2438_gb300.workloads import Model  # noqa: F401
+    M, S = model.n_rules, model.n_species
+    B = (M + 31) // 32
+    lhs = model.lhs[:, 0, :]
+    delta = model.rhs[:, 0, :] - lhs
+    upd = []
+    for j in range(M):
+        changed = set(np.nonzero(delta[j])[0].tolist())
+        deps = [i for i in range(M) if changed & set(np.nonzero(lhs[i])[0].tolist())]
+        leaves = sorted(set(i // B for i in deps))
+        nodes = set()
+        for l in leaves:
+            nodes |= {l >> 1, 16 + (l >> 2), 24 + (l >> 3), 28 + (l >> 4), 30}
+        upd.append(len(deps) + (B - 1) * len(leaves) + len(nodes))
+    return 26 + 3 + 5 + (B - 1) + float(np.mean(upd))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+
+def oracle_events_per_sec(batch, n_traj: int, threads: int):
+    import oracle
+    t0 = time.perf_counter()
+    res = oracle.simulate(batch, 0, n_traj, states=True, threads=threads)
+    dt = time.perf_counter() - t0
+    ev = int(res["events"].sum())
+    return ev / dt, ev, dt
+
+
+def cpu_baseline(batch, threads: int, n_traj: int):
+    rate, ev, dt = oracle_events_per_sec(batch, n_traj, threads)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of %d trajectories (%d events, %.1f s wall on %d threads), full horizon and grid"
+                      % (n_traj, batch.n_traj, ev, dt, threads)}
+
+
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1010_2438_gb300 import workloads as W
+    batch = W.flat32x64()
+    threads = os.cpu_count() or 1
+    n_traj = max(threads, 2 * threads)
+    for _ in range(args.warmup):
+        oracle_events_per_sec(batch, threads, threads)
+    times, evs = [], []
+    for _ in range(args.steps):
+        rate, ev, dt = oracle_events_per_sec(batch, n_traj, threads)
+        times.append(dt)
+        evs.append(ev)
+    value = sum(evs) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC,
+                       "sample_per_step": "%d trajectories" % n_traj},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d of 65536 trajectories per step, full horizon and grid" % n_traj},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--layout", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1010_2438_gb300 import api, capi
+    from paper_1010_2438_gb300 import build as lib_build
+    from paper_1010_2438_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lib_build.build()
+    batch = W.flat32x64()
+    R = batch.R
+    cm = api.CompiledModel(batch.model)
+    rates, init, grid = api.device_inputs(batch, dev)
+    stream = torch.cuda.current_stream()
+    l2_flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = None
+
+    def step(o):
+        return api.simulate(cm, rates, init, grid, R, batch.seed, batch.max_events, states=True, traj=True,
+                            layout=args.layout, block_threads=args.threads, replica_offset=rank * R, out=o)
+
+    for _ in range(args.warmup):
+        out = step(out)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index)
+    barrier()
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        l2_flush.zero_()                      # write 256 MiB > L2 between timed steps
+        starts[i].record(stream)
+        out = step(out)
+        ends[i].record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_total = sum(step_ms) / 1e3
+    events = int(out["events"].sum().item())
+    statuses = torch.bincount(out["status"].reshape(-1).to(torch.int64), minlength=8).tolist()
+    ev_all, t_max = events * args.steps, t_total
+    if world > 1:
+        tt = torch.tensor([float(ev_all), t_total], dtype=torch.float64, device=dev)
+        ev_t = tt[:1].clone()
+        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
+        tm = tt[1:].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ev_all, t_max = float(ev_t.item()), float(tm.item())
+    value = ev_all / t_max
+
+    # roofline of the dominant kernel (the SSA kernel is the whole step but a
+    # 256-byte workspace memset)
+    f_evt = fp64_ops_per_event(batch.model)
+    kernel_s = t_total / args.steps
+    achieved = f_evt * events / kernel_s
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "flat_ssa_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("kernel_source_hash") == kernel_source_hash() and tj.get("workload") == WORKLOAD:
+            traffic = tj.get("dram_bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9, "unit": "GFLOP/s (FP64)",
+                "frac": achieved / FP64_PEAK_OPS, "traffic": traffic,
+                "note": "FP64-pipe bound; %.1f algorithmic FP64 ops/event x %d events / %.4f s; peak derived from "
+                        "152 SMs x 2 FP64 lanes/clk x 2.07 GHz" % (f_evt, events, kernel_s)}
+
+    # end to end through host buffers (pinned): H2D inputs, simulate, D2H states
+    e2e = None
+    if not args.no_e2e:
+        rates_h = torch.from_numpy(np.ascontiguousarray(batch.rates)).pin_memory()
+        init_h = torch.from_numpy(np.ascontiguousarray(batch.init)).pin_memory()
+        grid_h = torch.from_numpy(np.ascontiguousarray(batch.grid)).pin_memory()
+        host_out = torch.empty(tuple(out["states"].shape), dtype=torch.int32, pin_memory=True)
+        bufs = {"out": out}
+        e2e_steps = min(args.steps, 3)
+        api.simulate_host(cm, rates_h, init_h, grid_h, R, batch.seed, batch.max_events, dev_bufs=bufs,
+                          host_out=host_out, replica_offset=rank * R)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            api.simulate_host(cm, rates_h, init_h, grid_h, R, batch.seed, batch.max_events, dev_bufs=bufs,
+                              host_out=host_out, replica_offset=rank * R)
+        e1.record(stream)
+        barrier()
+        te = e0.elapsed_time(e1) / 1e3
+        ev_e = float(events * e2e_steps)
+        if world > 1:
+            t2 = torch.tensor([ev_e, te], dtype=torch.float64, device=dev)
+            a_, b_ = t2[:1].clone(), t2[1:].clone()
+            dist.all_reduce(a_, op=dist.ReduceOp.SUM)
+            dist.all_reduce(b_, op=dist.ReduceOp.MAX)
+            ev_e, te = float(a_.item()), float(b_.item())
+        h2d = rates_h.numel() * 8 + init_h.numel() * 4 + grid_h.numel() * 8
+        e2e = {"value": ev_e / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": host_out.numel() * 4, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        cpu = cpu_baseline(batch, threads, 2 * threads)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "P": batch.P, "R": R,
+                           "G": batch.G, "S": batch.model.n_species, "M": batch.model.n_rules,
+                           "events_per_step_per_gpu": events, "statuses": statuses,
+                           "layout": ["auto(queue)", "static", "queue"][args.layout],
+                           "l2": "256 MiB buffer written between timed steps; outputs 8.4 GB per step",
+                           "parallelism": "replica shards, %d GPU(s)" % world},
+                "gpu_launches": args.steps, "clocks": clk, "roofline": roofline,
+                "e2e": e2e, "cpu_baseline": cpu,
+                "step_ms": [round(x, 3) for x in step_ms]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

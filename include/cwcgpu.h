@@ -1,0 +1,258 @@
+/*
+ * cwcgpu.h -- C ABI of the GB300 library for batched Gillespie direct-method
+ * simulation of Calculus of Wrapped Compartments (CWC) rewrite systems.
+ *
+ * The method (Aldinucci et al., "On Designing Multicore-aware Simulators for
+ * Biological Systems"): CWC terms and rules, Sec. 2.1; stochastic rules whose
+ * rate is the kinetic constant times the number of distinct reactant
+ * combinations, and Gillespie's two-step direct method, Sec. 2.2; the
+ * Match / Resolve / Update simulator step, Sec. 2.3 and Fig. "CWC simulator
+ * pseudo-code" (Sec. 5.1); many independent replicas and parameter-sweep
+ * instances sampled on a fixed simulation-time grid, Sec. 5.2.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device addresses on the current device; host
+ *     pointers are read before the call returns and may be freed afterwards.
+ *   - The caller owns every buffer it passes.  The library owns only what
+ *     cwc_model_create allocates (the compiled rule tables), released by
+ *     cwc_model_destroy.  No entry point other than cwc_model_create
+ *     allocates device memory.
+ *   - Work is enqueued on the given CUDA stream (cudaStream_t passed as
+ *     void*; NULL = the legacy default stream) and runs asynchronously; an
+ *     entry point returns after enqueueing.  Argument errors are detected on
+ *     the host before anything is enqueued and return a status; per-
+ *     trajectory problems found on the device (bad rates, bad grid, counts
+ *     out of range) are reported in the per-trajectory status array.
+ *   - No entry point throws, aborts or falls back to the CPU.  On failure a
+ *     description is available from cwc_last_error() (thread-local).
+ */
+#ifndef CWCGPU_H_
+#define CWCGPU_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes of the entry points. */
+typedef enum {
+  CWC_OK = 0,
+  CWC_ERR_INVALID_ARG = 1,   /* a pointer, size or model field is invalid      */
+  CWC_ERR_UNSUPPORTED = 2,   /* outside the rule language this library runs     */
+  CWC_ERR_CUDA = 3,          /* a CUDA call failed (message in cwc_last_error) */
+  CWC_ERR_WORKSPACE = 4,     /* workspace missing or smaller than required     */
+  CWC_ERR_INTERNAL = 5
+} cwc_status;
+
+/* Status of one trajectory (int32 array traj_status). */
+enum {
+  CWC_TRAJ_OK = 0,            /* reached the last grid point                       */
+  CWC_TRAJ_ABSORBED = 1,      /* total propensity 0; remaining grid = current term */
+  CWC_TRAJ_INT_OVERFLOW = 2,  /* an event would push a count above INT32_MAX; not applied */
+  CWC_TRAJ_PROP_OVERFLOW = 3, /* an int64 combinatorial count overflowed or a0 = +inf */
+  CWC_TRAJ_CAPACITY = 4,      /* CREATE found no free compartment slot; not applied */
+  CWC_TRAJ_EVENT_LIMIT = 5,   /* max_events events applied                         */
+  CWC_TRAJ_BAD_INPUT = 6,     /* a rate <= 0 or not finite, a negative count, an
+                                 invalid slot image, or a grid that is not strictly
+                                 increasing from a value >= 0                      */
+  CWC_TRAJ_TIMEOUT = 7        /* the call's deadline passed                        */
+};
+
+/* Rule kinds of the restricted CWC language (Sec. 2.1 rule application:
+ * the left-hand side is matched against the content, or the wrap, of a
+ * compartment of the rule's label). */
+enum {
+  CWC_RULE_LOCAL = 0,        /* l: p X -> p' X                               */
+  CWC_RULE_PARENT_CHILD = 1, /* l: p X (w x | q Y)^l' -> p' X (w' x | q' Y)^l' */
+  CWC_RULE_CREATE = 2,       /* l: p X -> p' X (w' | q')^l'                  */
+  CWC_RULE_DISSOLVE = 3      /* l: p X (w x | q Y)^l' -> p' X x Y            */
+};
+
+/*
+ * Model description (host memory).
+ *   n_species S >= 1, n_labels L >= 1 (label 0 = the top level, whose single
+ *   compartment is slot 0, the root, without a wrap), n_rules M >= 1,
+ *   max_compartments C >= 1 (slots per trajectory, including the root).
+ *   kind[M], ctx_label[M] in [0, L), child_label[M] in [1, L) (ignored, and
+ *   conventionally -1, for LOCAL).
+ *   lhs[M][3][S]: multiplicities of the context (parent) content, child wrap
+ *   and child content patterns, each in {0, 1, 2}; rhs[M][3][S] >= 0 the
+ *   same for the right-hand side (<= 1000).  LOCAL uses row 0 only; CREATE
+ *   uses lhs row 0 and rhs rows 0..2 (rows 1, 2 = the new compartment's wrap
+ *   and content); DISSOLVE uses lhs rows 0..2 and rhs row 0.  At most four
+ *   species with a nonzero left-hand multiplicity per rule.
+ * Flat mass-action networks are L = 1, C = 1, all rules LOCAL on label 0.
+ */
+typedef struct {
+  int32_t n_species;
+  int32_t n_labels;
+  int32_t n_rules;
+  int32_t max_compartments;
+  const int32_t* kind;
+  const int32_t* ctx_label;
+  const int32_t* child_label;
+  const int32_t* lhs;
+  const int32_t* rhs;
+} cwc_model_desc;
+
+typedef struct cwc_model cwc_model;
+
+/*
+ * Validate a model, compile it (reactant lists, stoichiometry changes, the
+ * rule dependency graph and the propensity-tree paths each rule touches)
+ * and upload the tables to the current device.
+ * Errors: CWC_ERR_INVALID_ARG (NULL pointers, sizes or fields out of
+ * range), CWC_ERR_UNSUPPORTED (more than four reactant species in a rule,
+ * a model too large for one trajectory's state), CWC_ERR_CUDA.
+ * On success *out owns device memory until cwc_model_destroy.
+ */
+cwc_status cwc_model_create(const cwc_model_desc* desc, cwc_model** out);
+
+/* Free a model (NULL is ignored).  Work using it must have completed. */
+void cwc_model_destroy(cwc_model* model);
+
+/*
+ * Number of observables O per grid point: S for a flat model (the root
+ * content); otherwise L*S content totals by label, (L-1)*S wrap totals for
+ * labels 1..L-1, and L alive-compartment counts, each an int64 sum
+ * saturated at INT32_MAX.  Returns -1 for NULL.
+ */
+int32_t cwc_model_num_observables(const cwc_model* model);
+
+/* Layout choices for cwc_sim_args.layout. */
+enum {
+  CWC_LAYOUT_AUTO = 0,        /* the autotuner's cached choice for this shape   */
+  CWC_LAYOUT_STATIC = 1,      /* one thread per trajectory; a lane that finishes
+                                 takes trajectory q + (threads in the grid)     */
+  CWC_LAYOUT_QUEUE = 2        /* persistent grid; a lane that finishes takes the
+                                 next trajectory from a device work queue       */
+};
+
+/*
+ * Arguments of one simulation call: P sweep points x R replicas, trajectory
+ * q = p*R + r (p < P, r < R), sampled at G grid points.  The random stream
+ * of trajectory q is keyed by (replica_offset + r, p), so splitting a batch's
+ * replicas into shards with matching offsets reproduces it exactly.
+ *
+ *   rates   device double [P][M]    stochastic constants k_j > 0 per point
+ *   init    device int32 [Pi][S] (flat) or [Pi][C][3+2S] slot image per
+ *           point (Pi = 1: shared by all points): row c = (alive, label,
+ *           parent, wrap[S], content[S]); slot 0 must be the root
+ *   grid    device double [G], 0 <= grid[0] < grid[1] < ...; T = grid[G-1]
+ *   seed    Philox4x32-10 key (low word, high word)
+ *   max_events  per trajectory, 0 .. 2^32-1
+ *
+ * Outputs (device, each may be NULL):
+ *   states        int32 [P][R][G][O]   observables at each grid point
+ *   sums          int64 [P][G][O]      exact sums over replicas (zeroed by
+ *                                      the call before accumulation)
+ *   means         double [P][G][O]     sums / R (one IEEE division)
+ *   traj_status   int32 [P][R]         CWC_TRAJ_* codes
+ *   traj_events   int64 [P][R]         applied events
+ *   traj_hash     uint64 [P][R]        FNV-1a-64 over (rule, slot) of every
+ *                                      applied event, little-endian uint32s
+ *   traj_final_t  double [P][R]        time of the last applied event
+ *   log_rule/log_slot int32, log_t double [P][R][log_cap]: the first log_cap
+ *                                      events of each trajectory
+ *
+ *   layout, block_threads (0 = automatic), deadline_ns (0 = none: a
+ *   trajectory still running when this many nanoseconds of device time have
+ *   passed since the launch stops with CWC_TRAJ_TIMEOUT).
+ *   workspace / workspace_bytes: caller-owned device scratch of at least
+ *   cwc_simulate_workspace_size() bytes, 256-byte aligned (NULL if that size
+ *   is 0).
+ *
+ * Semantics of each trajectory (the written specification this library and
+ * its test oracle both follow; Sec. 2.2 steps 1-2 with Sec. 5.1's order):
+ * per event n, Philox4x32-10 with counter (n, 0, r, p) gives u_tau, u_sel
+ * (52-bit uniforms (k + 1/2) 2^-52); a0 is the 32-lane blocked FP64 tree
+ * sum of a_j = k_j * H_j (H_j the int64 number of reactant combinations
+ * summed over the rule's contexts); tau = -log(u_tau) / a0 with a fixed
+ * atanh-series logarithm; grid points before t + tau record the current
+ * term; an event past T is discarded; rule j is chosen by guarded tree
+ * descent of u_sel * a0; its context by the integer draw
+ * floor(W * H_j / 2^64), W from counter (n, 1, r, p); then the rewrite.
+ */
+typedef struct {
+  int32_t P, R, G, Pi;
+  uint32_t replica_offset;   /* replica r of this call is replica r + replica_offset of
+                                the random streams (shards of one large batch) */
+  const double* rates;
+  const int32_t* init;
+  const double* grid;
+  uint64_t seed;
+  int64_t max_events;
+  int32_t* states;
+  int64_t* sums;
+  double* means;
+  int32_t* traj_status;
+  int64_t* traj_events;
+  uint64_t* traj_hash;
+  double* traj_final_t;
+  int32_t log_cap;
+  int32_t* log_rule;
+  int32_t* log_slot;
+  double* log_t;
+  int32_t layout;
+  int32_t block_threads;
+  int64_t deadline_ns;
+  void* workspace;
+  size_t workspace_bytes;
+} cwc_sim_args;
+
+/* Workspace bytes cwc_simulate needs for these arguments (0 if none). */
+cwc_status cwc_simulate_workspace_size(const cwc_model* model, const cwc_sim_args* args, size_t* bytes);
+
+/*
+ * Enqueue the simulation described by args on stream.
+ * Errors: CWC_ERR_INVALID_ARG (NULL model/args/rates/init/grid, P, R, G < 1,
+ * Pi not 1 or P, replica_offset + R > 2^32, max_events out of range,
+ * log_cap < 0 or a log buffer missing), CWC_ERR_WORKSPACE,
+ * CWC_ERR_UNSUPPORTED, CWC_ERR_CUDA.
+ */
+cwc_status cwc_simulate(const cwc_model* model, const cwc_sim_args* args, void* stream);
+
+/*
+ * Likelihood-ratio sensitivities of mean observables with respect to the
+ * rate constants, by replaying every trajectory's Philox stream (the same
+ * paths cwc_simulate produces for the same args; nothing is stored between
+ * the calls).  For a CTMC path the score of rule j up to time g is
+ * S_j(g) = N_j(g)/k_j - int_0^g H_j(X(s)) ds (a_j = k_j H_j); with the
+ * upstream gradient G = grad_means[p][g][o] of L = sum G * E[X_o(g)],
+ *   grad_rates[p][j] = (1/R) sum_r sum_g c_r(g) S_rj(g),
+ *   c_r(g) = sum_o G[p][g][o] (X_ro(g) - means[p][g][o]).
+ *
+ *   means, grad_means  device double [P][G][O]
+ *   grad_rates         device double [P][M]   (output)
+ *   partials           device double [P][R][M] per-trajectory terms
+ *                      (output if non-NULL, else kept in the workspace)
+ * The sum over r is a fixed pairwise tree, so results are identical from
+ * run to run.  Workspace: cwc_sensitivity_workspace_size().
+ * Errors as cwc_simulate, plus CWC_ERR_INVALID_ARG for missing
+ * means/grad_means/grad_rates.
+ */
+typedef struct {
+  const double* means;
+  const double* grad_means;
+  double* grad_rates;
+  double* partials;
+} cwc_sens_args;
+
+cwc_status cwc_sensitivity_workspace_size(const cwc_model* model, const cwc_sim_args* sim,
+                                          const cwc_sens_args* sens, size_t* bytes);
+cwc_status cwc_sensitivity(const cwc_model* model, const cwc_sim_args* sim, const cwc_sens_args* sens,
+                           void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cwc_last_error(void);
+
+/* Library version string. */
+const char* cwc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CWCGPU_H_ */

@@ -1,0 +1,413 @@
+// C ABI of the library (declared in include/cwcgpu.h): model validation and
+// compilation, argument checking, workspace layout and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cwc_internal.h"
+#include "cwcgpu.h"
+#include "ssa_device.cuh"
+
+namespace cwcgpu {
+cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queue, bool sens, int T,
+                        int blocks_per_sm_cap, cudaStream_t stream, int* used_blocks);
+size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens);
+int flat_table_bytes_host(int M, int n_deps);
+cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
+cudaError_t launch_reduce_partials(const double* partials, double* grad, int P, int R, int M, cudaStream_t st);
+}  // namespace cwcgpu
+
+using namespace cwcgpu;
+
+struct cwc_model {
+  int S = 0, L = 0, C = 0, M = 0;
+  bool flat = false;
+  int device = 0;
+  // flat compilation
+  int B = 1, MP = 32, n_deps = 0;
+  int32_t* d_tables = nullptr;  // [M][RULE_WORDS] followed by [n_deps]
+  std::vector<int32_t> h_tables;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cwc_status fail(cwc_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+cwc_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(CWC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+LogConstants make_log_constants() {
+  LogConstants lc;
+  std::memset(&lc, 0, sizeof(lc));
+  for (int k = 3; k <= 21; k += 2) lc.c[k] = 1.0 / (double)k;
+  const double LN2 = 0.6931471805599453;  // the double nearest ln 2
+  for (int e = -53; e <= 0; ++e) lc.e_ln2[e + 53] = (double)e * LN2;
+  return lc;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout: [header 256 B][sums P*G*O int64 if needed][partials Q*M double if needed]
+struct WsLayout {
+  size_t header = 0, sums = 0, partials = 0, total = 0;
+  bool need_header = false, need_sums = false, need_partials = false;
+};
+
+int chosen_layout(const cwc_sim_args* a) { return a->layout == CWC_LAYOUT_AUTO ? CWC_LAYOUT_QUEUE : a->layout; }
+
+WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool sens_partials_given) {
+  WsLayout w;
+  const int O = m->flat ? m->S : (m->L * m->S + (m->L - 1) * m->S + m->L);
+  w.need_header = chosen_layout(a) == CWC_LAYOUT_QUEUE || a->deadline_ns > 0;
+  w.need_sums = !sens && a->means != nullptr && a->sums == nullptr;
+  w.need_partials = sens && !sens_partials_given;
+  size_t off = 0;
+  if (w.need_header) {
+    w.header = off;
+    off += 256;
+  }
+  if (w.need_sums) {
+    w.sums = off;
+    off = align256(off + (size_t)a->P * a->G * O * sizeof(long long));
+  }
+  if (w.need_partials) {
+    w.partials = off;
+    off = align256(off + (size_t)a->P * a->R * m->M * sizeof(double));
+  }
+  w.total = off;
+  return w;
+}
+
+cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
+  if (m == nullptr || a == nullptr) return fail(CWC_ERR_INVALID_ARG, "model and args must not be NULL");
+  if (a->rates == nullptr || a->init == nullptr || a->grid == nullptr)
+    return fail(CWC_ERR_INVALID_ARG, "rates, init and grid must not be NULL");
+  if (a->P < 1 || a->R < 1 || a->G < 1) return fail(CWC_ERR_INVALID_ARG, "P, R and G must be >= 1");
+  if (a->Pi != 1 && a->Pi != a->P) return fail(CWC_ERR_INVALID_ARG, "Pi must be 1 or P");
+  if ((unsigned long long)a->replica_offset + (unsigned long long)a->R > 0x100000000ull)
+    return fail(CWC_ERR_INVALID_ARG, "replica_offset + R must be <= 2^32");
+  if (a->max_events < 0 || a->max_events > 0xFFFFFFFFll)
+    return fail(CWC_ERR_INVALID_ARG, "max_events must be in [0, 2^32-1]");
+  if (a->log_cap < 0) return fail(CWC_ERR_INVALID_ARG, "log_cap must be >= 0");
+  if (a->log_cap > 0 && a->log_rule == nullptr) return fail(CWC_ERR_INVALID_ARG, "log_cap > 0 needs log_rule");
+  if (a->layout < CWC_LAYOUT_AUTO || a->layout > CWC_LAYOUT_QUEUE) return fail(CWC_ERR_INVALID_ARG, "bad layout");
+  if (a->block_threads != 0 && (a->block_threads < 32 || a->block_threads > 256 || a->block_threads % 32 != 0))
+    return fail(CWC_ERR_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 256]");
+  if (a->deadline_ns < 0) return fail(CWC_ERR_INVALID_ARG, "deadline_ns must be >= 0");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != m->device) return fail(CWC_ERR_INVALID_ARG, "model was created on another device");
+  return CWC_OK;
+}
+
+FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
+  FlatParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.S = m->S;
+  prm.M = m->M;
+  prm.B = m->B;
+  prm.MP = m->MP;
+  prm.n_deps = m->n_deps;
+  prm.rules = m->d_tables;
+  prm.deps = m->d_tables + (size_t)m->M * RULE_WORDS;
+  prm.P = a->P;
+  prm.R = a->R;
+  prm.G = a->G;
+  prm.Pi = a->Pi;
+  prm.r_offset = a->replica_offset;
+  prm.Q = (long long)a->P * a->R;
+  prm.rates = a->rates;
+  prm.init = a->init;
+  prm.grid = a->grid;
+  prm.key0 = (uint32_t)a->seed;
+  prm.key1 = (uint32_t)(a->seed >> 32);
+  prm.max_events = a->max_events;
+  prm.deadline_ns = a->deadline_ns;
+  prm.smem_table_bytes = flat_table_bytes_host(m->M, m->n_deps);
+  return prm;
+}
+
+int pick_threads(const cwc_model* m, const cwc_sim_args* a, bool sens) {
+  if (a->block_threads > 0) return a->block_threads;
+  // largest of 128 / 64 / 32 threads whose block fits in shared memory twice per SM
+  FlatParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.S = m->S;
+  prm.M = m->M;
+  prm.B = m->B;
+  prm.MP = m->MP;
+  prm.smem_table_bytes = flat_table_bytes_host(m->M, m->n_deps);
+  for (int T : {128, 64, 32})
+    if (flat_smem_bytes(prm, T, sens) * 2 <= 220 * 1024) return T;
+  return 32;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cwc_last_error(void) { return g_last_error.c_str(); }
+
+const char* cwc_version(void) { return "cwcgpu 0.1 (sm_103a)"; }
+
+cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
+  g_last_error.clear();
+  if (d == nullptr || out == nullptr) return fail(CWC_ERR_INVALID_ARG, "desc and out must not be NULL");
+  *out = nullptr;
+  const int S = d->n_species, L = d->n_labels, M = d->n_rules, C = d->max_compartments;
+  if (S < 1 || S > 4096 || L < 1 || L > 64 || M < 1 || M > 65535 || C < 1 || C > 1024)
+    return fail(CWC_ERR_INVALID_ARG, "sizes out of range (1<=S<=4096, 1<=L<=64, 1<=M<=65535, 1<=C<=1024)");
+  if (!d->kind || !d->ctx_label || !d->child_label || !d->lhs || !d->rhs)
+    return fail(CWC_ERR_INVALID_ARG, "rule arrays must not be NULL");
+  for (int j = 0; j < M; ++j) {
+    const int k = d->kind[j];
+    if (k < CWC_RULE_LOCAL || k > CWC_RULE_DISSOLVE) return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": bad kind");
+    if (d->ctx_label[j] < 0 || d->ctx_label[j] >= L)
+      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": ctx_label out of range");
+    if (k != CWC_RULE_LOCAL && (d->child_label[j] < 1 || d->child_label[j] >= L))
+      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": child_label out of [1, L)");
+    const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
+    const int32_t* rhs = d->rhs + (size_t)j * 3 * S;
+    int factors = 0;
+    for (int i = 0; i < 3 * S; ++i) {
+      if (lhs[i] < 0 || lhs[i] > 2) return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": lhs entries must be 0, 1 or 2");
+      if (rhs[i] < 0 || rhs[i] > 1000) return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": rhs entries must be in [0, 1000]");
+      factors += lhs[i] != 0;
+    }
+    if (factors > MAX_REAC) return fail(CWC_ERR_UNSUPPORTED, "rule " + std::to_string(j) + ": more than 4 reactant species");
+    bool lhs_child = false, rhs_child = false;
+    for (int i = S; i < 3 * S; ++i) {
+      lhs_child |= lhs[i] != 0;
+      rhs_child |= rhs[i] != 0;
+    }
+    if (k == CWC_RULE_LOCAL && (lhs_child || rhs_child))
+      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": LOCAL rules use row 0 only");
+    if (k == CWC_RULE_CREATE && lhs_child)
+      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": CREATE matches the context content only");
+    if (k == CWC_RULE_DISSOLVE && rhs_child)
+      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": DISSOLVE writes the parent content only");
+  }
+  cwc_model* m = new cwc_model();
+  m->S = S;
+  m->L = L;
+  m->C = C;
+  m->M = M;
+  m->flat = (L == 1 && C == 1);
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  if (!m->flat) {
+    delete m;
+    return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
+  }
+  // ---- flat compilation ----
+  m->B = (M + 31) / 32;
+  m->MP = std::max(M, 32);
+  std::vector<std::vector<int>> reac(M), delta(M);
+  for (int j = 0; j < M; ++j) {
+    const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
+    const int32_t* rhs = d->rhs + (size_t)j * 3 * S;
+    for (int s = 0; s < S; ++s) {
+      if (lhs[s] > 0) reac[j].push_back(s);
+      if (rhs[s] != lhs[s]) delta[j].push_back(s);
+    }
+    if ((int)delta[j].size() > MAX_DELTA) {
+      delete m;
+      return fail(CWC_ERR_UNSUPPORTED, "rule " + std::to_string(j) + ": more than 8 species change");
+    }
+  }
+  // dependents of j: rules with a reactant species whose count j changes
+  std::vector<std::vector<int>> deps(M);
+  std::vector<std::vector<int>> readers(S);
+  for (int i = 0; i < M; ++i)
+    for (int s : reac[i]) readers[s].push_back(i);
+  for (int j = 0; j < M; ++j) {
+    std::vector<char> mark(M, 0);
+    for (int s : delta[j])
+      for (int i : readers[s]) mark[i] = 1;
+    for (int i = 0; i < M; ++i)
+      if (mark[i]) deps[j].push_back(i);
+  }
+  int n_deps = 0;
+  for (int j = 0; j < M; ++j) n_deps += (int)deps[j].size();
+  m->n_deps = n_deps;
+  std::vector<int32_t>& tb = m->h_tables;
+  tb.assign((size_t)M * RULE_WORDS + n_deps, 0);
+  int off = 0;
+  for (int j = 0; j < M; ++j) {
+    int32_t* rec = tb.data() + (size_t)j * RULE_WORDS;
+    const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
+    const int32_t* rhs = d->rhs + (size_t)j * 3 * S;
+    rec[R_NREAC] = (int32_t)reac[j].size();
+    for (size_t a = 0; a < reac[j].size(); ++a) rec[R_REAC + a] = reac[j][a] | (lhs[reac[j][a]] << 16);
+    rec[R_NDELTA] = (int32_t)delta[j].size();
+    for (size_t a = 0; a < delta[j].size(); ++a) {
+      const int s = delta[j][a];
+      const int dv = rhs[s] - lhs[s];
+      rec[R_DELTA + a] = (int32_t)((uint32_t)s | ((uint32_t)(dv & 0xffff) << 16));
+    }
+    rec[R_DEPOFF] = off;
+    rec[R_DEPCNT] = (int32_t)deps[j].size();
+    uint32_t leafmask = 0, nodemask = 0;
+    for (int i : deps[j]) {
+      tb[(size_t)M * RULE_WORDS + off++] = i;
+      const int l = i / m->B;
+      leafmask |= 1u << l;
+      nodemask |= 1u << (l >> 1);
+      nodemask |= 1u << (16 + (l >> 2));
+      nodemask |= 1u << (24 + (l >> 3));
+      nodemask |= 1u << (28 + (l >> 4));
+      nodemask |= 1u << TREE_ROOT;
+    }
+    rec[R_LEAFMASK] = (int32_t)leafmask;
+    rec[R_NODEMASK] = (int32_t)nodemask;
+  }
+  // one trajectory's state must fit: 32 threads per block at least
+  {
+    FlatParams prm;
+    std::memset(&prm, 0, sizeof(prm));
+    prm.S = S;
+    prm.M = M;
+    prm.B = m->B;
+    prm.MP = m->MP;
+    prm.smem_table_bytes = flat_table_bytes_host(M, n_deps);
+    if (flat_smem_bytes(prm, 32, true) > 220 * 1024) {
+      delete m;
+      return fail(CWC_ERR_UNSUPPORTED, "model too large for one block of 32 trajectories in shared memory");
+    }
+  }
+  e = cudaMalloc(&m->d_tables, tb.size() * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "cudaMalloc(model tables)");
+  }
+  e = cudaMemcpy(m->d_tables, tb.data(), tb.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(m->d_tables);
+    delete m;
+    return cuda_fail(e, "cudaMemcpy(model tables)");
+  }
+  *out = m;
+  return CWC_OK;
+}
+
+void cwc_model_destroy(cwc_model* m) {
+  if (m == nullptr) return;
+  if (m->d_tables) cudaFree(m->d_tables);
+  delete m;
+}
+
+int32_t cwc_model_num_observables(const cwc_model* m) {
+  if (m == nullptr) return -1;
+  if (m->flat) return m->S;
+  return m->L * m->S + (m->L - 1) * m->S + m->L;
+}
+
+cwc_status cwc_simulate_workspace_size(const cwc_model* m, const cwc_sim_args* a, size_t* bytes) {
+  g_last_error.clear();
+  if (bytes == nullptr) return fail(CWC_ERR_INVALID_ARG, "bytes must not be NULL");
+  cwc_status st = check_sim_args(m, a);
+  if (st != CWC_OK) return st;
+  *bytes = ws_layout(m, a, false, false).total;
+  return CWC_OK;
+}
+
+cwc_status cwc_sensitivity_workspace_size(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* s,
+                                          size_t* bytes) {
+  g_last_error.clear();
+  if (bytes == nullptr || s == nullptr) return fail(CWC_ERR_INVALID_ARG, "sens and bytes must not be NULL");
+  cwc_status st = check_sim_args(m, a);
+  if (st != CWC_OK) return st;
+  *bytes = ws_layout(m, a, true, s->partials != nullptr).total;
+  return CWC_OK;
+}
+
+static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* sens, cudaStream_t st) {
+  const bool is_sens = sens != nullptr;
+  const WsLayout w = ws_layout(m, a, is_sens, is_sens && sens->partials != nullptr);
+  if (w.total > 0) {
+    if (a->workspace == nullptr || a->workspace_bytes < w.total)
+      return fail(CWC_ERR_WORKSPACE, "workspace of " + std::to_string(w.total) + " bytes required");
+    if ((reinterpret_cast<uintptr_t>(a->workspace) & 255) != 0)
+      return fail(CWC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  }
+  unsigned char* ws = static_cast<unsigned char*>(a->workspace);
+  FlatParams prm = make_flat_params(m, a);
+  const int O = m->S;
+  cudaError_t e;
+  if (w.need_header) {
+    prm.ws = reinterpret_cast<WorkspaceHeader*>(ws + w.header);
+    e = cudaMemsetAsync(prm.ws, 0, sizeof(WorkspaceHeader), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
+  }
+  if (!is_sens) {
+    prm.states = a->states;
+    unsigned long long* sums = reinterpret_cast<unsigned long long*>(a->sums);
+    if (w.need_sums) sums = reinterpret_cast<unsigned long long*>(ws + w.sums);
+    prm.sums = sums;
+    if (sums != nullptr) {
+      e = cudaMemsetAsync(sums, 0, (size_t)a->P * a->G * O * sizeof(long long), st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sums)");
+    }
+    prm.traj_status = a->traj_status;
+    prm.traj_events = reinterpret_cast<long long*>(a->traj_events);
+    prm.traj_hash = reinterpret_cast<unsigned long long*>(a->traj_hash);
+    prm.traj_final_t = a->traj_final_t;
+    prm.log_cap = a->log_cap;
+    prm.log_rule = a->log_rule;
+    prm.log_slot = a->log_slot;
+    prm.log_t = a->log_t;
+  } else {
+    prm.means = sens->means;
+    prm.grad_means = sens->grad_means;
+    prm.partials = sens->partials != nullptr ? sens->partials : reinterpret_cast<double*>(ws + w.partials);
+  }
+  const LogConstants lc = make_log_constants();
+  const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
+  const int T = pick_threads(m, a, is_sens);
+  e = launch_flat(prm, lc, queue, is_sens, T, 0, st, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "flat SSA kernel launch");
+  if (!is_sens && a->means != nullptr) {
+    e = launch_means(prm.sums, a->means, (long long)a->P * a->G * O, a->R, st);
+    if (e != cudaSuccess) return cuda_fail(e, "means kernel launch");
+  }
+  if (is_sens) {
+    e = launch_reduce_partials(prm.partials, sens->grad_rates, a->P, a->R, m->M, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce kernel launch");
+  }
+  return CWC_OK;
+}
+
+cwc_status cwc_simulate(const cwc_model* m, const cwc_sim_args* a, void* stream) {
+  g_last_error.clear();
+  cwc_status st = check_sim_args(m, a);
+  if (st != CWC_OK) return st;
+  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
+  return run_flat(m, a, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+cwc_status cwc_sensitivity(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* s, void* stream) {
+  g_last_error.clear();
+  cwc_status st = check_sim_args(m, a);
+  if (st != CWC_OK) return st;
+  if (s == nullptr || s->means == nullptr || s->grad_means == nullptr || s->grad_rates == nullptr)
+    return fail(CWC_ERR_INVALID_ARG, "means, grad_means and grad_rates must not be NULL");
+  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
+  return run_flat(m, a, s, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal layout shared by the host-side model compiler and the kernels of
+// the CUDA library.  Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace cwcgpu {
+
+// Per-rule record of a compiled flat model, RULE_WORDS int32 words:
+//   [0]      number of reactant species (<= MAX_REAC)
+//   [1..4]   reactant: species (low 16 bits) | multiplicity nu (high 16 bits)
+//   [5]      number of species whose count changes (<= MAX_DELTA)
+//   [6..13]  change: species (low 16 bits) | signed delta (high 16 bits)
+//   [14]     offset of the rule's dependents in the dependency array
+//   [15]     number of dependents (rules whose propensity reads a species
+//            this rule changes), ascending
+//   [16]     bit mask of the 32 tree leaves the dependents live in
+//   [17]     bit mask of the 31 internal tree nodes above those leaves
+//   [18..19] unused
+constexpr int RULE_WORDS = 20;
+constexpr int MAX_REAC = 4;
+constexpr int MAX_DELTA = 8;
+constexpr int R_NREAC = 0, R_REAC = 1, R_NDELTA = 5, R_DELTA = 6, R_DEPOFF = 14, R_DEPCNT = 15,
+              R_LEAFMASK = 16, R_NODEMASK = 17;
+
+// Internal nodes of the 32-lane tree: level 1 nodes 0..15 (children: leaves
+// 2n, 2n+1), level 2 nodes 16..23, level 3 24..27, level 4 28..29, root 30.
+// For n >= 16 the children are nodes 2n-32 and 2n-31.
+constexpr int TREE_NODES = 31;
+constexpr int TREE_ROOT = 30;
+
+// Trajectory status codes (same values as CWC_TRAJ_* in the C header).
+enum : int32_t {
+  TS_OK = 0, TS_ABSORBED = 1, TS_INT_OVERFLOW = 2, TS_PROP_OVERFLOW = 3, TS_CAPACITY = 4,
+  TS_EVENT_LIMIT = 5, TS_BAD_INPUT = 6, TS_TIMEOUT = 7
+};
+
+// Workspace header (first 256 bytes when used): work-queue ticket and the
+// launch timestamp for deadlines.
+struct WorkspaceHeader {
+  unsigned long long queue_next;
+  unsigned long long t_start_ns;
+  unsigned long long pad[30];
+};
+static_assert(sizeof(WorkspaceHeader) == 256, "workspace header size");
+
+// Everything one flat-model launch needs.
+struct FlatParams {
+  // compiled model
+  int S, M, B, MP;          // species, rules, leaf block size, rows of prop (max(M, 32))
+  int n_deps;
+  const int32_t* rules;     // [M][RULE_WORDS]
+  const int32_t* deps;      // [n_deps]
+  // batch
+  int P, R, G, Pi;
+  uint32_t r_offset;        // replica index offset of the random streams
+  long long Q;              // P * R
+  const double* rates;      // [P][M]
+  const int32_t* init;      // [Pi][S]
+  const double* grid;       // [G]
+  uint32_t key0, key1;
+  long long max_events;
+  // outputs
+  int32_t* states;                 // [Q][G][S]
+  unsigned long long* sums;        // [P][G][S]
+  int32_t* traj_status;
+  long long* traj_events;
+  unsigned long long* traj_hash;
+  double* traj_final_t;
+  int log_cap;
+  int32_t* log_rule;
+  int32_t* log_slot;
+  double* log_t;
+  // score replay
+  const double* means;             // [P][G][S]
+  const double* grad_means;        // [P][G][S]
+  double* partials;                // [Q][M]
+  // scheduling
+  WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)
+  long long deadline_ns;
+  int smem_table_bytes;            // bytes of the shared-memory table region
+};
+
+}  // namespace cwcgpu

@@ -1,0 +1,474 @@
+// Flat mass-action networks (one compartment): Gillespie's direct method
+// (Sec. 2.2) run by one thread per trajectory over replicas x sweep points
+// (Sec. 5.2).
+//
+// Layout.  A block of T threads holds, in shared memory, the compiled rule
+// tables (shared by the block) and per-thread arrays stored [index][thread],
+// so that every thread reading "its" element i of an array touches bank
+// (2*tid) mod 32 whatever i is: data-dependent indices never conflict.
+//   prop[MP][T]  double  a_j = k_j * H_j (rows M..31 stay +0 when M < 32)
+//   leaf[32][T]  double  leaf sums of the 32-lane blocked tree (B > 1 only;
+//                        for B = 1 the leaves are prop rows 0..31)
+//   node[31][T]  double  internal tree nodes, root = node[30] = a0
+//   cnt[S][T]    int32   species counts
+// plus, for the score replay, Hd/I/tl/partial [M][T] doubles and N [M][T].
+//
+// Per event the thread: draws Philox(n, 0, r, p); computes tau with the
+// fixed FP64 logarithm and one IEEE division; records grid points passed;
+// descends the tree (integer compares of non-negative doubles, one FP64
+// subtraction per level); applies the stoichiometry change; recomputes the
+// propensities of the rule's dependents (Gibson-Bruck dependency graph) and
+// only the leaves and internal nodes above them.  a0 is always the tree root,
+// never a running sum, so the values equal a full rebuild bit for bit.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "cwc_internal.h"
+#include "ssa_device.cuh"
+
+namespace cwcgpu {
+
+__device__ __forceinline__ long long grab_next(WorkspaceHeader* ws) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(&ws->queue_next, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return (long long)(base + (unsigned long long)__popc(mask & ((1u << lane) - 1u)));
+}
+
+// Shared-memory table region: rules, dependents, e*ln2 table (doubles last,
+// 8-byte aligned).  Must match flat_table_bytes() on the host.
+__host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
+  int words = M * RULE_WORDS + n_deps;
+  int bytes = ((words * 4 + 15) / 16) * 16;
+  return bytes + 54 * 8;
+}
+
+__host__ __device__ inline int flat_thread_bytes(int S, int M, int B, int MP, bool sens) {
+  int doubles = MP + (B > 1 ? 32 : 0) + TREE_NODES + (sens ? 4 * M : 0);
+  int ints = S + (sens ? M : 0);
+  return doubles * 8 + ints * 4;
+}
+
+template <bool kQueue, bool kSens>
+__global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ FlatParams prm,
+                                                       const __grid_constant__ LogConstants lc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x;
+  const int tid = threadIdx.x;
+  const int S = prm.S, M = prm.M, B = prm.B, MP = prm.MP, G = prm.G;
+
+  int32_t* s_rules = reinterpret_cast<int32_t*>(smem);
+  int32_t* s_deps = s_rules + M * RULE_WORDS;
+  const int tbl_words = M * RULE_WORDS + prm.n_deps;
+  double* s_eln2 = reinterpret_cast<double*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
+  double* prop = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
+  double* leaf = prop + MP * T;
+  double* node = leaf + (B > 1 ? 32 * T : 0);
+  double* Hd = node + TREE_NODES * T;    // score replay only
+  double* Iac = Hd + M * T;
+  double* tl = Iac + M * T;
+  double* part = tl + M * T;
+  int32_t* cnt = reinterpret_cast<int32_t*>(kSens ? part + M * T : node + TREE_NODES * T);
+  int32_t* Nf = cnt + S * T;
+
+#define PROP(i) prop[(i) * T + tid]
+#define LEAFV(l) (B > 1 ? leaf[(l) * T + tid] : prop[(l) * T + tid])
+#define NODE(i) node[(i) * T + tid]
+#define CNT(s) cnt[(s) * T + tid]
+
+  for (int i = tid; i < tbl_words; i += T) s_rules[i] = prm.rules[i];   // rules then deps, contiguous
+  for (int i = tid; i < 54; i += T) s_eln2[i] = lc.e_ln2[i];
+  // grid check, once per block: finite, grid[0] >= 0, strictly increasing
+  bool bad_grid = false;
+  for (int g = tid; g < G; g += T) {
+    const double v = prm.grid[g];
+    if ((dbits(v) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) bad_grid = true;
+    if (g == 0 && !(v >= 0.0)) bad_grid = true;
+    if (g > 0 && !(v > prm.grid[g - 1])) bad_grid = true;
+  }
+  __shared__ unsigned long long s_deadline;
+  if (tid == 0) {
+    unsigned long long dl = ~0ull;
+    if (prm.deadline_ns > 0) {
+      const unsigned long long now = globaltimer_ns();
+      unsigned long long start = now;
+      if (prm.ws != nullptr) {
+        const unsigned long long prev = atomicCAS(&prm.ws->t_start_ns, 0ull, now);
+        start = prev == 0ull ? now : prev;
+      }
+      dl = start + (unsigned long long)prm.deadline_ns;
+    }
+    s_deadline = dl;
+  }
+  bad_grid = __syncthreads_or(bad_grid);
+  const unsigned long long deadline = s_deadline;
+  const long long T_bits = dbits(prm.grid[G - 1]);
+  const bool vec_states = (S % 4 == 0) && ((reinterpret_cast<uintptr_t>(prm.states) & 15) == 0);
+
+  // ---- trajectory state (registers) ----
+  long long q = 0;
+  int p = 0, r = 0;
+  const double* kp = nullptr;
+  double t = 0.0;
+  unsigned int n = 0;
+  int gi = 0;
+  long long gbits = 0;
+  unsigned long long h = FNV_OFFSET;
+  bool ovf = false;
+  int status = TS_OK;
+  const long long Q = prm.Q;
+  const long long qstride = (long long)gridDim.x * T;
+  bool first = true;
+
+  // observables of the current term at grid point g
+  auto record = [&](int g) {
+    if (prm.states != nullptr) {
+      int32_t* dst = prm.states + ((size_t)q * G + g) * S;
+      if (vec_states) {
+        for (int s = 0; s < S; s += 4)
+          *reinterpret_cast<int4*>(dst + s) = make_int4(CNT(s), CNT(s + 1), CNT(s + 2), CNT(s + 3));
+      } else {
+        for (int s = 0; s < S; ++s) dst[s] = CNT(s);
+      }
+    }
+    if (prm.sums != nullptr) {
+      unsigned long long* dst = prm.sums + ((size_t)p * G + g) * S;
+      for (int s = 0; s < S; ++s) atomicAdd(dst + s, (unsigned long long)(long long)CNT(s));
+    }
+    if (kSens) {
+      const double* gm = prm.grad_means + ((size_t)p * G + g) * S;
+      const double* mm = prm.means + ((size_t)p * G + g) * S;
+      double c = 0.0;
+      for (int o = 0; o < S; ++o)
+        c = __dadd_rn(c, __dmul_rn(gm[o], __dadd_rn((double)CNT(o), -mm[o])));
+      const double gt = prm.grid[g];
+      for (int i = 0; i < M; ++i) {
+        const double Ig = __dadd_rn(Iac[i * T + tid], __dmul_rn(Hd[i * T + tid], __dadd_rn(gt, -tl[i * T + tid])));
+        const double Si = __dadd_rn(__ddiv_rn((double)Nf[i * T + tid], kp[i]), -Ig);
+        part[i * T + tid] = __dadd_rn(part[i * T + tid], __dmul_rn(c, Si));
+      }
+    }
+  };
+
+  auto fill = [&]() {
+    for (; gi < G; ++gi) record(gi);
+  };
+
+  // H_i of rule i at the current counts (int64 with overflow flag)
+  auto count_h = [&](int i) -> unsigned long long {
+    const int32_t* rec = s_rules + i * RULE_WORDS;
+    const int nr = rec[R_NREAC];
+    unsigned long long hh = 1ull;
+    for (int a = 0; a < nr; ++a) {
+      const int v = rec[R_REAC + a];
+      hh = mul_checked(hh, binom12(CNT(v & 0xffff), v >> 16), &ovf);
+    }
+    return hh;
+  };
+
+  auto finalize = [&]() {
+    if (prm.traj_status) prm.traj_status[q] = status;
+    if (prm.traj_events) prm.traj_events[q] = (long long)n;
+    if (prm.traj_hash) prm.traj_hash[q] = h;
+    if (prm.traj_final_t) prm.traj_final_t[q] = t;
+    if (kSens) {
+      for (int i = 0; i < M; ++i) prm.partials[(size_t)q * M + i] = part[i * T + tid];
+    }
+  };
+
+  // set up trajectory q; returns true if it ends immediately (bad input)
+  auto start = [&]() -> bool {
+    p = (int)(q / prm.R);
+    r = (int)(q - (long long)p * prm.R);
+    kp = prm.rates + (size_t)p * M;
+    t = 0.0;
+    n = 0u;
+    gi = 0;
+    gbits = dbits(prm.grid[0]);
+    h = FNV_OFFSET;
+    ovf = false;
+    status = TS_OK;
+    bool bad = bad_grid;
+    for (int j = 0; j < M; ++j) {
+      const long long kb = dbits(kp[j]);
+      if (!(kb > 0 && kb < 0x7FF0000000000000ll)) bad = true;
+    }
+    const int32_t* x0 = prm.init + (size_t)(prm.Pi == 1 ? 0 : p) * S;
+    for (int s = 0; s < S; ++s) {
+      const int v = x0[s];
+      if (v < 0) bad = true;
+      CNT(s) = v;
+    }
+    if (kSens) {
+      for (int i = 0; i < M; ++i) part[i * T + tid] = 0.0;
+    }
+    if (bad) {
+      status = TS_BAD_INPUT;
+      if (prm.states != nullptr) {
+        int32_t* dst = prm.states + (size_t)q * G * S;
+        for (long long e = 0; e < (long long)G * S; ++e) dst[e] = 0;
+      }
+      return true;
+    }
+    for (int i = 0; i < M; ++i) {
+      const unsigned long long hh = count_h(i);
+      PROP(i) = __dmul_rn(kp[i], __ll2double_rn((long long)hh));
+      if (kSens) {
+        Hd[i * T + tid] = __ll2double_rn((long long)hh);
+        Iac[i * T + tid] = 0.0;
+        tl[i * T + tid] = 0.0;
+        Nf[i * T + tid] = 0;
+      }
+    }
+    for (int i = M; i < MP; ++i) PROP(i) = 0.0;
+    if (B > 1) {
+      for (int l = 0; l < 32; ++l) {
+        const int j0 = l * B, j1 = min(j0 + B, M);
+        double s = 0.0;
+        for (int j = j0; j < j1; ++j) s = __dadd_rn(s, PROP(j));
+        leaf[l * T + tid] = s;
+      }
+    }
+    for (int nd = 0; nd < TREE_NODES; ++nd) {
+      const double a = nd < 16 ? LEAFV(2 * nd) : NODE(2 * nd - 32);
+      const double b = nd < 16 ? LEAFV(2 * nd + 1) : NODE(2 * nd - 31);
+      NODE(nd) = __dadd_rn(a, b);
+    }
+    return false;
+  };
+
+  // one event (or the end of the trajectory); returns true when it ended
+  auto step = [&]() -> bool {
+    if (ovf) {
+      status = TS_PROP_OVERFLOW;
+      if (kSens)
+        for (int i = 0; i < M; ++i) Hd[i * T + tid] = 0.0;
+      fill();
+      return true;
+    }
+    if ((long long)n == prm.max_events) {
+      status = TS_EVENT_LIMIT;
+      fill();
+      return true;
+    }
+    const double a0 = NODE(TREE_ROOT);
+    const long long a0b = dbits(a0);
+    if (a0b == 0) {
+      status = TS_ABSORBED;
+      fill();
+      return true;
+    }
+    if (a0b >= 0x7FF0000000000000ll) {
+      status = TS_PROP_OVERFLOW;
+      if (kSens)
+        for (int i = 0; i < M; ++i) Hd[i * T + tid] = 0.0;
+      fill();
+      return true;
+    }
+    if ((n & 1023u) == 0u && deadline != ~0ull && globaltimer_ns() > deadline) {
+      status = TS_TIMEOUT;
+      fill();
+      return true;
+    }
+    const uint4 w = philox4x32_10(make_uint4(n, 0u, (uint32_t)r + prm.r_offset, (uint32_t)p), prm.key0, prm.key1);
+    const double u_tau = uniform52(w.x, w.y);
+    const double u_sel = uniform52(w.z, w.w);
+    const double tau = __ddiv_rn(-log_fixed(u_tau, lc.c, s_eln2), a0);
+    const double tn = __dadd_rn(t, tau);
+    const long long tnb = dbits(tn);
+    while (gi < G && gbits < tnb) {
+      record(gi);
+      ++gi;
+      if (gi < G) gbits = dbits(prm.grid[gi]);
+    }
+    if (tnb > T_bits) {
+      status = TS_OK;
+      return true;
+    }
+    // rule selection: guarded descent of x = u_sel * a0
+    double x = __dmul_rn(u_sel, a0);
+    int nd = TREE_ROOT;
+#pragma unroll
+    for (int lvl = 5; lvl >= 2; --lvl) {
+      const double L = NODE(2 * nd - 32);
+      const double Rv = NODE(2 * nd - 31);
+      const bool left = dbits(x) < dbits(L) || dbits(Rv) == 0;
+      const double xr = __dadd_rn(x, -L);
+      x = left ? x : xr;
+      nd = left ? 2 * nd - 32 : 2 * nd - 31;
+    }
+    int l;
+    {
+      const double L = LEAFV(2 * nd);
+      const double Rv = LEAFV(2 * nd + 1);
+      const bool left = dbits(x) < dbits(L) || dbits(Rv) == 0;
+      const double xr = __dadd_rn(x, -L);
+      x = left ? x : xr;
+      l = left ? 2 * nd : 2 * nd + 1;
+    }
+    int j;
+    if (B == 1) {
+      j = l;
+    } else {
+      const int j0 = l * B, j1 = min(j0 + B, M);
+      int last = -1;
+      j = -1;
+      double s = 0.0;
+      for (int jj = j0; jj < j1; ++jj) {
+        const double a = PROP(jj);
+        if (dbits(a) > 0) {
+          s = last < 0 ? a : __dadd_rn(s, a);
+          last = jj;
+          if (dbits(x) < dbits(s)) {
+            j = jj;
+            break;
+          }
+        }
+      }
+      if (j < 0) j = last;
+    }
+    // The guarded descent always ends on a positive entry because every node
+    // equals the sum of its children; the clamp only keeps indices in range.
+    j = min(max(j, 0), M - 1);
+    // apply the stoichiometry change (checked first: nothing changes on overflow)
+    const int32_t* rec = s_rules + j * RULE_WORDS;
+    const int nd_ = rec[R_NDELTA];
+    for (int d = 0; d < nd_; ++d) {
+      const int v = rec[R_DELTA + d];
+      const int dv = v >> 16;
+      if (dv > 0 && CNT(v & 0xffff) > 0x7FFFFFFF - dv) {
+        status = TS_INT_OVERFLOW;
+        fill();
+        return true;
+      }
+    }
+    for (int d = 0; d < nd_; ++d) {
+      const int v = rec[R_DELTA + d];
+      CNT(v & 0xffff) += v >> 16;
+    }
+    if (kSens) Nf[j * T + tid] += 1;
+    // dependents: new propensities
+    const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
+    for (int e = 0; e < dcnt; ++e) {
+      const int i = s_deps[doff + e];
+      const unsigned long long hh = count_h(i);
+      const double hd = __ll2double_rn((long long)hh);
+      PROP(i) = __dmul_rn(kp[i], hd);
+      if (kSens) {
+        Iac[i * T + tid] = __dadd_rn(Iac[i * T + tid], __dmul_rn(Hd[i * T + tid], __dadd_rn(tn, -tl[i * T + tid])));
+        tl[i * T + tid] = tn;
+        Hd[i * T + tid] = hd;
+      }
+    }
+    if (B > 1) {
+      unsigned lm = (unsigned)rec[R_LEAFMASK];
+      while (lm) {
+        const int ll = __ffs(lm) - 1;
+        lm &= lm - 1u;
+        const int j0 = ll * B, j1 = min(j0 + B, M);
+        double s = PROP(j0);
+        for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, PROP(jj));
+        leaf[ll * T + tid] = s;
+      }
+    }
+    unsigned nm = (unsigned)rec[R_NODEMASK];
+    while (nm) {
+      const int k = __ffs(nm) - 1;
+      nm &= nm - 1u;
+      const double a = k < 16 ? LEAFV(2 * k) : NODE(2 * k - 32);
+      const double b = k < 16 ? LEAFV(2 * k + 1) : NODE(2 * k - 31);
+      NODE(k) = __dadd_rn(a, b);
+    }
+    if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
+      const size_t at = (size_t)q * prm.log_cap + n;
+      prm.log_rule[at] = j;
+      if (prm.log_slot) prm.log_slot[at] = 0;
+      if (prm.log_t) prm.log_t[at] = tn;
+    }
+    t = tn;
+    ++n;
+    h = fnv1a_event(h, (uint32_t)j, 0u);
+    return false;
+  };
+
+  bool need_new = true;
+  for (;;) {
+    if (need_new) {
+      if (kQueue) {
+        q = grab_next(prm.ws);
+      } else {
+        q = first ? (long long)blockIdx.x * T + tid : q + qstride;
+        first = false;
+      }
+      if (q >= Q) break;
+      if (start()) {
+        finalize();
+        continue;
+      }
+      need_new = false;
+    }
+    if (step()) {
+      finalize();
+      need_new = true;
+    }
+  }
+#undef PROP
+#undef LEAFV
+#undef NODE
+#undef CNT
+}
+
+// ---------------------------------------------------------------------------
+// Host launcher
+// ---------------------------------------------------------------------------
+
+template <bool kQueue, bool kSens>
+static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
+                            cudaStream_t stream, int* used_blocks) {
+  auto kern = flat_ssa_kernel<kQueue, kSens>;
+  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, prm.B, prm.MP, kSens);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  long long blocks;
+  if (kQueue) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (blocks_per_sm_cap > 0 && per_sm > blocks_per_sm_cap) per_sm = blocks_per_sm_cap;
+    blocks = (long long)sms * per_sm;
+    const long long need = (prm.Q + T - 1) / T;
+    if (blocks > need) blocks = need;
+  } else {
+    blocks = (prm.Q + T - 1) / T;
+    if (blocks > 0x7FFFFFFFll) blocks = 0x7FFFFFFFll;
+  }
+  if (blocks < 1) blocks = 1;
+  if (used_blocks) *used_blocks = (int)blocks;
+  kern<<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  return cudaGetLastError();
+}
+
+size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens) {
+  return (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, prm.B, prm.MP, sens);
+}
+
+int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps); }
+
+cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queue, bool sens, int T,
+                        int blocks_per_sm_cap, cudaStream_t stream, int* used_blocks) {
+  if (queue) {
+    return sens ? launch_t<true, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks)
+                : launch_t<true, false>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
+  }
+  return sens ? launch_t<false, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks)
+              : launch_t<false, false>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
+}
+
+}  // namespace cwcgpu

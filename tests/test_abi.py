@@ -1,0 +1,104 @@
+"""The C ABI: the library builds for sm_103a, loads, exports every symbol the
+headers declare, and rejects bad arguments on the host (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+from paper_1010_2438_gb300 import capi
+from paper_1010_2438_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(cwc_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not capi.lib_exists():
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc not available to build the library")
+        from paper_1010_2438_gb300 import build
+        build.build()
+    return capi.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("cwc_model_create", "cwc_model_destroy", "cwc_simulate", "cwc_sensitivity", "cwc_last_error"):
+        assert n in names
+    assert set(capi.EXPORTED) <= names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in sorted(declared_functions()):
+        assert hasattr(lib, n), n
+
+
+def test_version(lib):
+    assert "sm_103a" in capi.cwc_version()
+
+
+def _desc(model):
+    m = model.contiguous()
+    keep = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs)
+    d = capi.cwc_model_desc(m.n_species, m.n_labels, m.n_rules, m.max_compartments,
+                            *(a.ctypes.data for a in keep))
+    return d, keep
+
+
+def test_model_validation_on_host(lib):
+    out = ctypes.c_void_p()
+    assert lib.cwc_model_create(None, ctypes.byref(out)) == capi.CWC_ERR_INVALID_ARG
+    assert "NULL" in capi.cwc_last_error()
+    base = W.flat8x12(R=1).model
+    cases = []
+    m = base.contiguous()
+    bad = W.Model(m.n_species, m.n_labels, m.max_compartments, m.kind.copy(), m.ctx_label, m.child_label,
+                  m.lhs, m.rhs)
+    bad.kind[0] = 9
+    cases.append((bad, capi.CWC_ERR_INVALID_ARG, "kind"))
+    bad = W.Model(m.n_species, m.n_labels, m.max_compartments, m.kind, m.ctx_label, m.child_label,
+                  m.lhs.copy(), m.rhs)
+    bad.lhs[0, 0, 0] = 3
+    cases.append((bad, capi.CWC_ERR_INVALID_ARG, "lhs"))
+    bad = W.Model(m.n_species, m.n_labels, m.max_compartments, m.kind, m.ctx_label, m.child_label,
+                  m.lhs.copy(), m.rhs)
+    bad.lhs[0, 0, :5] = 1
+    cases.append((bad, capi.CWC_ERR_UNSUPPORTED, "4 reactant"))
+    bad = W.Model(m.n_species, m.n_labels, m.max_compartments, m.kind, m.ctx_label, m.child_label,
+                  m.lhs, m.rhs.copy())
+    bad.rhs[0, 1, 0] = 1
+    cases.append((bad, capi.CWC_ERR_INVALID_ARG, "LOCAL"))
+    bad = W.Model(m.n_species, 1, 1, np.full(m.n_rules, 1, np.int32), m.ctx_label, m.child_label, m.lhs, m.rhs)
+    cases.append((bad, capi.CWC_ERR_INVALID_ARG, "child_label"))
+    bad = W.Model(0, 1, 1, m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs)
+    cases.append((bad, capi.CWC_ERR_INVALID_ARG, "sizes"))
+    for model, code, text in cases:
+        d, keep = _desc(model)
+        rc = lib.cwc_model_create(ctypes.byref(d), ctypes.byref(out))
+        assert rc == code, (rc, capi.cwc_last_error())
+        assert text in capi.cwc_last_error()
+        assert out.value is None
+
+
+def test_simulate_argument_checks_on_host(lib):
+    args = capi.cwc_sim_args()
+    assert lib.cwc_simulate(None, ctypes.byref(args), None) == capi.CWC_ERR_INVALID_ARG
+    assert lib.cwc_sensitivity(None, ctypes.byref(args), None, None) == capi.CWC_ERR_INVALID_ARG
+    n = ctypes.c_size_t()
+    assert lib.cwc_simulate_workspace_size(None, ctypes.byref(args), ctypes.byref(n)) == capi.CWC_ERR_INVALID_ARG
+    assert lib.cwc_model_num_observables(None) == -1
+    lib.cwc_model_destroy(None)  # NULL is ignored

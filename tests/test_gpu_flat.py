@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path against the CPU oracle, through the C ABI.
+
+Bit-exact on every integer and hash output and on the FP64 event times
+(both sides follow the same written specification); the score replay is
+compared within a tolerance derived from its FP64 rounding (see
+test_sensitivity_partials_match_oracle).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1010_2438_gb300 import api, capi
+from paper_1010_2438_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1010_2438_gb300 import build
+    build.build()
+    capi.lib()
+
+
+def gpu_run(batch, **kw):
+    cm = api.CompiledModel(batch.model)
+    rates, init, grid = api.device_inputs(batch)
+    res = api.simulate(cm, rates, init, grid, batch.R, batch.seed, batch.max_events, **kw)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in res.items() if not k.startswith("_")}
+    Q = batch.P * batch.R
+    for k in ("status", "events", "final_t"):
+        if k in out:
+            out[k] = out[k].reshape(Q)
+    if "hash" in out:
+        out["hash"] = out["hash"].reshape(Q).view(np.uint64)
+    if "states" in out:
+        out["states"] = out["states"].reshape(Q, batch.G, -1)
+    for k in ("log_rule", "log_slot", "log_t"):
+        if k in out:
+            out[k] = out[k].reshape(Q, -1)
+    return out
+
+
+def assert_same(g, o, keys=("status", "events", "hash", "final_t", "states")):
+    for k in keys:
+        a, b = g[k], o[k]
+        if k == "final_t":
+            assert np.array_equal(a.view(np.int64), b.view(np.int64)), k
+        else:
+            assert np.array_equal(a, b), (k, np.argwhere(a != b)[:5])
+
+
+# ----------------------------------------------------------------------------
+
+def _compile_curand_ref():
+    out_dir = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    so = os.path.join(out_dir, "curand_philox_ref.so")
+    src = os.path.join(ROOT, "tests", "cuda", "curand_philox_ref.cu")
+    if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared",
+                        "-Xcompiler", "-fPIC", "-o", so, src], check=True)
+    return ctypes.CDLL(so)
+
+
+def test_oracle_philox_matches_curand():
+    lib = _compile_curand_ref()
+    rng = np.random.default_rng(1)
+    n = 4096
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    ctr[:, 1] = rng.integers(0, 2, n)
+    ctr[:, 2] = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    ctr[:, 3] = rng.integers(0, 2 ** 16, n)
+    for seed in (0, 0x0123456789ABCDEF, 2 ** 64 - 1):
+        out = np.zeros_like(ctr)
+        assert lib.curand_ref(ctr.ctypes.data, ctypes.c_ulonglong(seed), out.ctypes.data, n) == 0
+        ref = oracle.philox(ctr, (seed & 0xFFFFFFFF, seed >> 32))
+        assert np.array_equal(out, ref)
+
+
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("layout", [capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE])
+@pytest.mark.parametrize("threads", [32, 64, 128])
+def test_flat8x12_bit_exact_with_event_log(layout, threads):
+    b = W.flat8x12()                     # 64 replicas, ~1e4 events, 100-point grid
+    cap = 256
+    g = gpu_run(b, log_cap=cap, layout=layout, block_threads=threads)
+    o = oracle.simulate(b, log_cap=cap, threads=8)
+    assert_same(g, o)
+    assert np.array_equal(g["log_rule"], o["log_rule"])
+    assert np.array_equal(g["log_slot"], o["log_slot"])
+    assert np.array_equal(g["log_t"].view(np.int64), o["log_t"].view(np.int64))
+    assert np.all(g["status"] == oracle.ST_OK)
+
+
+@pytest.mark.parametrize("name,R,scale", [("flat16x24", 333, 1.0), ("flat32x64", 97, 0.1)])
+def test_flat_workloads_ragged_bit_exact(name, R, scale):
+    """Several blocks and a ragged last block; flat32x64 with a tenth of its horizon."""
+    b0 = getattr(W, name)(R=R)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * scale, R, b0.seed)
+    for layout in (capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE):
+        g = gpu_run(b, layout=layout)
+        o = oracle.simulate(b, threads=8)
+        assert_same(g, o)
+
+
+def test_sweep_points_bit_exact():
+    b0 = W.sweep256x256(P=7, R=9)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.05, b0.R, b0.seed)
+    g = gpu_run(b, sums=True, means=True)
+    o = oracle.simulate(b, threads=8)
+    assert_same(g, o)
+    sums = oracle.sums(o["states"], b.P, b.R)
+    assert np.array_equal(g["sums"], sums)
+    assert np.array_equal(g["means"].view(np.int64), (sums.astype(np.float64) / b.R).view(np.int64))
+
+
+def test_init_per_sweep_point():
+    b0 = W.flat8x12(R=5)
+    P = 3
+    rates = np.tile(b0.rates, (P, 1)) * np.array([[1.0], [0.5], [2.0]])
+    init = np.stack([b0.init[0], b0.init[0] * 2, b0.init[0] // 2]).astype(np.int32)
+    b = W.Batch(b0.model, rates, init, b0.grid * 0.2, 5, 77)
+    assert_same(gpu_run(b), oracle.simulate(b))
+
+
+# ----------------------------------------------------------------------------
+# Edge cases and statuses
+# ----------------------------------------------------------------------------
+
+def test_single_trajectory_single_grid_point():
+    b0 = W.flat8x12(R=1)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid[-1:].copy(), 1, 3)
+    assert_same(gpu_run(b), oracle.simulate(b))
+    b = W.Batch(b0.model, b0.rates, b0.init, np.array([0.0]), 1, 3)      # T = 0: no event
+    g = gpu_run(b)
+    assert_same(g, oracle.simulate(b))
+    assert g["events"][0] == 0
+
+
+def test_event_limit_zero_and_small():
+    b0 = W.flat8x12(R=40)
+    for me in (0, 1, 37):
+        b = W.Batch(b0.model, b0.rates, b0.init, b0.grid, 40, b0.seed, max_events=me)
+        g = gpu_run(b)
+        assert_same(g, oracle.simulate(b))
+        assert np.all(g["status"] == oracle.ST_EVENT_LIMIT)
+
+
+def test_absorbed_int_overflow_prop_overflow_bad_input():
+    death = W.flat_model(1, [({0: 1}, {})])
+    cases = [
+        W.Batch(death, np.array([[2.0]]), np.array([[30]], np.int32), np.array([0.0, 100.0]), 50, 3),
+        W.Batch(W.birth_death(), np.array([[1e6, 1e-9]]), np.array([[2 ** 31 - 3]], np.int32),
+                np.array([0.0, 1.0]), 10, 1),
+        W.Batch(W.dimerisation(), np.array([[1e300, 1.0]]), np.array([[2 ** 30, 0]], np.int32),
+                np.array([0.0, 1.0]), 10, 1),
+        W.Batch(W.birth_death(), np.array([[-1.0, 1.0]]), np.array([[3]], np.int32), np.array([0.0, 1.0]), 4, 1),
+        W.Batch(W.birth_death(), np.array([[1.0, np.nan]]), np.array([[3]], np.int32), np.array([0.0, 1.0]), 4, 1),
+        W.Batch(W.birth_death(), np.array([[1.0, 1.0]]), np.array([[3]], np.int32), np.array([0.0, 0.0]), 4, 1),
+        W.Batch(W.birth_death(), np.array([[1.0, 1.0]]), np.array([[3]], np.int32), np.array([-1.0, 1.0]), 4, 1),
+        W.Batch(W.birth_death(), np.array([[1.0, 1.0]]), np.array([[-3]], np.int32), np.array([0.0, 1.0]), 4, 1),
+        W.Batch(W.birth_death(), np.array([[1.0, 1.0]]), np.array([[3]], np.int32), np.array([0.0, np.inf]), 4, 1),
+    ]
+    expect = [oracle.ST_ABSORBED, oracle.ST_INT_OVERFLOW, oracle.ST_PROP_OVERFLOW] + [oracle.ST_BAD_INPUT] * 6
+    for b, st in zip(cases, expect):
+        g = gpu_run(b, sums=True)
+        o = oracle.simulate(b)
+        assert_same(g, o)
+        assert np.all(g["status"] == st), (st, g["status"])
+        assert np.array_equal(g["sums"], oracle.sums(o["states"], b.P, b.R))
+
+
+def test_deadline_stops_with_timeout_status():
+    b0 = W.flat32x64(R=4096)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 100.0, b0.R, b0.seed)   # ~1e7 events each
+    g = gpu_run(b, deadline_ns=20_000_000, layout=capi.CWC_LAYOUT_QUEUE)
+    assert np.all(g["status"] == capi.CWC_TRAJ_TIMEOUT)
+    # the trajectories that ran are a prefix of the exact ones: oracle with the same event count
+    q = int(np.argmax(g["events"]))
+    o = oracle.simulate(b, q, q + 1, max_events=int(g["events"][q]))
+    assert o["hash"][0] == g["hash"][q]
+
+
+def test_argument_errors_do_not_launch():
+    b = W.flat8x12(R=2)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    with pytest.raises(capi.CwcError):
+        api.simulate(cm, rates, init, grid, 0, 1)
+    with pytest.raises(capi.CwcError):
+        api.simulate(cm, rates, init, grid, 2, 1, max_events=2 ** 32)
+    a = api._sim_args(cm, rates, init, grid, 2, 1, 10, capi.CWC_LAYOUT_QUEUE, 0, 0)
+    with pytest.raises(capi.CwcError, match="WORKSPACE"):
+        capi.cwc_simulate(cm.handle, a, 0)
+
+
+# ----------------------------------------------------------------------------
+# Score replay
+# ----------------------------------------------------------------------------
+
+def test_sensitivity_partials_match_oracle():
+    """Per-trajectory score contractions vs the oracle.  Both sides evaluate
+    the same formula on the same path; the integral int H_j dt is accumulated
+    lazily on the GPU (only when H_j changes) and at every event in the
+    oracle, so values differ by FP64 rounding only: |d| <= 1e-9 * (|x| + s),
+    s = the mean magnitude of the partials (~1e4 additions of terms of that
+    size, each off by <= 1 ulp)."""
+    b0 = W.flat8x12(R=96, G=12)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.25, b0.R, b0.seed)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    means = torch.from_numpy(oracle.mean_observables(b, threads=8)).cuda()
+    rng = np.random.default_rng(3)
+    gm = torch.from_numpy(rng.standard_normal((1, b.G, b.model.n_observables))).cuda()
+    res = api.sensitivity(cm, rates, init, grid, b.R, b.seed, means, gm, partials=True)
+    torch.cuda.synchronize()
+    gp = res["partials"].cpu().numpy().reshape(b.R, -1)
+    ograd, op = oracle.sensitivity(b, means.cpu().numpy(), gm.cpu().numpy(), threads=8)
+    scale = np.mean(np.abs(op))
+    assert np.all(np.abs(gp - op) <= 1e-9 * (np.abs(op) + scale))
+    gg = res["grad_rates"].cpu().numpy()
+    assert np.all(np.abs(gg - ograd) <= 1e-9 * (np.abs(ograd) + scale))
+
+
+def test_autograd_function_forward_and_backward():
+    b0 = W.flat8x12(R=256, G=10)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.1, b0.R, b0.seed)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    k = rates.clone().requires_grad_(True)
+    m = api.mean_observables(k, cm, init, grid, b.R, b.seed)
+    om = oracle.mean_observables(b, threads=8)
+    assert np.array_equal(m.detach().cpu().numpy().view(np.int64), om.view(np.int64))
+    w = torch.linspace(-1, 1, m.numel(), dtype=torch.float64, device="cuda").reshape(m.shape)
+    (m * w).sum().backward()
+    direct = api.sensitivity(cm, rates, init, grid, b.R, b.seed, m.detach(), w)["grad_rates"]
+    torch.cuda.synchronize()
+    assert torch.equal(k.grad, direct)
+    og, _ = oracle.sensitivity(b, om, w.cpu().numpy(), threads=8)
+    assert np.allclose(k.grad.cpu().numpy(), og, rtol=1e-9, atol=1e-9 * np.abs(og).max())
+
+
+def test_sensitivity_deterministic():
+    b = W.flat16x24(R=2048, G=20)
+    b = W.Batch(b.model, b.rates, b.init, b.grid * 0.1, b.R, b.seed)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    m = api.simulate(cm, rates, init, grid, b.R, b.seed, states=False, means=True, traj=False)["means"]
+    gm = torch.ones_like(m)
+    g1 = api.sensitivity(cm, rates, init, grid, b.R, b.seed, m, gm)["grad_rates"]
+    g2 = api.sensitivity(cm, rates, init, grid, b.R, b.seed, m, gm, layout=capi.CWC_LAYOUT_STATIC)["grad_rates"]
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
