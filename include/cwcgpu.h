@@ -202,6 +202,31 @@ typedef struct {
   size_t workspace_bytes;
 } cwc_sim_args;
 
+/*
+ * cwc_simulate_noalloc: the same simulation as cwc_simulate for callers that
+ * cannot allocate device memory, so cannot size and pass a workspace (for
+ * example code whose device memory is owned by another framework's pool, or
+ * a service with a fixed device-memory budget reserved up front).  The paper
+ * has no counterpart: this is an interface convenience of this library.
+ *
+ * The scratch it needs (the work-queue ticket, the deadline timestamp and,
+ * when only `means` is requested, the int64 replica sums) lives in one
+ * statically sized device array of CWC_NOALLOC_SCRATCH_BYTES inside the
+ * library; every GPU that loads the library holds that array until the
+ * process exits.  args->workspace and args->workspace_bytes are ignored.
+ * A call whose scratch would exceed the array (256 bytes + 8 * P * G * O when
+ * means are requested without sums) returns CWC_ERR_INVALID_ARG and enqueues
+ * nothing.  It calls no cudaMalloc or cudaFree.
+ *
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.  All
+ * calls on a device share the one array and each clears what must start at
+ * zero, so calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it: serialise them.
+ */
+#define CWC_NOALLOC_SCRATCH_BYTES (1u << 20)
+cwc_status cwc_simulate_noalloc(const cwc_model* model, const cwc_sim_args* args, void* stream);
+
 /* Workspace bytes cwc_simulate needs for these arguments (0 if none). */
 cwc_status cwc_simulate_workspace_size(const cwc_model* model, const cwc_sim_args* args, size_t* bytes);
 

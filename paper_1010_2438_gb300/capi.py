@@ -24,7 +24,9 @@ CWC_LAYOUT_AUTO, CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE = range(3)
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = ("cwc_model_create", "cwc_model_destroy", "cwc_model_num_observables", "cwc_simulate_workspace_size",
-            "cwc_simulate", "cwc_sensitivity_workspace_size", "cwc_sensitivity", "cwc_last_error", "cwc_version")
+            "cwc_simulate", "cwc_simulate_noalloc", "cwc_sensitivity_workspace_size", "cwc_sensitivity",
+            "cwc_last_error", "cwc_version")
+CWC_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -82,6 +84,8 @@ def lib() -> ctypes.CDLL:
         L.cwc_simulate_workspace_size.restype = ctypes.c_int
         L.cwc_simulate.argtypes = [_vp, ctypes.POINTER(cwc_sim_args), _vp]
         L.cwc_simulate.restype = ctypes.c_int
+        L.cwc_simulate_noalloc.argtypes = [_vp, ctypes.POINTER(cwc_sim_args), _vp]
+        L.cwc_simulate_noalloc.restype = ctypes.c_int
         L.cwc_sensitivity_workspace_size.argtypes = [_vp, ctypes.POINTER(cwc_sim_args),
                                                      ctypes.POINTER(cwc_sens_args), ctypes.POINTER(ctypes.c_size_t)]
         L.cwc_sensitivity_workspace_size.restype = ctypes.c_int
@@ -131,6 +135,13 @@ def cwc_simulate_workspace_size(handle: int, args: cwc_sim_args) -> int:
 
 def cwc_simulate(handle: int, args: cwc_sim_args, stream: int = 0) -> None:
     _check(lib().cwc_simulate(handle, ctypes.byref(args), stream))
+
+
+def cwc_simulate_noalloc(handle: int, args: cwc_sim_args, stream: int = 0) -> None:
+    """cwc_simulate for callers that cannot allocate device memory (no
+    workspace: the library's fixed CWC_NOALLOC_SCRATCH_BYTES device array is
+    used instead; calls overlapping on the GPU race on it)."""
+    _check(lib().cwc_simulate_noalloc(handle, ctypes.byref(args), stream))
 
 
 def cwc_sensitivity_workspace_size(handle: int, args: cwc_sim_args, sens: cwc_sens_args) -> int:

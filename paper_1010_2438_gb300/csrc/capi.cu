@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -390,6 +391,47 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     if (e != cudaSuccess) return cuda_fail(e, "reduce kernel launch");
   }
   return CWC_OK;
+}
+
+// Scratch of cwc_simulate_noalloc: one statically sized array per device that
+// loads the library.  In host code its name is only a stand-in; the device
+// address comes from cudaGetSymbolAddress, looked up once per device with
+// that device current and cached here.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CWC_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[256];
+
+static cwc_status noalloc_scratch_address(int device, void** addr) {
+  if (device < 0 || device >= 256) return fail(CWC_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_addr[device] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_addr[device] = p;
+  }
+  *addr = g_noalloc_addr[device];
+  return CWC_OK;
+}
+
+cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void* stream) {
+  g_last_error.clear();
+  cwc_status st = check_sim_args(m, a);  // also checks that m's device is the current one
+  if (st != CWC_OK) return st;
+  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
+  const WsLayout w = ws_layout(m, a, false, false);
+  if (w.total > CWC_NOALLOC_SCRATCH_BYTES)
+    return fail(CWC_ERR_INVALID_ARG, "this call needs " + std::to_string(w.total) +
+                                         " bytes of scratch; cwc_simulate_noalloc holds " +
+                                         std::to_string(CWC_NOALLOC_SCRATCH_BYTES) +
+                                         " (request sums, or use cwc_simulate with a workspace)");
+  void* scratch = nullptr;
+  st = noalloc_scratch_address(m->device, &scratch);
+  if (st != CWC_OK) return st;
+  cwc_sim_args b = *a;
+  b.workspace = scratch;
+  b.workspace_bytes = CWC_NOALLOC_SCRATCH_BYTES;
+  return run_flat(m, &b, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 cwc_status cwc_simulate(const cwc_model* m, const cwc_sim_args* a, void* stream) {
