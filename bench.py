@@ -199,6 +199,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--layout", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--replicas", type=int, default=0, help="smaller case for profiling (default: 65536)")
+    ap.add_argument("--horizon-scale", type=float, default=1.0, help="scale the time grid (profiling only)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -217,7 +219,10 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.device("cuda", torch.cuda.current_device())
     lib_build.build()
-    batch = W.flat32x64()
+    batch = W.flat32x64(R=args.replicas) if args.replicas else W.flat32x64()
+    if args.horizon_scale != 1.0:
+        batch = W.Batch(batch.model, batch.rates, batch.init, batch.grid * args.horizon_scale, batch.R, batch.seed,
+                        name=batch.name)
     R = batch.R
     cm = api.CompiledModel(batch.model)
     rates, init, grid = api.device_inputs(batch, dev)
@@ -316,13 +321,15 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        cpu = cpu_baseline(batch, threads, 2 * threads)
+        cpu = cpu_baseline(batch, threads, min(batch.n_traj, 6 * threads))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "P": batch.P, "R": R,
+                "config": {"workload": WORKLOAD if not (args.replicas or args.horizon_scale != 1.0) else
+                       "%s (profiling case: R=%d, horizon x%g)" % (WORKLOAD, R, args.horizon_scale),
+                       "description": WORKLOAD_DESC, "P": batch.P, "R": R,
                            "G": batch.G, "S": batch.model.n_species, "M": batch.model.n_rules,
                            "events_per_step_per_gpu": events, "statuses": statuses,
                            "layout": ["auto(queue)", "static", "queue"][args.layout],

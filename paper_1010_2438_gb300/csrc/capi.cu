@@ -19,6 +19,7 @@ cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queu
                         int blocks_per_sm_cap, cudaStream_t stream, int* used_blocks);
 size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens);
 int flat_table_bytes_host(int M, int n_deps);
+int flat_best_threads(const FlatParams& prm, bool queue, bool sens);
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, double* grad, int P, int R, int M, cudaStream_t st);
 }  // namespace cwcgpu
@@ -30,7 +31,8 @@ struct cwc_model {
   bool flat = false;
   int device = 0;
   // flat compilation
-  int B = 1, MP = 32, n_deps = 0;
+  int B = 1, n_deps = 0;
+  int checked_counts = 0;
   int32_t* d_tables = nullptr;  // [M][RULE_WORDS] followed by [n_deps]
   std::vector<int32_t> h_tables;
 };
@@ -119,8 +121,8 @@ FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
   prm.S = m->S;
   prm.M = m->M;
   prm.B = m->B;
-  prm.MP = m->MP;
   prm.n_deps = m->n_deps;
+  prm.checked_counts = m->checked_counts;
   prm.rules = m->d_tables;
   prm.deps = m->d_tables + (size_t)m->M * RULE_WORDS;
   prm.P = a->P;
@@ -140,19 +142,9 @@ FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
   return prm;
 }
 
-int pick_threads(const cwc_model* m, const cwc_sim_args* a, bool sens) {
+int pick_threads(const cwc_model* m, const cwc_sim_args* a, const FlatParams& prm, bool queue, bool sens) {
   if (a->block_threads > 0) return a->block_threads;
-  // largest of 128 / 64 / 32 threads whose block fits in shared memory twice per SM
-  FlatParams prm;
-  std::memset(&prm, 0, sizeof(prm));
-  prm.S = m->S;
-  prm.M = m->M;
-  prm.B = m->B;
-  prm.MP = m->MP;
-  prm.smem_table_bytes = flat_table_bytes_host(m->M, m->n_deps);
-  for (int T : {128, 64, 32})
-    if (flat_smem_bytes(prm, T, sens) * 2 <= 220 * 1024) return T;
-  return 32;
+  return flat_best_threads(prm, queue, sens);
 }
 
 }  // namespace
@@ -217,7 +209,11 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
   }
   // ---- flat compilation ----
   m->B = (M + 31) / 32;
-  m->MP = std::max(M, 32);
+  for (int j = 0; j < M; ++j) {
+    int order = 0;
+    for (int s = 0; s < S; ++s) order += d->lhs[(size_t)j * 3 * S + s];
+    if (order >= 3) m->checked_counts = 1;
+  }
   std::vector<std::vector<int>> reac(M), delta(M);
   for (int j = 0; j < M; ++j) {
     const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
@@ -284,7 +280,6 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
     prm.S = S;
     prm.M = M;
     prm.B = m->B;
-    prm.MP = m->MP;
     prm.smem_table_bytes = flat_table_bytes_host(M, n_deps);
     if (flat_smem_bytes(prm, 32, true) > 220 * 1024) {
       delete m;
@@ -379,7 +374,9 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
   }
   const LogConstants lc = make_log_constants();
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
-  const int T = pick_threads(m, a, is_sens);
+  const int T = pick_threads(m, a, prm, queue, is_sens);
+  if (flat_smem_bytes(prm, T, is_sens) > 227 * 1024)
+    return fail(CWC_ERR_INVALID_ARG, "block_threads too large for this model's shared-memory state");
   e = launch_flat(prm, lc, queue, is_sens, T, 0, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "flat SSA kernel launch");
   if (!is_sens && a->means != nullptr) {

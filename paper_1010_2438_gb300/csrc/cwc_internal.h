@@ -48,8 +48,9 @@ static_assert(sizeof(WorkspaceHeader) == 256, "workspace header size");
 // Everything one flat-model launch needs.
 struct FlatParams {
   // compiled model
-  int S, M, B, MP;          // species, rules, leaf block size, rows of prop (max(M, 32))
+  int S, M, B;              // species, rules, leaf block size ceil(M/32)
   int n_deps;
+  int checked_counts;       // 1 if some rule has order >= 3 (int64 products may overflow)
   const int32_t* rules;     // [M][RULE_WORDS]
   const int32_t* deps;      // [n_deps]
   // batch

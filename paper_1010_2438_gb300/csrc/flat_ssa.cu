@@ -4,22 +4,27 @@
 //
 // Layout.  A block of T threads holds, in shared memory, the compiled rule
 // tables (shared by the block) and per-thread arrays stored [index][thread],
-// so that every thread reading "its" element i of an array touches bank
-// (2*tid) mod 32 whatever i is: data-dependent indices never conflict.
-//   prop[MP][T]  double  a_j = k_j * H_j (rows M..31 stay +0 when M < 32)
-//   leaf[32][T]  double  leaf sums of the 32-lane blocked tree (B > 1 only;
-//                        for B = 1 the leaves are prop rows 0..31)
+// so that every thread reading "its" element i touches bank (2*tid) mod 32
+// whatever i is: data-dependent indices never conflict.
+//   leaf[32][T]  double  leaves of the 32-lane blocked tree.  With B = 1 leaf
+//                        l is a_l itself (l >= M: +0); with B > 1 it is the
+//                        block sum and the a_j are recomputed from the counts
+//                        when needed instead of being stored
 //   node[31][T]  double  internal tree nodes, root = node[30] = a0
 //   cnt[S][T]    int32   species counts
 // plus, for the score replay, Hd/I/tl/partial [M][T] doubles and N [M][T].
+// Keeping only the tree and the counts (504 + 4S bytes per trajectory) is
+// what lets 8-10 warps share an SM: GB300's FP64 pipe (~1.6 lane-ops per
+// clock per SM) has long latency, and hiding it needs resident warps.
 //
 // Per event the thread: draws Philox(n, 0, r, p); computes tau with the
 // fixed FP64 logarithm and one IEEE division; records grid points passed;
 // descends the tree (integer compares of non-negative doubles, one FP64
-// subtraction per level); applies the stoichiometry change; recomputes the
-// propensities of the rule's dependents (Gibson-Bruck dependency graph) and
-// only the leaves and internal nodes above them.  a0 is always the tree root,
-// never a running sum, so the values equal a full rebuild bit for bit.
+// subtraction per level); applies the stoichiometry change; rebuilds only the
+// leaves holding a rule whose propensity reads a changed species (Gibson-
+// Bruck dependency graph) and the internal nodes above them.  a0 is always
+// the tree root, never a running sum, so values equal a full rebuild bit for
+// bit.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -40,15 +45,15 @@ __device__ __forceinline__ long long grab_next(WorkspaceHeader* ws) {
 }
 
 // Shared-memory table region: rules, dependents, e*ln2 table (doubles last,
-// 8-byte aligned).  Must match flat_table_bytes() on the host.
+// 16-byte aligned).  Must match on host and device.
 __host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
   int words = M * RULE_WORDS + n_deps;
   int bytes = ((words * 4 + 15) / 16) * 16;
   return bytes + 54 * 8;
 }
 
-__host__ __device__ inline int flat_thread_bytes(int S, int M, int B, int MP, bool sens) {
-  int doubles = MP + (B > 1 ? 32 : 0) + TREE_NODES + (sens ? 4 * M : 0);
+__host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
+  int doubles = 32 + TREE_NODES + (sens ? 4 * M : 0);
   int ints = S + (sens ? M : 0);
   return doubles * 8 + ints * 4;
 }
@@ -59,26 +64,29 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
   const int tid = threadIdx.x;
-  const int S = prm.S, M = prm.M, B = prm.B, MP = prm.MP, G = prm.G;
+  const int S = prm.S, M = prm.M, B = prm.B, G = prm.G;
 
   int32_t* s_rules = reinterpret_cast<int32_t*>(smem);
   int32_t* s_deps = s_rules + M * RULE_WORDS;
   const int tbl_words = M * RULE_WORDS + prm.n_deps;
   double* s_eln2 = reinterpret_cast<double*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
-  double* prop = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
-  double* leaf = prop + MP * T;
-  double* node = leaf + (B > 1 ? 32 * T : 0);
-  double* Hd = node + TREE_NODES * T;    // score replay only
+  // Per-thread arrays [index][T]: each pointer below already points at this
+  // thread's column, so element i of the array is ptr[i * T].
+  double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
+  const int n_dbl_rows = 32 + TREE_NODES + (kSens ? 4 * M : 0);
+  double* leaf = dbase + tid;                                   // [32][T]
+  double* node = dbase + 32 * T + tid;                          // [31][T]
+  double* Hd = dbase + (32 + TREE_NODES) * T + tid;             // score replay only: [M][T] each
   double* Iac = Hd + M * T;
   double* tl = Iac + M * T;
   double* part = tl + M * T;
-  int32_t* cnt = reinterpret_cast<int32_t*>(kSens ? part + M * T : node + TREE_NODES * T);
-  int32_t* Nf = cnt + S * T;
+  int32_t* ibase = reinterpret_cast<int32_t*>(dbase + (size_t)n_dbl_rows * T);
+  int32_t* cnt = ibase + tid;                                   // [S][T]
+  int32_t* Nf = ibase + S * T + tid;                            // score replay only: [M][T]
 
-#define PROP(i) prop[(i) * T + tid]
-#define LEAFV(l) (B > 1 ? leaf[(l) * T + tid] : prop[(l) * T + tid])
-#define NODE(i) node[(i) * T + tid]
-#define CNT(s) cnt[(s) * T + tid]
+#define LEAF(l) leaf[(l) * T]
+#define NODE(i) node[(i) * T]
+#define CNT(s) cnt[(s) * T]
 
   for (int i = tid; i < tbl_words; i += T) s_rules[i] = prm.rules[i];   // rules then deps, contiguous
   for (int i = tid; i < 54; i += T) s_eln2[i] = lc.e_ln2[i];
@@ -108,6 +116,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   const unsigned long long deadline = s_deadline;
   const long long T_bits = dbits(prm.grid[G - 1]);
   const bool vec_states = (S % 4 == 0) && ((reinterpret_cast<uintptr_t>(prm.states) & 15) == 0);
+  const bool checked = prm.checked_counts != 0;
 
   // ---- trajectory state (registers) ----
   long long q = 0;
@@ -147,9 +156,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
         c = __dadd_rn(c, __dmul_rn(gm[o], __dadd_rn((double)CNT(o), -mm[o])));
       const double gt = prm.grid[g];
       for (int i = 0; i < M; ++i) {
-        const double Ig = __dadd_rn(Iac[i * T + tid], __dmul_rn(Hd[i * T + tid], __dadd_rn(gt, -tl[i * T + tid])));
-        const double Si = __dadd_rn(__ddiv_rn((double)Nf[i * T + tid], kp[i]), -Ig);
-        part[i * T + tid] = __dadd_rn(part[i * T + tid], __dmul_rn(c, Si));
+        const double Ig = __dadd_rn(Iac[i * T], __dmul_rn(Hd[i * T], __dadd_rn(gt, -tl[i * T])));
+        const double Si = __dadd_rn(__ddiv_rn((double)Nf[i * T], kp[i]), -Ig);
+        part[i * T] = __dadd_rn(part[i * T], __dmul_rn(c, Si));
       }
     }
   };
@@ -158,16 +167,36 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     for (; gi < G; ++gi) record(gi);
   };
 
-  // H_i of rule i at the current counts (int64 with overflow flag)
+  // H_i of rule i at the current counts (Match_Populations: product of
+  // binomials).  Models whose rules all have order <= 2 cannot overflow
+  // (n*m < 2^62 for counts < 2^31) and take 32x32->64-bit products only.
   auto count_h = [&](int i) -> unsigned long long {
     const int32_t* rec = s_rules + i * RULE_WORDS;
     const int nr = rec[R_NREAC];
+    if (!checked) {
+      if (nr == 0) return 1ull;
+      const int v0 = rec[R_REAC];
+      const unsigned n0 = (unsigned)CNT(v0 & 0xffff);
+      if (nr == 1)
+        return (v0 >> 16) == 1 ? (unsigned long long)n0 : ((unsigned long long)n0 * (n0 - 1u)) >> 1;
+      const int v1 = rec[R_REAC + 1];
+      return (unsigned long long)n0 * (unsigned)CNT(v1 & 0xffff);
+    }
     unsigned long long hh = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[R_REAC + a];
       hh = mul_checked(hh, binom12(CNT(v & 0xffff), v >> 16), &ovf);
     }
     return hh;
+  };
+  auto prop_of = [&](int i) -> double { return __dmul_rn(kp[i], u63_to_double_rn(count_h(i))); };
+
+  // leaf l as the blocked sum of its rules (B > 1)
+  auto leaf_sum = [&](int l) -> double {
+    const int j0 = l * B, j1 = min(j0 + B, M);
+    double s = j0 < M ? prop_of(j0) : 0.0;
+    for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, prop_of(jj));
+    return s;
   };
 
   auto finalize = [&]() {
@@ -176,7 +205,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     if (prm.traj_hash) prm.traj_hash[q] = h;
     if (prm.traj_final_t) prm.traj_final_t[q] = t;
     if (kSens) {
-      for (int i = 0; i < M; ++i) prm.partials[(size_t)q * M + i] = part[i * T + tid];
+      for (int i = 0; i < M; ++i) prm.partials[(size_t)q * M + i] = part[i * T];
     }
   };
 
@@ -204,7 +233,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       CNT(s) = v;
     }
     if (kSens) {
-      for (int i = 0; i < M; ++i) part[i * T + tid] = 0.0;
+      for (int i = 0; i < M; ++i) part[i * T] = 0.0;
     }
     if (bad) {
       status = TS_BAD_INPUT;
@@ -214,28 +243,18 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       }
       return true;
     }
-    for (int i = 0; i < M; ++i) {
-      const unsigned long long hh = count_h(i);
-      PROP(i) = __dmul_rn(kp[i], __ll2double_rn((long long)hh));
-      if (kSens) {
-        Hd[i * T + tid] = __ll2double_rn((long long)hh);
-        Iac[i * T + tid] = 0.0;
-        tl[i * T + tid] = 0.0;
-        Nf[i * T + tid] = 0;
+    if (kSens) {
+      for (int i = 0; i < M; ++i) {
+        Hd[i * T] = u63_to_double_rn(count_h(i));
+        Iac[i * T] = 0.0;
+        tl[i * T] = 0.0;
+        Nf[i * T] = 0;
       }
     }
-    for (int i = M; i < MP; ++i) PROP(i) = 0.0;
-    if (B > 1) {
-      for (int l = 0; l < 32; ++l) {
-        const int j0 = l * B, j1 = min(j0 + B, M);
-        double s = 0.0;
-        for (int j = j0; j < j1; ++j) s = __dadd_rn(s, PROP(j));
-        leaf[l * T + tid] = s;
-      }
-    }
+    for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
     for (int nd = 0; nd < TREE_NODES; ++nd) {
-      const double a = nd < 16 ? LEAFV(2 * nd) : NODE(2 * nd - 32);
-      const double b = nd < 16 ? LEAFV(2 * nd + 1) : NODE(2 * nd - 31);
+      const double a = nd < 16 ? LEAF(2 * nd) : NODE(2 * nd - 32);
+      const double b = nd < 16 ? LEAF(2 * nd + 1) : NODE(2 * nd - 31);
       NODE(nd) = __dadd_rn(a, b);
     }
     return false;
@@ -246,7 +265,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     if (ovf) {
       status = TS_PROP_OVERFLOW;
       if (kSens)
-        for (int i = 0; i < M; ++i) Hd[i * T + tid] = 0.0;
+        for (int i = 0; i < M; ++i) Hd[i * T] = 0.0;
       fill();
       return true;
     }
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     if (a0b >= 0x7FF0000000000000ll) {
       status = TS_PROP_OVERFLOW;
       if (kSens)
-        for (int i = 0; i < M; ++i) Hd[i * T + tid] = 0.0;
+        for (int i = 0; i < M; ++i) Hd[i * T] = 0.0;
       fill();
       return true;
     }
@@ -303,8 +322,8 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     }
     int l;
     {
-      const double L = LEAFV(2 * nd);
-      const double Rv = LEAFV(2 * nd + 1);
+      const double L = LEAF(2 * nd);
+      const double Rv = LEAF(2 * nd + 1);
       const bool left = dbits(x) < dbits(L) || dbits(Rv) == 0;
       const double xr = __dadd_rn(x, -L);
       x = left ? x : xr;
@@ -319,8 +338,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       j = -1;
       double s = 0.0;
       for (int jj = j0; jj < j1; ++jj) {
-        const double a = PROP(jj);
-        if (dbits(a) > 0) {
+        const unsigned long long hh = count_h(jj);
+        if (hh != 0ull) {
+          const double a = __dmul_rn(kp[jj], u63_to_double_rn(hh));
           s = last < 0 ? a : __dadd_rn(s, a);
           last = jj;
           if (dbits(x) < dbits(s)) {
@@ -350,37 +370,38 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       const int v = rec[R_DELTA + d];
       CNT(v & 0xffff) += v >> 16;
     }
-    if (kSens) Nf[j * T + tid] += 1;
-    // dependents: new propensities
-    const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
-    for (int e = 0; e < dcnt; ++e) {
-      const int i = s_deps[doff + e];
-      const unsigned long long hh = count_h(i);
-      const double hd = __ll2double_rn((long long)hh);
-      PROP(i) = __dmul_rn(kp[i], hd);
-      if (kSens) {
-        Iac[i * T + tid] = __dadd_rn(Iac[i * T + tid], __dmul_rn(Hd[i * T + tid], __dadd_rn(tn, -tl[i * T + tid])));
-        tl[i * T + tid] = tn;
-        Hd[i * T + tid] = hd;
+    if (kSens) {
+      Nf[j * T] += 1;
+      const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
+      for (int e = 0; e < dcnt; ++e) {
+        const int i = s_deps[doff + e];
+        const double hd = u63_to_double_rn(count_h(i));
+        Iac[i * T] = __dadd_rn(Iac[i * T], __dmul_rn(Hd[i * T], __dadd_rn(tn, -tl[i * T])));
+        tl[i * T] = tn;
+        Hd[i * T] = hd;
       }
     }
-    if (B > 1) {
+    if (B == 1) {
+      // the leaves are the propensities: recompute the dependents
+      const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
+      for (int e = 0; e < dcnt; ++e) {
+        const int i = s_deps[doff + e];
+        LEAF(i) = prop_of(i);
+      }
+    } else {
       unsigned lm = (unsigned)rec[R_LEAFMASK];
       while (lm) {
         const int ll = __ffs(lm) - 1;
         lm &= lm - 1u;
-        const int j0 = ll * B, j1 = min(j0 + B, M);
-        double s = PROP(j0);
-        for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, PROP(jj));
-        leaf[ll * T + tid] = s;
+        LEAF(ll) = leaf_sum(ll);
       }
     }
     unsigned nm = (unsigned)rec[R_NODEMASK];
     while (nm) {
       const int k = __ffs(nm) - 1;
       nm &= nm - 1u;
-      const double a = k < 16 ? LEAFV(2 * k) : NODE(2 * k - 32);
-      const double b = k < 16 ? LEAFV(2 * k + 1) : NODE(2 * k - 31);
+      const double a = k < 16 ? LEAF(2 * k) : NODE(2 * k - 32);
+      const double b = k < 16 ? LEAF(2 * k + 1) : NODE(2 * k - 31);
       NODE(k) = __dadd_rn(a, b);
     }
     if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
@@ -416,8 +437,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       need_new = true;
     }
   }
-#undef PROP
-#undef LEAFV
+#undef LEAF
 #undef NODE
 #undef CNT
 }
@@ -430,7 +450,7 @@ template <bool kQueue, bool kSens>
 static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
                             cudaStream_t stream, int* used_blocks) {
   auto kern = flat_ssa_kernel<kQueue, kSens>;
-  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, prm.B, prm.MP, kSens);
+  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   long long blocks;
@@ -456,10 +476,35 @@ static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T
 }
 
 size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens) {
-  return (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, prm.B, prm.MP, sens);
+  return (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, sens);
 }
 
 int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps); }
+
+// Block size with the most resident warps per SM (ties: the larger block).
+template <bool kQueue, bool kSens>
+static int best_threads_t(const FlatParams& prm) {
+  auto kern = flat_ssa_kernel<kQueue, kSens>;
+  int best_T = 32, best_warps = -1;
+  for (int T = 32; T <= 256; T += 32) {
+    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
+    if (smem > 227 * 1024) break;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem) != cudaSuccess) break;
+    const int warps = per_sm * T / 32;
+    if (warps >= best_warps) {
+      best_warps = warps;
+      best_T = T;
+    }
+  }
+  return best_T;
+}
+
+int flat_best_threads(const FlatParams& prm, bool queue, bool sens) {
+  if (queue) return sens ? best_threads_t<true, true>(prm) : best_threads_t<true, false>(prm);
+  return sens ? best_threads_t<false, true>(prm) : best_threads_t<false, false>(prm);
+}
 
 cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queue, bool sens, int T,
                         int blocks_per_sm_cap, cudaStream_t stream, int* used_blocks) {

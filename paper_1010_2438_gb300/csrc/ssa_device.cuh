@@ -102,6 +102,33 @@ __device__ __forceinline__ unsigned long long fnv1a_event(unsigned long long h, 
 
 constexpr unsigned long long FNV_OFFSET = 0xcbf29ce484222325ull;
 
+// (double)x for 0 <= x < 2^63, rounded to nearest-even, with integer
+// instructions only.  Same value as the conversion instruction, which on
+// GB300 issues to the FP64 pipe.  Below 2^53 the value is exact: the double
+// is assembled from x's leading-one position and the bits under it; above,
+// the dropped low bits decide the rounding (ties to even), and a carry out of
+// the 53-bit significand bumps the exponent.
+__device__ __forceinline__ double u63_to_double_rn(unsigned long long x) {
+  if (x == 0ull) return 0.0;
+  int lead = 63 - __clzll((long long)x);
+  unsigned long long m;
+  if (lead <= 52) {
+    m = x << (52 - lead);
+  } else {
+    const int sh = lead - 52;
+    m = x >> sh;
+    const unsigned long long rem = x & ((1ull << sh) - 1ull);
+    const unsigned long long half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) m += 1ull;
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      lead += 1;
+    }
+  }
+  const unsigned long long bits = ((unsigned long long)(1023 + lead) << 52) | (m & 0x000FFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
 // Combinatorial count C(n, nu) for nu in {1, 2}, n >= 0 (Match_Populations).
 __device__ __forceinline__ unsigned long long binom12(int n, int nu) {
   const unsigned long long un = (unsigned long long)n;

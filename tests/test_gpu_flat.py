@@ -263,3 +263,23 @@ def test_sensitivity_deterministic():
     g2 = api.sensitivity(cm, rates, init, grid, b.R, b.seed, m, gm, layout=capi.CWC_LAYOUT_STATIC)["grad_rates"]
     torch.cuda.synchronize()
     assert torch.equal(g1, g2)
+
+
+def test_huge_counts_exercise_int64_to_double_rounding():
+    """Combinatorial counts above 2^53 (C(n,2), n*m with n ~ 2^30): the
+    propensity's int64 -> double conversion rounds, and any difference from
+    round-to-nearest-even would change a0 and so every event time."""
+    n = (1 << 30) + 12345
+    cases = [
+        W.Batch(W.dimerisation(), np.array([[1e-12, 1e-3]]), np.array([[n, 7]], np.int32), np.array([0.0, 1e9]), 64,
+                11, max_events=300),
+        W.Batch(W.heterodimer(), np.array([[3e-13, 2.5]]), np.array([[n, n - 999, 5]], np.int32),
+                np.array([0.0, 1e9]), 64, 12, max_events=300),
+        W.Batch(W.heterodimer(), np.array([[3e-13, 2.5]]), np.array([[(1 << 31) - 2, (1 << 31) - 5, 5]], np.int32),
+                np.array([0.0, 1e9]), 64, 13, max_events=300),
+    ]
+    for b in cases:
+        g = gpu_run(b, log_cap=300)
+        o = oracle.simulate(b, log_cap=300)
+        assert_same(g, o)
+        assert np.array_equal(g["log_t"].view(np.int64), o["log_t"].view(np.int64))
