@@ -201,6 +201,7 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--replicas", type=int, default=0, help="smaller case for profiling (default: 65536)")
     ap.add_argument("--horizon-scale", type=float, default=1.0, help="scale the time grid (profiling only)")
+    ap.add_argument("--grid-points", type=int, default=0, help="grid points (profiling only; default 1000)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -209,7 +210,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_1010_2438_gb300 import api, capi
+    from paper_1010_2438_gb300 import api, capi, shard
     from paper_1010_2438_gb300 import build as lib_build
     from paper_1010_2438_gb300 import workloads as W
 
@@ -219,11 +220,12 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.device("cuda", torch.cuda.current_device())
     lib_build.build()
-    batch = W.flat32x64(R=args.replicas) if args.replicas else W.flat32x64()
+    batch = W.flat32x64(R=args.replicas or 65536, G=args.grid_points or 1000)
     if args.horizon_scale != 1.0:
         batch = W.Batch(batch.model, batch.rates, batch.init, batch.grid * args.horizon_scale, batch.R, batch.seed,
                         name=batch.name)
     R = batch.R
+    r_off, _ = shard.weak_shard(R, rank)
     cm = api.CompiledModel(batch.model)
     rates, init, grid = api.device_inputs(batch, dev)
     stream = torch.cuda.current_stream()
@@ -232,7 +234,7 @@ def main():
 
     def step(o):
         return api.simulate(cm, rates, init, grid, R, batch.seed, batch.max_events, states=True, traj=True,
-                            layout=args.layout, block_threads=args.threads, replica_offset=rank * R, out=o)
+                            layout=args.layout, block_threads=args.threads, replica_offset=r_off, out=o)
 
     for _ in range(args.warmup):
         out = step(out)
@@ -259,14 +261,7 @@ def main():
     t_total = sum(step_ms) / 1e3
     events = int(out["events"].sum().item())
     statuses = torch.bincount(out["status"].reshape(-1).to(torch.int64), minlength=8).tolist()
-    ev_all, t_max = events * args.steps, t_total
-    if world > 1:
-        tt = torch.tensor([float(ev_all), t_total], dtype=torch.float64, device=dev)
-        ev_t = tt[:1].clone()
-        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
-        tm = tt[1:].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ev_all, t_max = float(ev_t.item()), float(tm.item())
+    ev_all, t_max = shard.combine(events * args.steps, t_total, device=dev)
     value = ev_all / t_max
 
     # roofline of the dominant kernel (the SSA kernel is the whole step but a
@@ -275,7 +270,7 @@ def main():
     kernel_s = t_total / args.steps
     achieved = f_evt * events / kernel_s
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "flat_ssa_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", "flat_ssa_kernel_flat32x64_traffic.txt")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
@@ -296,24 +291,18 @@ def main():
         bufs = {"out": out}
         e2e_steps = min(args.steps, 3)
         api.simulate_host(cm, rates_h, init_h, grid_h, R, batch.seed, batch.max_events, dev_bufs=bufs,
-                          host_out=host_out, replica_offset=rank * R)
+                          host_out=host_out, replica_offset=r_off)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(e2e_steps):
             api.simulate_host(cm, rates_h, init_h, grid_h, R, batch.seed, batch.max_events, dev_bufs=bufs,
-                              host_out=host_out, replica_offset=rank * R)
+                              host_out=host_out, replica_offset=r_off)
         e1.record(stream)
         barrier()
         te = e0.elapsed_time(e1) / 1e3
-        ev_e = float(events * e2e_steps)
-        if world > 1:
-            t2 = torch.tensor([ev_e, te], dtype=torch.float64, device=dev)
-            a_, b_ = t2[:1].clone(), t2[1:].clone()
-            dist.all_reduce(a_, op=dist.ReduceOp.SUM)
-            dist.all_reduce(b_, op=dist.ReduceOp.MAX)
-            ev_e, te = float(a_.item()), float(b_.item())
+        ev_e, te = shard.combine(float(events * e2e_steps), te, device=dev)
         h2d = rates_h.numel() * 8 + init_h.numel() * 4 + grid_h.numel() * 8
         e2e = {"value": ev_e / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": host_out.numel() * 4, "steps": e2e_steps}
@@ -327,8 +316,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD if not (args.replicas or args.horizon_scale != 1.0) else
-                       "%s (profiling case: R=%d, horizon x%g)" % (WORKLOAD, R, args.horizon_scale),
+                "config": {"workload": WORKLOAD if not (args.replicas or args.grid_points or args.horizon_scale != 1.0)
+                       else "%s (profiling case: R=%d, G=%d, horizon x%g)" % (WORKLOAD, R, batch.G, args.horizon_scale),
                        "description": WORKLOAD_DESC, "P": batch.P, "R": R,
                            "G": batch.G, "S": batch.model.n_species, "M": batch.model.n_rules,
                            "events_per_step_per_gpu": events, "statuses": statuses,

@@ -283,3 +283,13 @@ def test_huge_counts_exercise_int64_to_double_rounding():
         o = oracle.simulate(b, log_cap=300)
         assert_same(g, o)
         assert np.array_equal(g["log_t"].view(np.int64), o["log_t"].view(np.int64))
+
+
+def test_replica_offset_shards_reproduce_one_batch():
+    b_full = W.flat8x12(R=96)
+    o = oracle.simulate(b_full)
+    for off, cnt in ((0, 40), (40, 56), (17, 9)):
+        b = W.Batch(b_full.model, b_full.rates, b_full.init, b_full.grid, cnt, b_full.seed)
+        g = gpu_run(b, replica_offset=off)
+        sub = {k: v[off:off + cnt] for k, v in o.items()}
+        assert_same(g, sub)
