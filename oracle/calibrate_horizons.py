@@ -20,6 +20,7 @@ TARGETS = {  # workload -> (constructor, target mean events, replicas used)
     "flat8x12": (W.flat8x12, 1e4, 16),
     "flat32x64": (W.flat32x64, 1e5, 8),
     "flat16x24": (W.flat16x24, 1e4, 16),
+    "cwc3x24": (W.cwc3x24, 1e4, 16),
 }
 
 

@@ -22,6 +22,11 @@ int flat_table_bytes_host(int M, int n_deps);
 int flat_best_threads(const FlatParams& prm, bool queue, bool sens);
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, double* grad, int P, int R, int M, cudaStream_t st);
+cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, cudaStream_t stream);
+cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int T, int* blocks);
+int cwc_best_threads(const CwcParams& prm, bool queue);
+int cwc_table_bytes_host(int M, int n_deps);
+long long cwc_slab_words_host(int S, int L, int C);
 }  // namespace cwcgpu
 
 using namespace cwcgpu;
@@ -35,6 +40,11 @@ struct cwc_model {
   int checked_counts = 0;
   int32_t* d_tables = nullptr;  // [M][RULE_WORDS] followed by [n_deps]
   std::vector<int32_t> h_tables;
+  // compartmentalised compilation
+  int O = 0;
+  int c_n_deps = 0;
+  int32_t* d_ctables = nullptr;  // [M][CWC_RULE_WORDS] followed by [c_n_deps]
+  std::vector<int32_t> h_ctables;
 };
 
 namespace {
@@ -63,9 +73,27 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout: [header 256 B][sums P*G*O int64 if needed][partials Q*M double if needed]
 struct WsLayout {
-  size_t header = 0, sums = 0, partials = 0, total = 0;
+  size_t header = 0, sums = 0, partials = 0, slabs = 0, total = 0;
   bool need_header = false, need_sums = false, need_partials = false;
+  int T = 0, blocks = 0;          // compartmentalised launch shape (its slabs are per thread)
+  long long slab_words = 0;
 };
+
+CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a) {
+  CwcParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.S = m->S;
+  prm.L = m->L;
+  prm.C = m->C;
+  prm.M = m->M;
+  prm.B = m->B;
+  prm.O = m->O;
+  prm.n_deps = m->c_n_deps;
+  prm.Q = (long long)a->P * a->R;
+  prm.smem_table_bytes = cwc_table_bytes_host(m->M, m->c_n_deps);
+  prm.slab_words = cwc_slab_words_host(m->S, m->L, m->C);
+  return prm;
+}
 
 int chosen_layout(const cwc_sim_args* a) { return a->layout == CWC_LAYOUT_AUTO ? CWC_LAYOUT_QUEUE : a->layout; }
 
@@ -87,6 +115,15 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
   if (w.need_partials) {
     w.partials = off;
     off = align256(off + (size_t)a->P * a->R * m->M * sizeof(double));
+  }
+  if (!m->flat) {
+    const CwcParams prm = cwc_shape_params(m, a);
+    const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
+    w.T = a->block_threads > 0 ? a->block_threads : cwc_best_threads(prm, queue);
+    if (cwc_launch_shape(prm, queue, w.T, &w.blocks) != cudaSuccess) w.blocks = 0;
+    w.slab_words = prm.slab_words;
+    w.slabs = off;
+    off = align256(off + (size_t)w.blocks * w.T * (size_t)prm.slab_words * sizeof(int32_t));
   }
   w.total = off;
   return w;
@@ -203,12 +240,109 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
     delete m;
     return cuda_fail(e, "cudaGetDevice");
   }
+  m->O = m->flat ? S : (L * S + (L - 1) * S + L);
+  m->B = (M + 31) / 32;
   if (!m->flat) {
-    delete m;
-    return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
+    if (C > CWC_MAX_SLOTS) {
+      delete m;
+      return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models need max_compartments <= 64");
+    }
+    // ---- compartmentalised compilation ----
+    std::vector<int32_t>& tb = m->h_ctables;
+    tb.assign((size_t)M * CWC_RULE_WORDS, 0);
+    // read and write sets: location key = ((role * L) + label) * S + species, role 0 content, 1 wrap
+    auto key = [&](int role, int lab, int sp) { return ((long long)role * L + lab) * S + sp; };
+    std::vector<std::vector<long long>> reads(M), writes(M);
+    for (int j = 0; j < M; ++j) {
+      const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
+      const int32_t* rhs = d->rhs + (size_t)j * 3 * S;
+      const int kind = d->kind[j], ctx = d->ctx_label[j], ch = d->child_label[j];
+      int32_t* rec = tb.data() + (size_t)j * CWC_RULE_WORDS;
+      rec[CR_KIND] = kind;
+      rec[CR_CTX] = ctx;
+      rec[CR_CHILD] = kind == CWC_RULE_LOCAL ? 0 : ch;
+      int nr = 0;
+      for (int row = 0; row < 3; ++row)
+        for (int s = 0; s < S; ++s)
+          if (lhs[row * S + s] > 0) {
+            rec[CR_REAC + nr++] = s | (lhs[row * S + s] << 16) | (row << 24);
+            const bool child_row = row > 0;
+            reads[j].push_back(key(row == 1 ? 1 : 0, child_row ? ch : ctx, s));
+          }
+      rec[CR_NREAC] = nr;
+      auto put = [&](int base_n, int base_d, int row_delta_only, const int32_t* lo, const int32_t* hi, bool values) -> bool {
+        int k = 0;
+        for (int s = 0; s < S; ++s) {
+          const int dv = values ? hi[s] : hi[s] - lo[s];
+          if (dv == 0) continue;
+          if (k == MAX_DELTA) return false;
+          rec[base_d + k++] = (int32_t)((uint32_t)s | ((uint32_t)(dv & 0xffff) << 16));
+        }
+        rec[base_n] = k;
+        (void)row_delta_only;
+        return true;
+      };
+      bool ok = put(CR_ND0, CR_D0, 0, lhs, rhs, false);
+      if (kind == CWC_RULE_PARENT_CHILD) {
+        ok = ok && put(CR_ND1, CR_D1, 1, lhs + S, rhs + S, false) && put(CR_ND2, CR_D2, 2, lhs + 2 * S, rhs + 2 * S, false);
+      } else if (kind == CWC_RULE_CREATE) {
+        ok = ok && put(CR_ND1, CR_D1, 1, nullptr, rhs + S, true) && put(CR_ND2, CR_D2, 2, nullptr, rhs + 2 * S, true);
+      }
+      if (!ok) {
+        delete m;
+        return fail(CWC_ERR_UNSUPPORTED, "rule " + std::to_string(j) + ": more than 8 species change in one pattern");
+      }
+      for (int k = 0; k < rec[CR_ND0]; ++k) writes[j].push_back(key(0, ctx, rec[CR_D0 + k] & 0xffff));
+      if (kind == CWC_RULE_PARENT_CHILD) {
+        for (int k = 0; k < rec[CR_ND1]; ++k) writes[j].push_back(key(1, ch, rec[CR_D1 + k] & 0xffff));
+        for (int k = 0; k < rec[CR_ND2]; ++k) writes[j].push_back(key(0, ch, rec[CR_D2 + k] & 0xffff));
+      }
+    }
+    std::vector<int32_t> deps_all;
+    for (int j = 0; j < M; ++j) {
+      int32_t* rec = tb.data() + (size_t)j * CWC_RULE_WORDS;
+      rec[CR_DEPOFF] = (int32_t)deps_all.size();
+      uint32_t leafmask = 0, nodemask = 0;
+      int cnt = 0;
+      if (d->kind[j] == CWC_RULE_LOCAL || d->kind[j] == CWC_RULE_PARENT_CHILD) {
+        for (int i = 0; i < M; ++i) {
+          bool hit = false;
+          for (long long w : writes[j])
+            for (long long r : reads[i]) hit |= (w == r);
+          if (!hit) continue;
+          deps_all.push_back(i);
+          ++cnt;
+          const int l = i / m->B;
+          leafmask |= 1u << l;
+          nodemask |= (1u << (l >> 1)) | (1u << (16 + (l >> 2))) | (1u << (24 + (l >> 3))) |
+                      (1u << (28 + (l >> 4))) | (1u << TREE_ROOT);
+        }
+      }
+      rec[CR_DEPCNT] = cnt;
+      rec[CR_LEAFMASK] = (int32_t)leafmask;
+      rec[CR_NODEMASK] = (int32_t)nodemask;
+    }
+    m->c_n_deps = (int)deps_all.size();
+    tb.insert(tb.end(), deps_all.begin(), deps_all.end());
+    if ((size_t)cwc_table_bytes_host(M, m->c_n_deps) + 32ull * (32 + TREE_NODES + M) * 8 > 220 * 1024) {
+      delete m;
+      return fail(CWC_ERR_UNSUPPORTED, "model too large for one block of 32 trajectories in shared memory");
+    }
+    e = cudaMalloc(&m->d_ctables, tb.size() * sizeof(int32_t));
+    if (e != cudaSuccess) {
+      delete m;
+      return cuda_fail(e, "cudaMalloc(model tables)");
+    }
+    e = cudaMemcpy(m->d_ctables, tb.data(), tb.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(m->d_ctables);
+      delete m;
+      return cuda_fail(e, "cudaMemcpy(model tables)");
+    }
+    *out = m;
+    return CWC_OK;
   }
   // ---- flat compilation ----
-  m->B = (M + 31) / 32;
   for (int j = 0; j < M; ++j) {
     int order = 0;
     for (int s = 0; s < S; ++s) order += d->lhs[(size_t)j * 3 * S + s];
@@ -304,13 +438,13 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
 void cwc_model_destroy(cwc_model* m) {
   if (m == nullptr) return;
   if (m->d_tables) cudaFree(m->d_tables);
+  if (m->d_ctables) cudaFree(m->d_ctables);
   delete m;
 }
 
 int32_t cwc_model_num_observables(const cwc_model* m) {
   if (m == nullptr) return -1;
-  if (m->flat) return m->S;
-  return m->L * m->S + (m->L - 1) * m->S + m->L;
+  return m->O;
 }
 
 cwc_status cwc_simulate_workspace_size(const cwc_model* m, const cwc_sim_args* a, size_t* bytes) {
@@ -390,6 +524,8 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
   return CWC_OK;
 }
 
+static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_t st);
+
 // Scratch of cwc_simulate_noalloc: one statically sized array per device that
 // loads the library.  In host code its name is only a stand-in; the device
 // address comes from cudaGetSymbolAddress, looked up once per device with
@@ -415,7 +551,6 @@ cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void*
   g_last_error.clear();
   cwc_status st = check_sim_args(m, a);  // also checks that m's device is the current one
   if (st != CWC_OK) return st;
-  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
   const WsLayout w = ws_layout(m, a, false, false);
   if (w.total > CWC_NOALLOC_SCRATCH_BYTES)
     return fail(CWC_ERR_INVALID_ARG, "this call needs " + std::to_string(w.total) +
@@ -428,14 +563,71 @@ cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void*
   cwc_sim_args b = *a;
   b.workspace = scratch;
   b.workspace_bytes = CWC_NOALLOC_SCRATCH_BYTES;
+  if (!m->flat) return run_cwc(m, &b, static_cast<cudaStream_t>(stream));
   return run_flat(m, &b, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_t st) {
+  const WsLayout w = ws_layout(m, a, false, false);
+  if (w.blocks < 1) return fail(CWC_ERR_CUDA, "could not size the compartmentalised launch");
+  if (a->workspace == nullptr || a->workspace_bytes < w.total)
+    return fail(CWC_ERR_WORKSPACE, "workspace of " + std::to_string(w.total) + " bytes required");
+  if ((reinterpret_cast<uintptr_t>(a->workspace) & 255) != 0)
+    return fail(CWC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  unsigned char* ws = static_cast<unsigned char*>(a->workspace);
+  CwcParams prm = cwc_shape_params(m, a);
+  prm.rules = m->d_ctables;
+  prm.P = a->P;
+  prm.R = a->R;
+  prm.G = a->G;
+  prm.Pi = a->Pi;
+  prm.r_offset = a->replica_offset;
+  prm.rates = a->rates;
+  prm.init = a->init;
+  prm.grid = a->grid;
+  prm.key0 = (uint32_t)a->seed;
+  prm.key1 = (uint32_t)(a->seed >> 32);
+  prm.max_events = a->max_events;
+  prm.deadline_ns = a->deadline_ns;
+  prm.states = a->states;
+  prm.traj_status = a->traj_status;
+  prm.traj_events = reinterpret_cast<long long*>(a->traj_events);
+  prm.traj_hash = reinterpret_cast<unsigned long long*>(a->traj_hash);
+  prm.traj_final_t = a->traj_final_t;
+  prm.log_cap = a->log_cap;
+  prm.log_rule = a->log_rule;
+  prm.log_slot = a->log_slot;
+  prm.log_t = a->log_t;
+  prm.slabs = reinterpret_cast<int32_t*>(ws + w.slabs);
+  cudaError_t e;
+  if (w.need_header) {
+    prm.ws = reinterpret_cast<WorkspaceHeader*>(ws + w.header);
+    e = cudaMemsetAsync(prm.ws, 0, sizeof(WorkspaceHeader), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
+  }
+  unsigned long long* sums = reinterpret_cast<unsigned long long*>(a->sums);
+  if (w.need_sums) sums = reinterpret_cast<unsigned long long*>(ws + w.sums);
+  prm.sums = sums;
+  if (sums != nullptr) {
+    e = cudaMemsetAsync(sums, 0, (size_t)a->P * a->G * m->O * sizeof(long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sums)");
+  }
+  const LogConstants lc = make_log_constants();
+  const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
+  e = launch_cwc(prm, lc, queue, w.T, w.blocks, st);
+  if (e != cudaSuccess) return cuda_fail(e, "CWC SSA kernel launch");
+  if (a->means != nullptr) {
+    e = launch_means(sums, a->means, (long long)a->P * a->G * m->O, a->R, st);
+    if (e != cudaSuccess) return cuda_fail(e, "means kernel launch");
+  }
+  return CWC_OK;
 }
 
 cwc_status cwc_simulate(const cwc_model* m, const cwc_sim_args* a, void* stream) {
   g_last_error.clear();
   cwc_status st = check_sim_args(m, a);
   if (st != CWC_OK) return st;
-  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
+  if (!m->flat) return run_cwc(m, a, static_cast<cudaStream_t>(stream));
   return run_flat(m, a, nullptr, static_cast<cudaStream_t>(stream));
 }
 
@@ -445,7 +637,7 @@ cwc_status cwc_sensitivity(const cwc_model* m, const cwc_sim_args* a, const cwc_
   if (st != CWC_OK) return st;
   if (s == nullptr || s->means == nullptr || s->grad_means == nullptr || s->grad_rates == nullptr)
     return fail(CWC_ERR_INVALID_ARG, "means, grad_means and grad_rates must not be NULL");
-  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "compartmentalised models are not compiled by this build");
+  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "sensitivities are implemented for flat models only");
   return run_flat(m, a, s, static_cast<cudaStream_t>(stream));
 }
 

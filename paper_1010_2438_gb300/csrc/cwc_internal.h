@@ -30,6 +30,21 @@ constexpr int R_NREAC = 0, R_REAC = 1, R_NDELTA = 5, R_DELTA = 6, R_DEPOFF = 14,
 constexpr int TREE_NODES = 31;
 constexpr int TREE_ROOT = 30;
 
+// Per-rule record of a compiled compartmentalised model, CWC_RULE_WORDS words:
+//   [0] kind  [1] context label  [2] child label  [3] number of reactant entries
+//   [4..7]   reactant: species | nu << 16 | row << 24 (row 0 = context / parent
+//            content, 1 = child wrap, 2 = child content), rows then species ascending
+//   [8]  n0, [9..16]   changes of the context (parent) content: species | delta << 16
+//   [17] n1, [18..25]  PARENT_CHILD: changes of the child wrap; CREATE: the new wrap
+//   [26] n2, [27..34]  PARENT_CHILD: changes of the child content; CREATE: the new content
+//   [35] offset and [36] number of dependents (rules reading a location this rule
+//        writes; unused for CREATE / DISSOLVE, after which every rule is recomputed)
+//   [37] dirty-leaf mask, [38] dirty-node mask of those dependents
+constexpr int CWC_RULE_WORDS = 40;
+constexpr int CR_KIND = 0, CR_CTX = 1, CR_CHILD = 2, CR_NREAC = 3, CR_REAC = 4, CR_ND0 = 8, CR_D0 = 9, CR_ND1 = 17,
+              CR_D1 = 18, CR_ND2 = 26, CR_D2 = 27, CR_DEPOFF = 35, CR_DEPCNT = 36, CR_LEAFMASK = 37, CR_NODEMASK = 38;
+constexpr int CWC_MAX_SLOTS = 64;
+
 // Trajectory status codes (same values as CWC_TRAJ_* in the C header).
 enum : int32_t {
   TS_OK = 0, TS_ABSORBED = 1, TS_INT_OVERFLOW = 2, TS_PROP_OVERFLOW = 3, TS_CAPACITY = 4,
@@ -81,6 +96,36 @@ struct FlatParams {
   WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)
   long long deadline_ns;
   int smem_table_bytes;            // bytes of the shared-memory table region
+};
+
+// Everything one compartmentalised-model launch needs.
+struct CwcParams {
+  int S, L, C, M, B, O;
+  int n_deps;
+  const int32_t* rules;     // [M][CWC_RULE_WORDS] then [n_deps]
+  int P, R, G, Pi;
+  uint32_t r_offset;
+  long long Q;
+  const double* rates;      // [P][M]
+  const int32_t* init;      // [Pi][C][3 + 2S]
+  const double* grid;       // [G]
+  uint32_t key0, key1;
+  long long max_events;
+  int32_t* states;                 // [Q][G][O]
+  unsigned long long* sums;        // [P][G][O]
+  int32_t* traj_status;
+  long long* traj_events;
+  unsigned long long* traj_hash;
+  double* traj_final_t;
+  int log_cap;
+  int32_t* log_rule;
+  int32_t* log_slot;
+  double* log_t;
+  int32_t* slabs;                  // per launched thread, slab_words each
+  long long slab_words;
+  WorkspaceHeader* ws;
+  long long deadline_ns;
+  int smem_table_bytes;
 };
 
 }  // namespace cwcgpu

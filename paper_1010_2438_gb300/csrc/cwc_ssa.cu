@@ -1,0 +1,705 @@
+// Compartmentalised CWC terms (Sec. 2.1) under Gillespie's direct method
+// (Sec. 2.2) with the Match / Resolve / Update step of Sec. 2.3 and Fig.
+// "CWC simulator pseudo-code": rule choice by the FP64 propensity tree, then
+// the stochastic choice of the context (compartment) inside the rule, then the
+// rewrite, including transport between a compartment and its parent, binding
+// to the wrap, creation and dissolution of compartments.
+//
+// One thread per trajectory, so the FP64 part (logarithm, tau, tree) keeps
+// every lane busy.  Shared memory per thread, [index][thread]-strided: the 32
+// FP64 leaves and 31 internal nodes of the rule tree and the int64 totals H_j
+// (combinatorial counts summed over the rule's contexts; a_j = k_j * H_j).
+// The term itself (C <= 64 slots x S species, content and wrap) lives in a
+// per-thread slab of the caller's workspace, reused across the trajectories a
+// thread runs:
+//   chmask[C]  u64  children of each slot        labmask[L] u64  alive slots per label
+//   alive      u64  alive slots                  meta[C]    i32  label | (parent + 1) << 8
+//   wrap[C][S], content[C][S]  i32
+// After an event, the totals H_i of the rules that read a location (content
+// or wrap of a label, a species) the fired rule wrote are recomputed from
+// scratch over their contexts (all rules after CREATE / DISSOLVE), so H is
+// always exactly the sum the oracle re-matches every step.
+#include <cuda_runtime.h>
+
+#include "cwc_internal.h"
+#include "ssa_device.cuh"
+
+namespace cwcgpu {
+
+__device__ __forceinline__ long long cwc_grab_next(WorkspaceHeader* ws) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(&ws->queue_next, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return (long long)(base + (unsigned long long)__popc(mask & ((1u << lane) - 1u)));
+}
+
+__host__ __device__ inline int cwc_table_bytes(int M, int n_deps) {
+  int words = M * CWC_RULE_WORDS + n_deps;
+  return ((words * 4 + 15) / 16) * 16 + 54 * 8;
+}
+
+__host__ __device__ inline int cwc_thread_bytes(int M) { return (32 + TREE_NODES + M) * 8; }
+
+__host__ __device__ inline long long cwc_slab_words(int S, int L, int C) {
+  long long w = 2LL * C + 2LL * L + 2 + C + 2LL * C * S;
+  return (w + 31) / 32 * 32;
+}
+
+template <bool kQueue>
+__global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ CwcParams prm,
+                                                      const __grid_constant__ LogConstants lc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x;
+  const int tid = threadIdx.x;
+  const int S = prm.S, L = prm.L, C = prm.C, M = prm.M, B = prm.B, G = prm.G, O = prm.O;
+
+  int32_t* s_rules = reinterpret_cast<int32_t*>(smem);
+  int32_t* s_deps = s_rules + M * CWC_RULE_WORDS;
+  const int tbl_words = M * CWC_RULE_WORDS + prm.n_deps;
+  double* s_eln2 = reinterpret_cast<double*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
+  double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
+  double* leaf = dbase + tid;                                     // [32][T]
+  double* node = dbase + 32 * T + tid;                            // [31][T]
+  unsigned long long* Hs = reinterpret_cast<unsigned long long*>(dbase + (32 + TREE_NODES) * T) + tid;  // [M][T]
+
+#define LEAF(l) leaf[(l) * T]
+#define NODE(i) node[(i) * T]
+#define HV(i) Hs[(i) * T]
+
+  for (int i = tid; i < tbl_words; i += T) s_rules[i] = prm.rules[i];
+  for (int i = tid; i < 54; i += T) s_eln2[i] = lc.e_ln2[i];
+  bool bad_grid = false;
+  for (int g = tid; g < G; g += T) {
+    const double v = prm.grid[g];
+    if ((dbits(v) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) bad_grid = true;
+    if (g == 0 && !(v >= 0.0)) bad_grid = true;
+    if (g > 0 && !(v > prm.grid[g - 1])) bad_grid = true;
+  }
+  __shared__ unsigned long long s_deadline;
+  if (tid == 0) {
+    unsigned long long dl = ~0ull;
+    if (prm.deadline_ns > 0) {
+      const unsigned long long now = globaltimer_ns();
+      unsigned long long start = now;
+      if (prm.ws != nullptr) {
+        const unsigned long long prev = atomicCAS(&prm.ws->t_start_ns, 0ull, now);
+        start = prev == 0ull ? now : prev;
+      }
+      dl = start + (unsigned long long)prm.deadline_ns;
+    }
+    s_deadline = dl;
+  }
+  bad_grid = __syncthreads_or(bad_grid);
+  const unsigned long long deadline = s_deadline;
+  const long long T_bits = dbits(prm.grid[G - 1]);
+
+  // this thread's slab of the term
+  const long long gthread = (long long)blockIdx.x * T + tid;
+  int32_t* slab = prm.slabs + gthread * prm.slab_words;
+  unsigned long long* chmask = reinterpret_cast<unsigned long long*>(slab);       // [C]
+  unsigned long long* labmask = chmask + C;                                       // [L]
+  unsigned long long* alive_p = labmask + L;                                      // [1]
+  int32_t* meta = reinterpret_cast<int32_t*>(alive_p + 1);                        // [C]
+  int32_t* wrap = meta + C;                                                       // [C][S]
+  int32_t* content = wrap + (size_t)C * S;                                        // [C][S]
+
+  auto LABEL = [&](int c) -> int { return meta[c] & 0xff; };
+  auto PARENT = [&](int c) -> int { return (meta[c] >> 8) - 1; };
+
+  long long q = 0;
+  int p = 0, r = 0;
+  const double* kp = nullptr;
+  double t = 0.0;
+  unsigned int n = 0;
+  int gi = 0;
+  long long gbits = 0;
+  unsigned long long h = FNV_OFFSET;
+  bool ovf = false;
+  int status = TS_OK;
+  const long long Q = prm.Q;
+  const long long qstride = (long long)gridDim.x * T;
+  bool first = true;
+
+  // product of binomials of the reactants of `row` over the multiset x
+  auto pattern = [&](const int32_t* rec, int row, const int32_t* x, unsigned long long acc) -> unsigned long long {
+    const int nr = rec[CR_NREAC];
+    for (int a = 0; a < nr; ++a) {
+      const int v = rec[CR_REAC + a];
+      if (((v >> 24) & 3) != row) continue;
+      acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &ovf);
+    }
+    return acc;
+  };
+  // combinatorial count of rule i at context slot c (c is the context for
+  // LOCAL / CREATE, the child for PARENT_CHILD / DISSOLVE)
+  auto count_at = [&](const int32_t* rec, int c) -> unsigned long long {
+    const int kind = rec[CR_KIND];
+    if (kind == 0 || kind == 2) return pattern(rec, 0, content + (size_t)c * S, 1ull);
+    const int qq = PARENT(c);
+    unsigned long long acc = pattern(rec, 0, content + (size_t)qq * S, 1ull);
+    acc = pattern(rec, 1, wrap + (size_t)c * S, acc);
+    return pattern(rec, 2, content + (size_t)c * S, acc);
+  };
+  // candidate contexts of rule i, in ascending slot order
+  auto ctx_mask = [&](const int32_t* rec) -> unsigned long long {
+    const int kind = rec[CR_KIND];
+    return (kind == 0 || kind == 2) ? labmask[rec[CR_CTX]] : labmask[rec[CR_CHILD]];
+  };
+  auto ctx_ok = [&](const int32_t* rec, int c) -> bool {
+    const int kind = rec[CR_KIND];
+    if (kind == 0 || kind == 2) return true;
+    return LABEL(PARENT(c)) == rec[CR_CTX];
+  };
+  // H_i from scratch: sum over contexts (ascending slots), overflow-checked
+  auto total_h = [&](int i) -> unsigned long long {
+    const int32_t* rec = s_rules + i * CWC_RULE_WORDS;
+    unsigned long long m = ctx_mask(rec);
+    unsigned long long tot = 0ull;
+    while (m) {
+      const int c = __ffsll((long long)m) - 1;
+      m &= m - 1ull;
+      if (!ctx_ok(rec, c)) continue;
+      const unsigned long long hc = count_at(rec, c);
+      const unsigned long long s2 = tot + hc;
+      if (s2 < tot || (s2 >> 63) != 0ull) ovf = true;
+      tot = s2;
+    }
+    return tot;
+  };
+  auto prop_of = [&](int i) -> double { return __dmul_rn(kp[i], u63_to_double_rn(HV(i))); };
+  auto leaf_sum = [&](int l) -> double {
+    const int j0 = l * B, j1 = min(j0 + B, M);
+    double s = j0 < M ? prop_of(j0) : 0.0;
+    for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, prop_of(jj));
+    return s;
+  };
+  auto rebuild_tree = [&]() {
+    for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
+    for (int nd = 0; nd < TREE_NODES; ++nd) {
+      const double a = nd < 16 ? LEAF(2 * nd) : NODE(2 * nd - 32);
+      const double b = nd < 16 ? LEAF(2 * nd + 1) : NODE(2 * nd - 31);
+      NODE(nd) = __dadd_rn(a, b);
+    }
+  };
+
+  auto record = [&](int g) {
+    int32_t* dst = prm.states != nullptr ? prm.states + ((size_t)q * G + g) * O : nullptr;
+    unsigned long long* sdst = prm.sums != nullptr ? prm.sums + ((size_t)p * G + g) * O : nullptr;
+    auto emit = [&](int o, long long v) {
+      const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
+      if (dst) dst[o] = sv;
+      if (sdst) atomicAdd(sdst + o, (unsigned long long)(long long)sv);
+    };
+    for (int l = 0; l < L; ++l) {
+      for (int x = 0; x < S; ++x) {
+        long long v = 0;
+        unsigned long long m = labmask[l];
+        while (m) {
+          const int c = __ffsll((long long)m) - 1;
+          m &= m - 1ull;
+          v += content[(size_t)c * S + x];
+        }
+        emit(l * S + x, v);
+      }
+    }
+    for (int l = 1; l < L; ++l) {
+      for (int x = 0; x < S; ++x) {
+        long long v = 0;
+        unsigned long long m = labmask[l];
+        while (m) {
+          const int c = __ffsll((long long)m) - 1;
+          m &= m - 1ull;
+          v += wrap[(size_t)c * S + x];
+        }
+        emit(L * S + (l - 1) * S + x, v);
+      }
+    }
+    for (int l = 0; l < L; ++l) emit(L * S + (L - 1) * S + l, __popcll(labmask[l]));
+  };
+  auto fill = [&]() {
+    for (; gi < G; ++gi) record(gi);
+  };
+
+  auto finalize = [&]() {
+    if (prm.traj_status) prm.traj_status[q] = status;
+    if (prm.traj_events) prm.traj_events[q] = (long long)n;
+    if (prm.traj_hash) prm.traj_hash[q] = h;
+    if (prm.traj_final_t) prm.traj_final_t[q] = t;
+  };
+
+  // load and validate the initial term (slot image), build masks, H and tree
+  auto start = [&]() -> bool {
+    p = (int)(q / prm.R);
+    r = (int)(q - (long long)p * prm.R);
+    kp = prm.rates + (size_t)p * M;
+    t = 0.0;
+    n = 0u;
+    gi = 0;
+    gbits = dbits(prm.grid[0]);
+    h = FNV_OFFSET;
+    ovf = false;
+    status = TS_OK;
+    bool bad = bad_grid;
+    for (int j = 0; j < M; ++j) {
+      const long long kb = dbits(kp[j]);
+      if (!(kb > 0 && kb < 0x7FF0000000000000ll)) bad = true;
+    }
+    const int W = 3 + 2 * S;
+    const int32_t* img = prm.init + (size_t)(prm.Pi == 1 ? 0 : p) * C * W;
+    unsigned long long alive = 0ull;
+    for (int l = 0; l < L; ++l) labmask[l] = 0ull;
+    for (int c = 0; c < C; ++c) {
+      chmask[c] = 0ull;
+      const int32_t* row = img + (size_t)c * W;
+      const int a = row[0];
+      if (a != 0 && a != 1) bad = true;
+      if (a == 1) {
+        const int lab = row[1], par = row[2];
+        if (c == 0 && (lab != 0 || par != -1)) bad = true;
+        if (c > 0 && (lab < 1 || lab >= L || par < 0 || par >= C)) bad = true;
+        for (int x = 0; x < S; ++x) {
+          const int wv = row[3 + x], cv = row[3 + S + x];
+          if (wv < 0 || cv < 0) bad = true;
+          if (c == 0 && wv != 0) bad = true;
+          wrap[(size_t)c * S + x] = wv;
+          content[(size_t)c * S + x] = cv;
+        }
+        alive |= 1ull << c;
+        meta[c] = (lab & 0xff) | ((par + 1) << 8);
+      } else {
+        meta[c] = 0;
+        for (int x = 0; x < S; ++x) {
+          wrap[(size_t)c * S + x] = 0;
+          content[(size_t)c * S + x] = 0;
+        }
+      }
+    }
+    if (!(alive & 1ull)) bad = true;
+    if (!bad) {
+      // every alive slot's parent chain reaches the root through alive slots
+      for (int c = 1; c < C && !bad; ++c) {
+        if (!((alive >> c) & 1ull)) continue;
+        int qq = c, steps = 0;
+        while (qq != 0) {
+          qq = PARENT(qq);
+          if (qq < 0 || qq >= C || !((alive >> qq) & 1ull) || ++steps > C) {
+            bad = true;
+            break;
+          }
+        }
+      }
+    }
+    if (bad) {
+      status = TS_BAD_INPUT;
+      if (prm.states != nullptr) {
+        int32_t* dst = prm.states + (size_t)q * G * O;
+        for (long long e = 0; e < (long long)G * O; ++e) dst[e] = 0;
+      }
+      return true;
+    }
+    *alive_p = alive;
+    for (int c = 0; c < C; ++c) {
+      if (!((alive >> c) & 1ull)) continue;
+      labmask[LABEL(c)] |= 1ull << c;
+      if (c > 0) chmask[PARENT(c)] |= 1ull << c;
+    }
+    for (int i = 0; i < M; ++i) HV(i) = total_h(i);
+    rebuild_tree();
+    return false;
+  };
+
+  auto fits_add = [](int32_t v, int d) -> bool {
+    const long long s = (long long)v + d;
+    return s >= 0 && s <= 0x7FFFFFFFll;
+  };
+
+  // the rewrite of rule j at context c; returns a status (TS_OK on success)
+  auto apply = [&](const int32_t* rec, int c) -> int {
+    const int kind = rec[CR_KIND];
+    const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
+    if (kind == 0) {
+      int32_t* x = content + (size_t)c * S;
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        x[v & 0xffff] += v >> 16;
+      }
+      return TS_OK;
+    }
+    if (kind == 1) {
+      const int qq = PARENT(c);
+      int32_t* xp = content + (size_t)qq * S;
+      int32_t* w = wrap + (size_t)c * S;
+      int32_t* xc = content + (size_t)c * S;
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      for (int d = 0; d < nd1; ++d) {
+        const int v = rec[CR_D1 + d];
+        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      for (int d = 0; d < nd2; ++d) {
+        const int v = rec[CR_D2 + d];
+        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        xp[v & 0xffff] += v >> 16;
+      }
+      for (int d = 0; d < nd1; ++d) {
+        const int v = rec[CR_D1 + d];
+        w[v & 0xffff] += v >> 16;
+      }
+      for (int d = 0; d < nd2; ++d) {
+        const int v = rec[CR_D2 + d];
+        xc[v & 0xffff] += v >> 16;
+      }
+      return TS_OK;
+    }
+    if (kind == 2) {
+      const unsigned long long alive = *alive_p;
+      const unsigned long long freeslots = ~alive & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
+      if (freeslots == 0ull) return TS_CAPACITY;
+      const int e = __ffsll((long long)freeslots) - 1;
+      int32_t* x = content + (size_t)c * S;
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        x[v & 0xffff] += v >> 16;
+      }
+      int32_t* we = wrap + (size_t)e * S;
+      int32_t* xe = content + (size_t)e * S;
+      for (int s = 0; s < S; ++s) {
+        we[s] = 0;
+        xe[s] = 0;
+      }
+      for (int d = 0; d < nd1; ++d) {
+        const int v = rec[CR_D1 + d];
+        we[v & 0xffff] = v >> 16;
+      }
+      for (int d = 0; d < nd2; ++d) {
+        const int v = rec[CR_D2 + d];
+        xe[v & 0xffff] = v >> 16;
+      }
+      const int lab = rec[CR_CHILD];
+      meta[e] = lab | ((c + 1) << 8);
+      chmask[e] = 0ull;
+      chmask[c] |= 1ull << e;
+      labmask[lab] |= 1ull << e;
+      *alive_p = alive | (1ull << e);
+      return TS_OK;
+    }
+    // DISSOLVE: matched atoms rewritten, the rest of the wrap and content go
+    // to the parent, children are reparented, the slot is freed
+    {
+      const int qq = PARENT(c);
+      int32_t* xp = content + (size_t)qq * S;
+      int32_t* w = wrap + (size_t)c * S;
+      int32_t* xc = content + (size_t)c * S;
+      // per-species change of the parent content: (rhs0 - lhs0) + (w - lhs1) + (xc - lhs2)
+      auto delta_at = [&](int s) -> long long {
+        long long dv = (long long)w[s] + xc[s];
+        for (int d = 0; d < nd0; ++d) {
+          const int v = rec[CR_D0 + d];
+          if ((v & 0xffff) == s) dv += v >> 16;
+        }
+        const int nr = rec[CR_NREAC];
+        for (int a = 0; a < nr; ++a) {
+          const int v = rec[CR_REAC + a];
+          const int row = (v >> 24) & 3;
+          if (row != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
+        }
+        return dv;
+      };
+      for (int s = 0; s < S; ++s) {
+        const long long nv = (long long)xp[s] + delta_at(s);
+        if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
+      }
+      for (int s = 0; s < S; ++s) xp[s] = (int32_t)((long long)xp[s] + delta_at(s));
+      unsigned long long kids = chmask[c];
+      while (kids) {
+        const int e = __ffsll((long long)kids) - 1;
+        kids &= kids - 1ull;
+        meta[e] = (meta[e] & 0xff) | ((qq + 1) << 8);
+      }
+      chmask[qq] = (chmask[qq] | chmask[c]) & ~(1ull << c);
+      chmask[c] = 0ull;
+      labmask[LABEL(c)] &= ~(1ull << c);
+      *alive_p &= ~(1ull << c);
+      meta[c] = 0;
+      for (int s = 0; s < S; ++s) {
+        w[s] = 0;
+        xc[s] = 0;
+      }
+      return TS_OK;
+    }
+  };
+
+  auto step = [&]() -> bool {
+    if (ovf) {
+      status = TS_PROP_OVERFLOW;
+      fill();
+      return true;
+    }
+    if ((long long)n == prm.max_events) {
+      status = TS_EVENT_LIMIT;
+      fill();
+      return true;
+    }
+    const double a0 = NODE(TREE_ROOT);
+    const long long a0b = dbits(a0);
+    if (a0b == 0) {
+      status = TS_ABSORBED;
+      fill();
+      return true;
+    }
+    if (a0b >= 0x7FF0000000000000ll) {
+      status = TS_PROP_OVERFLOW;
+      fill();
+      return true;
+    }
+    if ((n & 1023u) == 0u && deadline != ~0ull && globaltimer_ns() > deadline) {
+      status = TS_TIMEOUT;
+      fill();
+      return true;
+    }
+    const uint32_t rr = (uint32_t)r + prm.r_offset;
+    const uint4 w = philox4x32_10(make_uint4(n, 0u, rr, (uint32_t)p), prm.key0, prm.key1);
+    const double u_tau = uniform52(w.x, w.y);
+    const double u_sel = uniform52(w.z, w.w);
+    const double tau = __ddiv_rn(-log_fixed(u_tau, lc.c, s_eln2), a0);
+    const double tn = __dadd_rn(t, tau);
+    const long long tnb = dbits(tn);
+    while (gi < G && gbits < tnb) {
+      record(gi);
+      ++gi;
+      if (gi < G) gbits = dbits(prm.grid[gi]);
+    }
+    if (tnb > T_bits) {
+      status = TS_OK;
+      return true;
+    }
+    // 1. rule: guarded descent of x = u_sel * a0
+    double x = __dmul_rn(u_sel, a0);
+    int nd = TREE_ROOT;
+#pragma unroll
+    for (int lvl = 5; lvl >= 2; --lvl) {
+      const double Lv = NODE(2 * nd - 32);
+      const double Rv = NODE(2 * nd - 31);
+      const bool left = dbits(x) < dbits(Lv) || dbits(Rv) == 0;
+      const double xr = __dadd_rn(x, -Lv);
+      x = left ? x : xr;
+      nd = left ? 2 * nd - 32 : 2 * nd - 31;
+    }
+    int l;
+    {
+      const double Lv = LEAF(2 * nd);
+      const double Rv = LEAF(2 * nd + 1);
+      const bool left = dbits(x) < dbits(Lv) || dbits(Rv) == 0;
+      const double xr = __dadd_rn(x, -Lv);
+      x = left ? x : xr;
+      l = left ? 2 * nd : 2 * nd + 1;
+    }
+    int j;
+    if (B == 1) {
+      j = l;
+    } else {
+      const int j0 = l * B, j1 = min(j0 + B, M);
+      int last = -1;
+      j = -1;
+      double s = 0.0;
+      for (int jj = j0; jj < j1; ++jj) {
+        if (HV(jj) != 0ull) {
+          const double a = prop_of(jj);
+          s = last < 0 ? a : __dadd_rn(s, a);
+          last = jj;
+          if (dbits(x) < dbits(s)) {
+            j = jj;
+            break;
+          }
+        }
+      }
+      if (j < 0) j = last;
+    }
+    j = min(max(j, 0), M - 1);
+    const int32_t* rec = s_rules + j * CWC_RULE_WORDS;
+    // 2. context: integer draw xc in [0, H_j), first context whose running count exceeds it
+    const uint4 w1 = philox4x32_10(make_uint4(n, 1u, rr, (uint32_t)p), prm.key0, prm.key1);
+    const unsigned long long Wd = (unsigned long long)w1.x | ((unsigned long long)w1.y << 32);
+    const unsigned long long xc = __umul64hi(Wd, HV(j));
+    int ctx = -1;
+    {
+      unsigned long long m = ctx_mask(rec);
+      unsigned long long cum = 0ull;
+      int lastc = -1;
+      while (m) {
+        const int c = __ffsll((long long)m) - 1;
+        m &= m - 1ull;
+        if (!ctx_ok(rec, c)) continue;
+        const unsigned long long hc = count_at(rec, c);
+        if (hc == 0ull) continue;
+        lastc = c;
+        cum += hc;
+        if (xc < cum) {
+          ctx = c;
+          break;
+        }
+      }
+      if (ctx < 0) ctx = lastc;
+      if (ctx < 0) ctx = 0;  // unreachable: H_j > 0 has a context with h > 0
+    }
+    // 3. update
+    const int ast = apply(rec, ctx);
+    if (ast != TS_OK) {
+      status = ast;
+      fill();
+      return true;
+    }
+    const bool structural = rec[CR_KIND] >= 2;
+    if (structural) {
+      for (int i = 0; i < M; ++i) HV(i) = total_h(i);
+      rebuild_tree();
+    } else {
+      const int doff = rec[CR_DEPOFF], dcnt = rec[CR_DEPCNT];
+      for (int e = 0; e < dcnt; ++e) {
+        const int i = s_deps[doff + e];
+        HV(i) = total_h(i);
+      }
+      if (B == 1) {
+        for (int e = 0; e < dcnt; ++e) {
+          const int i = s_deps[doff + e];
+          LEAF(i) = prop_of(i);
+        }
+      } else {
+        unsigned lm = (unsigned)rec[CR_LEAFMASK];
+        while (lm) {
+          const int ll = __ffs(lm) - 1;
+          lm &= lm - 1u;
+          LEAF(ll) = leaf_sum(ll);
+        }
+      }
+      unsigned nm = (unsigned)rec[CR_NODEMASK];
+      while (nm) {
+        const int k = __ffs(nm) - 1;
+        nm &= nm - 1u;
+        const double a = k < 16 ? LEAF(2 * k) : NODE(2 * k - 32);
+        const double b = k < 16 ? LEAF(2 * k + 1) : NODE(2 * k - 31);
+        NODE(k) = __dadd_rn(a, b);
+      }
+    }
+    if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
+      const size_t at = (size_t)q * prm.log_cap + n;
+      prm.log_rule[at] = j;
+      if (prm.log_slot) prm.log_slot[at] = ctx;
+      if (prm.log_t) prm.log_t[at] = tn;
+    }
+    t = tn;
+    ++n;
+    h = fnv1a_event(h, (uint32_t)j, (uint32_t)ctx);
+    return false;
+  };
+
+  bool need_new = true;
+  for (;;) {
+    if (need_new) {
+      if (kQueue) {
+        q = cwc_grab_next(prm.ws);
+      } else {
+        q = first ? gthread : q + qstride;
+        first = false;
+      }
+      if (q >= Q) break;
+      if (start()) {
+        finalize();
+        continue;
+      }
+      need_new = false;
+    }
+    if (step()) {
+      finalize();
+      need_new = true;
+    }
+  }
+#undef LEAF
+#undef NODE
+#undef HV
+}
+
+// ---------------------------------------------------------------------------
+
+template <bool kQueue>
+static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, size_t* smem_out) {
+  auto kern = cwc_ssa_kernel<kQueue>;
+  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * cwc_thread_bytes(prm.M);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = (long long)sms * per_sm;
+  const long long need = (prm.Q + T - 1) / T;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  *blocks_out = (int)blocks;
+  *smem_out = smem;
+  return cudaSuccess;
+}
+
+// Launch shape (threads per block, blocks): both layouts use a grid of at most
+// the resident capacity, so the term slabs number threads, not trajectories.
+cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int T, int* blocks) {
+  size_t smem = 0;
+  return queue ? cwc_config_t<true>(prm, T, blocks, &smem) : cwc_config_t<false>(prm, T, blocks, &smem);
+}
+
+int cwc_best_threads(const CwcParams& prm, bool queue) {
+  int best_T = 32, best_warps = -1;
+  for (int T = 32; T <= 256; T += 32) {
+    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * cwc_thread_bytes(prm.M);
+    if (smem > 227 * 1024) break;
+    int per_sm = 0;
+    cudaError_t e = queue ? cudaFuncSetAttribute(cwc_ssa_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(cwc_ssa_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) break;
+    e = queue ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<true>, T, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<false>, T, smem);
+    if (e != cudaSuccess) break;
+    const int warps = per_sm * T / 32;
+    if (warps >= best_warps) {
+      best_warps = warps;
+      best_T = T;
+    }
+  }
+  return best_T;
+}
+
+int cwc_table_bytes_host(int M, int n_deps) { return cwc_table_bytes(M, n_deps); }
+long long cwc_slab_words_host(int S, int L, int C) { return cwc_slab_words(S, L, C); }
+
+cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks,
+                       cudaStream_t stream) {
+  size_t smem = 0;
+  int b = 0;
+  cudaError_t e = queue ? cwc_config_t<true>(prm, T, &b, &smem) : cwc_config_t<false>(prm, T, &b, &smem);
+  if (e != cudaSuccess) return e;
+  if (queue)
+    cwc_ssa_kernel<true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  else
+    cwc_ssa_kernel<false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  return cudaGetLastError();
+}
+
+}  // namespace cwcgpu

@@ -405,3 +405,121 @@ def heterodimer() -> Model:
 def paper_example_rule() -> Model:
     """The worked example of Sec. 2.2: l: a b X -> c X (species a=0, b=1, c=2)."""
     return flat_model(3, [({0: 1, 1: 1}, {2: 1})], "paper_example")
+
+
+# ----------------------------------------------------------------------------
+# Compartmentalised workload (labels top, 1, 2, 3; top contains 1 and 2, 1
+# contains 3): intra-compartment reactions, transport in and out, binding to
+# the wrap, creation and dissolution of compartments (Sec. 2.1 rule forms).
+# ----------------------------------------------------------------------------
+
+CWC_TOKEN = 23      # species that marks a compartment: one in every wrap
+
+
+def _cwc3_rules(rng: SplitMix64, S: int) -> List[RuleSpec]:
+    """48 rules: 24 LOCAL (6 per label: 4 conversions, 2 bimolecular), 12
+    PARENT_CHILD (6 in, 4 out, 2 wrap binding), 6 CREATE, 6 DISSOLVE.  The
+    token species is used only by CREATE (consumes one free token from the
+    parent content, puts it in the new wrap) and DISSOLVE (matches the wrap
+    token, released to the parent with the rest of the compartment)."""
+    mol = S - 1          # molecular species 0..S-2
+    rules: List[RuleSpec] = []
+    for lab in range(4):
+        for _ in range(4):
+            a = rng.randint(0, mol - 1)
+            b = (a + rng.randint(1, mol - 1)) % mol
+            rules.append(RuleSpec(LOCAL, lab, lhs_ctx={a: 1}, rhs_ctx={b: 1}))
+        for i in range(2):
+            if i == 0:
+                a, b = rng.choice_distinct(mol, 2)
+                reac = {a: 1, b: 1}
+            else:
+                a = rng.randint(0, mol - 1)
+                reac = {a: 2}
+            c, d = rng.randint(0, mol - 1), rng.randint(0, mol - 1)
+            prod: Dict[int, int] = {}
+            prod[c] = prod.get(c, 0) + 1
+            prod[d] = prod.get(d, 0) + 1
+            rules.append(RuleSpec(LOCAL, lab, lhs_ctx=reac, rhs_ctx=prod))
+    pairs_in = [(0, 1), (0, 1), (0, 2), (0, 2), (1, 3), (1, 3)]
+    for par, ch in pairs_in:
+        x = rng.randint(0, mol - 1)
+        rules.append(RuleSpec(PARENT_CHILD, par, ch, lhs_ctx={x: 1}, rhs_child={x: 1}))
+    for par, ch in [(0, 1), (0, 2), (1, 3), (1, 3)]:
+        x = rng.randint(0, mol - 1)
+        rules.append(RuleSpec(PARENT_CHILD, par, ch, lhs_child={x: 1}, rhs_ctx={x: 1}))
+    for par, ch in [(0, 1), (0, 2)]:
+        x, y = rng.choice_distinct(mol, 2)
+        z = rng.randint(0, mol - 1)
+        rules.append(RuleSpec(PARENT_CHILD, par, ch, lhs_ctx={x: 1}, lhs_wrap={y: 1}, rhs_wrap={z: 1, y: 1}))
+    for par, ch in [(0, 1), (0, 1), (0, 2), (0, 2), (1, 3), (1, 3)]:
+        x = rng.randint(0, mol - 1)
+        rules.append(RuleSpec(CREATE, par, ch, lhs_ctx={CWC_TOKEN: 1}, rhs_wrap={CWC_TOKEN: 1}, rhs_child={x: 20}))
+    for par, ch in [(0, 1), (0, 1), (0, 2), (0, 2), (1, 3), (1, 3)]:
+        rules.append(RuleSpec(DISSOLVE, par, ch, lhs_wrap={CWC_TOKEN: 1}))
+    return rules
+
+
+def cwc3x24(R: int = 16384, G: int = 500, use_calibrated: bool = True) -> Batch:
+    """3 labels below the top level (nesting depth 2), 24 species, 48 rules,
+    at most 64 compartments per trajectory (63 tokens), 16,384 replicas,
+    500-point grid.
+
+    Initial term: the root holds U{10..200} of each molecular species and 31
+    free tokens; 8 label-1 compartments (each containing 2 label-3 ones) and 8
+    label-2 compartments, every one with one token in its wrap and U{10..200}
+    of each molecular species inside: 33 compartments, 63 tokens in all, so
+    CREATE can never run out of slots.  Molecular rate constants are
+    log-uniform over three decades with volume scaling for Omega = 100
+    molecules; creation and dissolution constants are log-uniform over
+    [0.1, 1] per compartment or token, which keeps the compartment population
+    stable and makes structural events about 0.6 % of all events."""
+    S, L, C = 24, 4, 64
+    rng = SplitMix64(3)
+    rules = _cwc3_rules(rng, S)
+    model = cwc_model(S, L, C, rules, "cwc3x24")
+    omega = 100.0
+    M = model.n_rules
+    rates = np.empty(M, np.float64)
+    for j in range(M):
+        if model.kind[j] in (CREATE, DISSOLVE):
+            rates[j] = rng.log_uniform(-1.0, 0.0)
+        else:
+            order = int(model.lhs[j].sum())
+            rates[j] = rng.log_uniform(-3.0, 0.0) * omega ** (1 - order)
+    img = empty_slot_image(model)
+    W_ = slot_image_width(S)
+    mol = S - 1
+
+    def fill_content(slot):
+        for x in range(mol):
+            img[slot, 3 + S + x] = rng.randint(10, 200)
+
+    fill_content(0)
+    img[0, 3 + S + CWC_TOKEN] = 31
+    slot = 1
+    l1_slots = []
+    for _ in range(8):
+        img[slot, :3] = [1, 1, 0]
+        img[slot, 3 + CWC_TOKEN] = 1
+        fill_content(slot)
+        l1_slots.append(slot)
+        slot += 1
+    for par in l1_slots:
+        for _ in range(2):
+            img[slot, :3] = [1, 3, par]
+            img[slot, 3 + CWC_TOKEN] = 1
+            fill_content(slot)
+            slot += 1
+    for _ in range(8):
+        img[slot, :3] = [1, 2, 0]
+        img[slot, 3 + CWC_TOKEN] = 1
+        fill_content(slot)
+        slot += 1
+    assert img.shape[1] == W_
+    T = 1.0
+    if use_calibrated:
+        Tc = calibrated_horizon("cwc3x24")
+        if Tc is not None:
+            T = Tc
+    return Batch(model, rates[None, :], img[None], uniform_grid(T, G), R, 103, name="cwc3x24")

@@ -1,0 +1,141 @@
+"""GPU parity for compartmentalised CWC models (transport, wrap binding,
+creation and dissolution of compartments) against the oracle, bit for bit:
+label-aggregated observables, statuses, event counts, (rule, slot) hashes,
+final times and event logs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1010_2438_gb300 import api, capi
+from paper_1010_2438_gb300 import workloads as W
+
+from test_gpu_flat import assert_same, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1010_2438_gb300 import build
+    build.build()
+    capi.lib()
+
+
+def check(batch, threads=8, **kw):
+    g = gpu_run(batch, **kw)
+    o = oracle.simulate(batch, threads=threads, log_cap=kw.get("log_cap", 0))
+    assert_same(g, o)
+    cap = kw.get("log_cap", 0)
+    if cap:
+        # entries past a trajectory's last event are not written by the GPU
+        valid = np.arange(cap)[None, :] < np.minimum(o["events"], cap)[:, None]
+        assert np.array_equal(g["log_rule"][valid], o["log_rule"][valid])
+        assert np.array_equal(g["log_slot"][valid], o["log_slot"][valid])
+        assert np.array_equal(g["log_t"].view(np.int64)[valid], o["log_t"].view(np.int64)[valid])
+    return g, o
+
+
+@pytest.mark.parametrize("layout", [capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE])
+def test_cwc3x24_bit_exact_with_event_log(layout):
+    b = W.cwc3x24(R=48)
+    g, o = check(b, log_cap=512, layout=layout)
+    assert np.all(g["status"] == oracle.ST_OK)
+
+
+def test_cwc3x24_structural_events_occur_and_match():
+    """Longer horizon so that creations and dissolutions certainly happen."""
+    b0 = W.cwc3x24(R=24, G=50)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 3.0, b0.R, b0.seed)
+    g, o = check(b, log_cap=40000)
+    lr = o["log_rule"]
+    kinds = b.model.kind[lr[lr >= 0]]
+    assert np.sum(kinds == W.CREATE) > 0 and np.sum(kinds == W.DISSOLVE) > 0
+
+
+def _transport(n_children=2):
+    rules = [W.RuleSpec(W.PARENT_CHILD, 0, 1, lhs_ctx={0: 1}, rhs_child={0: 1}),
+             W.RuleSpec(W.PARENT_CHILD, 0, 1, lhs_child={0: 1}, rhs_ctx={0: 1})]
+    m = W.cwc_model(1, 2, 1 + n_children, rules)
+    img = W.empty_slot_image(m)
+    img[0, 4] = 40
+    for d in range(1, n_children + 1):
+        img[d, :3] = [1, 1, 0]
+    return m, img
+
+
+def test_law_models_bit_exact():
+    m, img = _transport()
+    check(W.Batch(m, np.array([[0.4, 1.1]]), img[None], np.array([0.0, 0.2, 0.6, 1.5, 6.0]), 300, 8), log_cap=64)
+    # create / dissolve with a conserved token
+    rules = [W.RuleSpec(W.CREATE, 0, 1, lhs_ctx={0: 1}, rhs_wrap={0: 1}), W.RuleSpec(W.DISSOLVE, 0, 1)]
+    m = W.cwc_model(1, 2, 13, rules)
+    img = W.empty_slot_image(m)
+    img[0, 4] = 12
+    check(W.Batch(m, np.array([[0.9, 0.5]]), img[None], np.array([0.0, 0.3, 1.0, 3.0, 10.0]), 300, 9), log_cap=64)
+    # dissolution reparents a label-2 child to the top, which a transport rule then drains
+    rules = [W.RuleSpec(W.DISSOLVE, 0, 1), W.RuleSpec(W.PARENT_CHILD, 0, 2, lhs_child={0: 1}, rhs_ctx={0: 1})]
+    m = W.cwc_model(1, 3, 3, rules)
+    img = W.empty_slot_image(m)
+    img[1, :3] = [1, 1, 0]
+    img[2, :3] = [1, 2, 1]
+    img[2, 4] = 5
+    g, _ = check(W.Batch(m, np.array([[1.0, 1.0]]), img[None], np.array([0.0, 200.0]), 64, 10), log_cap=8)
+    assert np.all(g["status"] == oracle.ST_ABSORBED)
+
+
+def test_capacity_and_bad_slot_images():
+    rules = [W.RuleSpec(W.CREATE, 0, 1, lhs_ctx={0: 1})]
+    m = W.cwc_model(1, 2, 3, rules)
+    img = W.empty_slot_image(m)
+    img[0, 4] = 10
+    g, _ = check(W.Batch(m, np.array([[1.0]]), img[None], np.array([0.0, 1e6]), 4, 11))
+    assert np.all(g["status"] == oracle.ST_CAPACITY)
+    m, good = _transport(2)
+    bads = []
+    x = good.copy(); x[0, 0] = 0; bads.append(x)            # root not alive
+    x = good.copy(); x[1, 1] = 0; bads.append(x)            # child with the top label
+    x = good.copy(); x[1, 1] = 5; bads.append(x)            # label out of range
+    x = good.copy(); x[1, 2] = 2; x[2, 2] = 1; bads.append(x)   # parent cycle
+    x = good.copy(); x[2, 4] = -1; bads.append(x)           # negative count
+    x = good.copy(); x[0, 3] = 1; bads.append(x)            # root with a wrap
+    x = good.copy(); x[1, 0] = 2; bads.append(x)            # alive flag not 0/1
+    x = good.copy(); x[1, 2] = 7; bads.append(x)            # parent out of range
+    for img in bads:
+        g, _ = check(W.Batch(m, np.array([[0.4, 1.1]]), img[None], np.array([0.0, 1.0]), 3, 1))
+        assert np.all(g["status"] == oracle.ST_BAD_INPUT)
+
+
+def test_flat_network_through_the_compartment_kernel_matches_the_flat_kernel():
+    """A flat network declared with a spare label and slot runs the
+    compartment kernel; its top-level totals, events, hashes and times equal
+    the flat kernel's."""
+    b = W.flat8x12(R=40)
+    mf = b.model
+    mc = W.Model(mf.n_species, 2, 2, mf.kind, mf.ctx_label, mf.child_label, mf.lhs, mf.rhs)
+    img = W.empty_slot_image(mc)
+    img[0, 3 + mf.n_species:] = b.init[0]
+    bc = W.Batch(mc, b.rates, img[None], b.grid, b.R, b.seed)
+    gf = gpu_run(b)
+    gc = gpu_run(bc)
+    S = mf.n_species
+    assert np.array_equal(gc["states"][:, :, :S], gf["states"])
+    for k in ("events", "hash", "status"):
+        assert np.array_equal(gc[k], gf[k])
+    assert np.array_equal(gc["final_t"].view(np.int64), gf["final_t"].view(np.int64))
+    assert_same(gc, oracle.simulate(bc, threads=8))
+
+
+def test_cwc3x24_full_size_sampled():
+    from test_gpu_fullsize import check_sampled, sample_indices
+    b = W.cwc3x24()                          # 16,384 replicas, 500-point grid, 172 observables
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    res = api.simulate(cm, rates, init, grid, b.R, b.seed, b.max_events, states=True, sums=True)
+    torch.cuda.synchronize()
+    assert torch.all(res["status"] == 0)
+    check_sampled(b, res, sample_indices(b.n_traj, 10, 7))
+    col = res["states"].reshape(b.R, b.G, -1).sum(dim=0, dtype=torch.int64)
+    assert torch.equal(col, res["sums"][0])
