@@ -153,6 +153,71 @@ def cpu_baseline(batch, threads: int, n_traj: int):
 
 
 # ---------------------------------------------------------------------------
+# Other workloads of the path (one timed step each, after one warm-up)
+# ---------------------------------------------------------------------------
+
+def _timed(fn):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def measure_extras(dev):
+    import torch
+
+    from paper_1010_2438_gb300 import api, capi
+    from paper_1010_2438_gb300 import workloads as W
+    extras = {}
+    # compartmentalised CWC: 16,384 replicas x ~1e4 events, 500-point grid, 172 observables
+    b = W.cwc3x24()
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b, dev)
+    lay, thr, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=500)
+    keep = {}
+
+    def run_cwc():
+        keep["o"] = api.simulate(cm, rates, init, grid, b.R, b.seed, states=True, out=keep.get("o"))
+        return keep["o"]
+
+    out, sec = _timed(run_cwc)
+    ev = int(out["events"].sum().item())
+    extras["cwc3x24"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay, "block_threads": thr,
+                         "workload": "3 labels below the top, 24 species, 48 rules (transport, wrap binding, create, "
+                                     "dissolve), <=64 compartments, 16384 replicas, 500-point grid"}
+    del out, keep
+    # uneven sweep: 256 rate vectors x 256 replicas of flat32x64's network, autotuned, CUDA graph
+    b = W.sweep256x256()
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b, dev)
+    lay, thr, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=2000)
+    g = api.GraphedSimulation(cm, rates, init, grid, b.R, b.seed, states=True)
+    out, sec = _timed(g.replay)
+    evp = out["events"].double().mean(dim=1)
+    ev = int(out["events"].sum().item())
+    extras["sweep256x256"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay,
+                              "block_threads": thr, "graph": True,
+                              "length_spread": float((evp.max() / evp.min()).item()),
+                              "workload": "256 rate vectors x 256 replicas, flat32x64 network, 1000-point grid"}
+    del g, out
+    # likelihood-ratio sensitivities: 16 species x 24 reactions, 131,072 replicas, 100-point grid
+    b = W.flat16x24()
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b, dev)
+    fwd, t_fwd = _timed(lambda: api.simulate(cm, rates, init, grid, b.R, b.seed, states=False, means=True, traj=True))
+    ev = int(fwd["events"].sum().item())
+    gm = torch.ones_like(fwd["means"])
+    _, t_bwd = _timed(lambda: api.sensitivity(cm, rates, init, grid, b.R, b.seed, fwd["means"], gm))
+    extras["flat16x24_sensitivity"] = {"forward_events_per_s": ev / t_fwd, "forward_s": t_fwd, "backward_s": t_bwd,
+                                       "grad_over_fwd": t_bwd / t_fwd, "events": ev,
+                                       "workload": "d E[X(g)]/d k for 24 rates, 131072 replicas, 100-point grid"}
+    return extras
+
 
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -197,6 +262,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads of the path")
     ap.add_argument("--layout", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--replicas", type=int, default=0, help="smaller case for profiling (default: 65536)")
@@ -307,6 +373,10 @@ def main():
         e2e = {"value": ev_e / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": host_out.numel() * 4, "steps": e2e_steps}
 
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = measure_extras(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -325,7 +395,7 @@ def main():
                            "l2": "256 MiB buffer written between timed steps; outputs 8.4 GB per step",
                            "parallelism": "replica shards, %d GPU(s)" % world},
                 "gpu_launches": args.steps, "clocks": clk, "roofline": roofline,
-                "e2e": e2e, "cpu_baseline": cpu,
+                "e2e": e2e, "cpu_baseline": cpu, "extras": extras,
                 "step_ms": [round(x, 3) for x in step_ms]}
         print(json.dumps(line), flush=True)
     if world > 1:

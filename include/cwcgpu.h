@@ -270,6 +270,23 @@ cwc_status cwc_sensitivity_workspace_size(const cwc_model* model, const cwc_sim_
 cwc_status cwc_sensitivity(const cwc_model* model, const cwc_sim_args* sim, const cwc_sens_args* sens,
                            void* stream);
 
+/*
+ * Pick the launch layout (CWC_LAYOUT_STATIC or CWC_LAYOUT_QUEUE) and the
+ * threads per block for these arguments by timing every candidate on this
+ * batch with at most `tune_events` events per trajectory (0 = 2048) and no
+ * outputs; all candidates do identical work because the random streams are
+ * keyed by (event, replica, point), not by thread.  One thread always runs one
+ * trajectory: on GB300 an FP64 instruction costs a full warp slot whatever the
+ * number of active lanes, so sharing a trajectory among lanes only multiplies
+ * the cost of its scalar FP64 work.  The winner is returned and cached for
+ * this model and batch shape; later calls with layout CWC_LAYOUT_AUTO and
+ * block_threads 0 use it.  Synchronises `stream`.  Uses args->workspace (a
+ * candidate that needs more than workspace_bytes is skipped).
+ * Errors: as cwc_simulate; CWC_ERR_INTERNAL if no candidate could run.
+ */
+cwc_status cwc_autotune(const cwc_model* model, const cwc_sim_args* args, int64_t tune_events, void* stream,
+                        int32_t* best_layout, int32_t* best_block_threads, double* best_ms);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* cwc_last_error(void);
 

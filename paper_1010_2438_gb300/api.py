@@ -216,3 +216,59 @@ def simulate_host(cm: CompiledModel, rates_h: torch.Tensor, init_h: torch.Tensor
             host_out = torch.empty(res["states"].shape, dtype=torch.int32, pin_memory=True)
         host_out.copy_(res["states"], non_blocking=True)
     return host_out
+
+
+def autotune(cm: CompiledModel, rates, init, grid, R: int, seed: int, max_events: int = (1 << 32) - 1,
+             tune_events: int = 0, stream: Optional[torch.cuda.Stream] = None):
+    """cwc_autotune on this batch: returns (layout, block_threads, ms) and
+    caches the choice for later CWC_LAYOUT_AUTO calls on the same shape."""
+    _check_inputs(cm, rates, init, grid)
+    nbytes = 0
+    for lay in (capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE):
+        for T in range(32, 257, 32):
+            a = _sim_args(cm, rates, init, grid, R, seed, max_events, lay, T, 0)
+            try:
+                nbytes = max(nbytes, capi.cwc_simulate_workspace_size(cm.handle, a))
+            except capi.CwcError:
+                pass
+    ws = _workspace(nbytes, rates.device)
+    a = _sim_args(cm, rates, init, grid, R, seed, max_events, capi.CWC_LAYOUT_AUTO, 0, 0)
+    a.workspace = _aligned(ws) if nbytes else None
+    a.workspace_bytes = nbytes
+    return capi.cwc_autotune(cm.handle, a, tune_events, _stream_handle(stream))
+
+
+class GraphedSimulation:
+    """One cwc_simulate call captured in a CUDA graph over static buffers.
+
+    ``replay(rates=..., init=..., grid=...)`` copies new inputs (same shapes)
+    into the captured buffers and relaunches the graph; the outputs are the
+    tensors in ``self.out`` (overwritten by every replay).  The seed and the
+    batch shape are part of the capture.
+    """
+
+    def __init__(self, cm: CompiledModel, rates, init, grid, R: int, seed: int,
+                 max_events: int = (1 << 32) - 1, **kw):
+        self.rates = rates.clone()
+        self.init = init.clone()
+        self.grid = grid.clone()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.out = simulate(cm, self.rates, self.init, self.grid, R, seed, max_events, stream=side, **kw)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            self.out = simulate(cm, self.rates, self.init, self.grid, R, seed, max_events, out=self.out,
+                                stream=torch.cuda.current_stream(), **kw)
+
+    def replay(self, rates=None, init=None, grid=None) -> Dict[str, torch.Tensor]:
+        if rates is not None:
+            self.rates.copy_(rates)
+        if init is not None:
+            self.init.copy_(init)
+        if grid is not None:
+            self.grid.copy_(grid)
+        self.graph.replay()
+        return self.out

@@ -25,7 +25,7 @@ CWC_LAYOUT_AUTO, CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE = range(3)
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = ("cwc_model_create", "cwc_model_destroy", "cwc_model_num_observables", "cwc_simulate_workspace_size",
             "cwc_simulate", "cwc_simulate_noalloc", "cwc_sensitivity_workspace_size", "cwc_sensitivity",
-            "cwc_last_error", "cwc_version")
+            "cwc_autotune", "cwc_last_error", "cwc_version")
 CWC_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 _vp = ctypes.c_void_p
@@ -91,6 +91,9 @@ def lib() -> ctypes.CDLL:
         L.cwc_sensitivity_workspace_size.restype = ctypes.c_int
         L.cwc_sensitivity.argtypes = [_vp, ctypes.POINTER(cwc_sim_args), ctypes.POINTER(cwc_sens_args), _vp]
         L.cwc_sensitivity.restype = ctypes.c_int
+        L.cwc_autotune.argtypes = [_vp, ctypes.POINTER(cwc_sim_args), _i64, _vp, ctypes.POINTER(_i32),
+                                   ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]
+        L.cwc_autotune.restype = ctypes.c_int
         L.cwc_last_error.argtypes = []
         L.cwc_last_error.restype = ctypes.c_char_p
         L.cwc_version.argtypes = []
@@ -142,6 +145,14 @@ def cwc_simulate_noalloc(handle: int, args: cwc_sim_args, stream: int = 0) -> No
     workspace: the library's fixed CWC_NOALLOC_SCRATCH_BYTES device array is
     used instead; calls overlapping on the GPU race on it)."""
     _check(lib().cwc_simulate_noalloc(handle, ctypes.byref(args), stream))
+
+
+def cwc_autotune(handle: int, args: cwc_sim_args, tune_events: int = 0, stream: int = 0):
+    """Time the launch candidates on this batch; returns (layout, block_threads, ms) and caches them."""
+    lay, thr, ms = _i32(), _i32(), ctypes.c_double()
+    _check(lib().cwc_autotune(handle, ctypes.byref(args), tune_events, stream, ctypes.byref(lay), ctypes.byref(thr),
+                              ctypes.byref(ms)))
+    return lay.value, thr.value, ms.value
 
 
 def cwc_sensitivity_workspace_size(handle: int, args: cwc_sim_args, sens: cwc_sens_args) -> int:

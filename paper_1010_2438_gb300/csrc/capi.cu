@@ -6,8 +6,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "cwc_internal.h"
@@ -95,7 +97,31 @@ CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a) {
   return prm;
 }
 
+// Autotuner cache: (model, P, R, G, Pi) -> (layout, threads per block).
+std::mutex g_tune_mutex;
+std::map<std::tuple<const void*, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+bool tuned_choice(const cwc_model* m, const cwc_sim_args* a, int* layout, int* threads) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tune_cache.find(std::make_tuple((const void*)m, a->P, a->R, a->G, a->Pi));
+  if (it == g_tune_cache.end()) return false;
+  *layout = it->second.first;
+  *threads = it->second.second;
+  return true;
+}
+
 int chosen_layout(const cwc_sim_args* a) { return a->layout == CWC_LAYOUT_AUTO ? CWC_LAYOUT_QUEUE : a->layout; }
+
+// Resolve CWC_LAYOUT_AUTO / block_threads 0 through the autotuner cache.
+cwc_sim_args resolve_auto(const cwc_model* m, const cwc_sim_args* a) {
+  cwc_sim_args b = *a;
+  int lay = 0, thr = 0;
+  if (a->layout == CWC_LAYOUT_AUTO && a->block_threads == 0 && tuned_choice(m, a, &lay, &thr)) {
+    b.layout = lay;
+    b.block_threads = thr;
+  }
+  return b;
+}
 
 WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool sens_partials_given) {
   WsLayout w;
@@ -437,6 +463,11 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
 
 void cwc_model_destroy(cwc_model* m) {
   if (m == nullptr) return;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (auto it = g_tune_cache.begin(); it != g_tune_cache.end();)
+      it = std::get<0>(it->first) == (const void*)m ? g_tune_cache.erase(it) : std::next(it);
+  }
   if (m->d_tables) cudaFree(m->d_tables);
   if (m->d_ctables) cudaFree(m->d_ctables);
   delete m;
@@ -452,7 +483,8 @@ cwc_status cwc_simulate_workspace_size(const cwc_model* m, const cwc_sim_args* a
   if (bytes == nullptr) return fail(CWC_ERR_INVALID_ARG, "bytes must not be NULL");
   cwc_status st = check_sim_args(m, a);
   if (st != CWC_OK) return st;
-  *bytes = ws_layout(m, a, false, false).total;
+  const cwc_sim_args b = resolve_auto(m, a);
+  *bytes = ws_layout(m, &b, false, false).total;
   return CWC_OK;
 }
 
@@ -551,7 +583,8 @@ cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void*
   g_last_error.clear();
   cwc_status st = check_sim_args(m, a);  // also checks that m's device is the current one
   if (st != CWC_OK) return st;
-  const WsLayout w = ws_layout(m, a, false, false);
+  const cwc_sim_args ra = resolve_auto(m, a);
+  const WsLayout w = ws_layout(m, &ra, false, false);
   if (w.total > CWC_NOALLOC_SCRATCH_BYTES)
     return fail(CWC_ERR_INVALID_ARG, "this call needs " + std::to_string(w.total) +
                                          " bytes of scratch; cwc_simulate_noalloc holds " +
@@ -560,7 +593,7 @@ cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void*
   void* scratch = nullptr;
   st = noalloc_scratch_address(m->device, &scratch);
   if (st != CWC_OK) return st;
-  cwc_sim_args b = *a;
+  cwc_sim_args b = ra;
   b.workspace = scratch;
   b.workspace_bytes = CWC_NOALLOC_SCRATCH_BYTES;
   if (!m->flat) return run_cwc(m, &b, static_cast<cudaStream_t>(stream));
@@ -627,8 +660,90 @@ cwc_status cwc_simulate(const cwc_model* m, const cwc_sim_args* a, void* stream)
   g_last_error.clear();
   cwc_status st = check_sim_args(m, a);
   if (st != CWC_OK) return st;
-  if (!m->flat) return run_cwc(m, a, static_cast<cudaStream_t>(stream));
-  return run_flat(m, a, nullptr, static_cast<cudaStream_t>(stream));
+  const cwc_sim_args b = resolve_auto(m, a);
+  if (!m->flat) return run_cwc(m, &b, static_cast<cudaStream_t>(stream));
+  return run_flat(m, &b, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_events, void* stream,
+                        int32_t* best_layout, int32_t* best_threads, double* best_ms) {
+  g_last_error.clear();
+  cwc_status st = check_sim_args(m, a);
+  if (st != CWC_OK) return st;
+  if (tune_events < 0) return fail(CWC_ERR_INVALID_ARG, "tune_events must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(CWC_ERR_CUDA, "cudaEventCreate");
+  cwc_sim_args c = *a;
+  c.states = nullptr;
+  c.sums = nullptr;
+  c.means = nullptr;
+  c.traj_status = nullptr;
+  c.traj_events = nullptr;
+  c.traj_hash = nullptr;
+  c.traj_final_t = nullptr;
+  c.log_cap = 0;
+  c.log_rule = nullptr;
+  c.log_slot = nullptr;
+  c.log_t = nullptr;
+  c.deadline_ns = 0;
+  const int64_t cap = tune_events == 0 ? 2048 : tune_events;
+  c.max_events = std::min<int64_t>(a->max_events, cap);
+  float best = -1.0f;
+  int bl = 0, bt = 0;
+  for (int lay : {CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE}) {
+    for (int T = 32; T <= 256; T += 32) {
+      c.layout = lay;
+      c.block_threads = T;
+      if (m->flat) {
+        FlatParams prm = make_flat_params(m, &c);
+        if (flat_smem_bytes(prm, T, false) > 227 * 1024) continue;
+      } else if ((size_t)cwc_table_bytes_host(m->M, m->c_n_deps) + (size_t)T * (32 + TREE_NODES + m->M) * 8 >
+                 227 * 1024) {
+        continue;
+      }
+      const WsLayout w = ws_layout(m, &c, false, false);
+      if (!m->flat && w.blocks < 1) continue;
+      if (w.total > 0 && (c.workspace == nullptr || c.workspace_bytes < w.total)) continue;
+      float ms_best = -1.0f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        st = m->flat ? run_flat(m, &c, nullptr, s) : run_cwc(m, &c, s);
+        cudaEventRecord(e1, s);
+        if (st != CWC_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return fail(CWC_ERR_CUDA, "autotune candidate failed");
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep == 1) ms_best = ms;
+      }
+      if (st != CWC_OK) {
+        st = CWC_OK;
+        continue;
+      }
+      if (ms_best >= 0.0f && (best < 0.0f || ms_best < best)) {
+        best = ms_best;
+        bl = lay;
+        bt = T;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0.0f) return fail(CWC_ERR_INTERNAL, "no autotune candidate could run (workspace too small?)");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[std::make_tuple((const void*)m, a->P, a->R, a->G, a->Pi)] = std::make_pair(bl, bt);
+  }
+  if (best_layout) *best_layout = bl;
+  if (best_threads) *best_threads = bt;
+  if (best_ms) *best_ms = best;
+  g_last_error.clear();
+  return CWC_OK;
 }
 
 cwc_status cwc_sensitivity(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* s, void* stream) {
