@@ -22,6 +22,7 @@ cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queu
 size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens);
 int flat_table_bytes_host(int M, int n_deps);
 int flat_best_threads(const FlatParams& prm, bool queue, bool sens);
+cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order, cudaStream_t stream);
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, double* grad, int P, int R, int M, cudaStream_t st);
 cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, cudaStream_t stream);
@@ -75,7 +76,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout: [header 256 B][sums P*G*O int64 if needed][partials Q*M double if needed]
 struct WsLayout {
-  size_t header = 0, sums = 0, partials = 0, slabs = 0, total = 0;
+  size_t header = 0, sums = 0, partials = 0, slabs = 0, order = 0, total = 0;
+  bool need_order = false;        // flat queue layout over several sweep points
   bool need_header = false, need_sums = false, need_partials = false;
   int T = 0, blocks = 0;          // compartmentalised launch shape (its slabs are per thread)
   long long slab_words = 0;
@@ -141,6 +143,11 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
   if (w.need_partials) {
     w.partials = off;
     off = align256(off + (size_t)a->P * a->R * m->M * sizeof(double));
+  }
+  w.need_order = m->flat && chosen_layout(a) == CWC_LAYOUT_QUEUE && a->P > 1 && a->P <= 65536;
+  if (w.need_order) {
+    w.order = off;
+    off = align256(off + (size_t)a->P * (sizeof(double) + sizeof(int32_t)));
   }
   if (!m->flat) {
     const CwcParams prm = cwc_shape_params(m, a);
@@ -540,6 +547,13 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
   }
   const LogConstants lc = make_log_constants();
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
+  if (w.need_order) {
+    double* est = reinterpret_cast<double*>(ws + w.order);
+    int32_t* order = reinterpret_cast<int32_t*>(est + a->P);
+    e = launch_flat_order(prm, est, order, st);
+    if (e != cudaSuccess) return cuda_fail(e, "queue order kernels");
+    prm.order = order;
+  }
   const int T = pick_threads(m, a, prm, queue, is_sens);
   if (flat_smem_bytes(prm, T, is_sens) > 227 * 1024)
     return fail(CWC_ERR_INVALID_ARG, "block_threads too large for this model's shared-memory state");

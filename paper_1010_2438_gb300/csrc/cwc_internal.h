@@ -94,6 +94,7 @@ struct FlatParams {
   double* partials;                // [Q][M]
   // scheduling
   WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)
+  const int32_t* order;            // queue mode: sweep points, longest expected first (or null)
   long long deadline_ns;
   int smem_table_bytes;            // bytes of the shared-memory table region
 };

@@ -13,8 +13,11 @@
 // per-thread slab of the caller's workspace, reused across the trajectories a
 // thread runs:
 //   chmask[C]  u64  children of each slot        labmask[L] u64  alive slots per label
-//   alive      u64  alive slots                  meta[C]    i32  label | (parent + 1) << 8
-//   wrap[C][S], content[C][S]  i32
+//   alive      u64  alive slots                  tot[O]     i64  observable totals
+//   meta[C]    i32  label | (parent + 1) << 8   wrap[C][S], content[C][S]  i32
+// The observable totals (content per label, wrap per label, alive compartments
+// per label) are kept up to date by every rewrite, so recording a grid point
+// is O stores.
 // After an event, the totals H_i of the rules that read a location (content
 // or wrap of a label, a species) the fired rule wrote are recomputed from
 // scratch over their contexts (all rules after CREATE / DISSOLVE), so H is
@@ -44,7 +47,8 @@ __host__ __device__ inline int cwc_table_bytes(int M, int n_deps) {
 __host__ __device__ inline int cwc_thread_bytes(int M) { return (32 + TREE_NODES + M) * 8; }
 
 __host__ __device__ inline long long cwc_slab_words(int S, int L, int C) {
-  long long w = 2LL * C + 2LL * L + 2 + C + 2LL * C * S;
+  const long long O = (long long)L * S + (long long)(L - 1) * S + L;
+  long long w = 2LL * C + 2LL * L + 2 + 2 * O + C + 2LL * C * S;
   return (w + 31) / 32 * 32;
 }
 
@@ -102,7 +106,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   unsigned long long* chmask = reinterpret_cast<unsigned long long*>(slab);       // [C]
   unsigned long long* labmask = chmask + C;                                       // [L]
   unsigned long long* alive_p = labmask + L;                                      // [1]
-  int32_t* meta = reinterpret_cast<int32_t*>(alive_p + 1);                        // [C]
+  long long* tot = reinterpret_cast<long long*>(alive_p + 1);                     // [O]
+  int32_t* meta = reinterpret_cast<int32_t*>(tot + O);                            // [C]
   int32_t* wrap = meta + C;                                                       // [C][S]
   int32_t* content = wrap + (size_t)C * S;                                        // [C][S]
 
@@ -185,39 +190,20 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
   };
 
+  // observable index of the content / wrap total of (label, species) and of the alive count
+  auto OC = [&](int l, int x) { return l * S + x; };
+  auto OW = [&](int l, int x) { return L * S + (l - 1) * S + x; };
+  auto OA = [&](int l) { return L * S + (L - 1) * S + l; };
+
   auto record = [&](int g) {
     int32_t* dst = prm.states != nullptr ? prm.states + ((size_t)q * G + g) * O : nullptr;
     unsigned long long* sdst = prm.sums != nullptr ? prm.sums + ((size_t)p * G + g) * O : nullptr;
-    auto emit = [&](int o, long long v) {
+    for (int o = 0; o < O; ++o) {
+      const long long v = tot[o];
       const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
       if (dst) dst[o] = sv;
       if (sdst) atomicAdd(sdst + o, (unsigned long long)(long long)sv);
-    };
-    for (int l = 0; l < L; ++l) {
-      for (int x = 0; x < S; ++x) {
-        long long v = 0;
-        unsigned long long m = labmask[l];
-        while (m) {
-          const int c = __ffsll((long long)m) - 1;
-          m &= m - 1ull;
-          v += content[(size_t)c * S + x];
-        }
-        emit(l * S + x, v);
-      }
     }
-    for (int l = 1; l < L; ++l) {
-      for (int x = 0; x < S; ++x) {
-        long long v = 0;
-        unsigned long long m = labmask[l];
-        while (m) {
-          const int c = __ffsll((long long)m) - 1;
-          m &= m - 1ull;
-          v += wrap[(size_t)c * S + x];
-        }
-        emit(L * S + (l - 1) * S + x, v);
-      }
-    }
-    for (int l = 0; l < L; ++l) emit(L * S + (L - 1) * S + l, __popcll(labmask[l]));
   };
   auto fill = [&]() {
     for (; gi < G; ++gi) record(gi);
@@ -306,6 +292,15 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       labmask[LABEL(c)] |= 1ull << c;
       if (c > 0) chmask[PARENT(c)] |= 1ull << c;
     }
+    for (int o = 0; o < O; ++o) tot[o] = 0;
+    for (int c = 0; c < C; ++c) {
+      if (!((alive >> c) & 1ull)) continue;
+      const int l = LABEL(c);
+      for (int x = 0; x < S; ++x) tot[OC(l, x)] += content[(size_t)c * S + x];
+      if (l > 0)
+        for (int x = 0; x < S; ++x) tot[OW(l, x)] += wrap[(size_t)c * S + x];
+      tot[OA(l)] += 1;
+    }
     for (int i = 0; i < M; ++i) HV(i) = total_h(i);
     rebuild_tree();
     return false;
@@ -326,9 +321,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int v = rec[CR_D0 + d];
         if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
+      const int l = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         x[v & 0xffff] += v >> 16;
+        tot[OC(l, v & 0xffff)] += v >> 16;
       }
       return TS_OK;
     }
@@ -349,17 +346,21 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int v = rec[CR_D2 + d];
         if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
+      const int lq = LABEL(qq), lc = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         xp[v & 0xffff] += v >> 16;
+        tot[OC(lq, v & 0xffff)] += v >> 16;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
         w[v & 0xffff] += v >> 16;
+        tot[OW(lc, v & 0xffff)] += v >> 16;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
         xc[v & 0xffff] += v >> 16;
+        tot[OC(lc, v & 0xffff)] += v >> 16;
       }
       return TS_OK;
     }
@@ -373,9 +374,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int v = rec[CR_D0 + d];
         if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
+      const int lctx = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         x[v & 0xffff] += v >> 16;
+        tot[OC(lctx, v & 0xffff)] += v >> 16;
       }
       int32_t* we = wrap + (size_t)e * S;
       int32_t* xe = content + (size_t)e * S;
@@ -392,6 +395,15 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         xe[v & 0xffff] = v >> 16;
       }
       const int lab = rec[CR_CHILD];
+      for (int d = 0; d < nd1; ++d) {
+        const int v = rec[CR_D1 + d];
+        tot[OW(lab, v & 0xffff)] += v >> 16;
+      }
+      for (int d = 0; d < nd2; ++d) {
+        const int v = rec[CR_D2 + d];
+        tot[OC(lab, v & 0xffff)] += v >> 16;
+      }
+      tot[OA(lab)] += 1;
       meta[e] = lab | ((c + 1) << 8);
       chmask[e] = 0ull;
       chmask[c] |= 1ull << e;
@@ -425,7 +437,15 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const long long nv = (long long)xp[s] + delta_at(s);
         if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
       }
-      for (int s = 0; s < S; ++s) xp[s] = (int32_t)((long long)xp[s] + delta_at(s));
+      const int lq = LABEL(qq), ld = LABEL(c);
+      for (int s = 0; s < S; ++s) {
+        const long long dv = delta_at(s);
+        xp[s] = (int32_t)((long long)xp[s] + dv);
+        tot[OC(lq, s)] += dv;
+        tot[OC(ld, s)] -= xc[s];
+        tot[OW(ld, s)] -= w[s];
+      }
+      tot[OA(ld)] -= 1;
       unsigned long long kids = chmask[c];
       while (kids) {
         const int e = __ffsll((long long)kids) - 1;

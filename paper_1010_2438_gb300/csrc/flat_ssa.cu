@@ -421,6 +421,10 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     if (need_new) {
       if (kQueue) {
         q = grab_next(prm.ws);
+        if (prm.order != nullptr && q < Q) {
+          const long long pp = prm.order[q / prm.R];
+          q = pp * prm.R + (q - (q / prm.R) * prm.R);
+        }
       } else {
         q = first ? (long long)blockIdx.x * T + tid : q + qstride;
         first = false;
@@ -440,6 +444,54 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
 #undef LEAF
 #undef NODE
 #undef CNT
+}
+
+// ---------------------------------------------------------------------------
+// Predictive queue order (longest expected sweep point first).  The initial
+// total propensity a0(x0; k_p) is the rate of events at the start, a proxy
+// for the trajectory length under the same horizon; serving the longest
+// sweep points first keeps them off the tail of the run.  Only the order in
+// which trajectories are taken changes, never their values.
+// ---------------------------------------------------------------------------
+
+__global__ void flat_estimate_kernel(const __grid_constant__ FlatParams prm, double* __restrict__ est) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= prm.P) return;
+  const int32_t* x0 = prm.init + (size_t)(prm.Pi == 1 ? 0 : p) * prm.S;
+  const double* k = prm.rates + (size_t)p * prm.M;
+  double a0 = 0.0;
+  for (int j = 0; j < prm.M; ++j) {
+    const int32_t* rec = prm.rules + j * RULE_WORDS;
+    double hh = 1.0;
+    for (int a = 0; a < rec[R_NREAC]; ++a) {
+      const int v = rec[R_REAC + a];
+      const double n = (double)max(x0[v & 0xffff], 0);
+      hh *= (v >> 16) == 1 ? n : 0.5 * n * (n - 1.0);
+    }
+    a0 += k[j] * hh;
+  }
+  est[p] = (a0 >= 0.0 && a0 < 1e300) ? a0 : 0.0;
+}
+
+__global__ void rank_desc_kernel(const double* __restrict__ est, int P, int32_t* __restrict__ order) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const double e = est[p];
+  int rank = 0;
+  for (int i = 0; i < P; ++i) {
+    const double f = est[i];
+    rank += (f > e) || (f == e && i < p);
+  }
+  order[rank] = p;
+}
+
+cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order, cudaStream_t stream) {
+  const int blocks = (prm.P + 127) / 128;
+  flat_estimate_kernel<<<blocks, 128, 0, stream>>>(prm, est);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rank_desc_kernel<<<blocks, 128, 0, stream>>>(est, prm.P, order);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
