@@ -440,6 +440,20 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
     rec[R_LEAFMASK] = (int32_t)leafmask;
     rec[R_NODEMASK] = (int32_t)nodemask;
   }
+  // reactant descriptors (used when every rule has order <= 2)
+  for (int j = 0; j < M; ++j) {
+    uint32_t kind = 0, s0 = 0, s1 = 0;
+    const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
+    if (reac[j].size() == 1) {
+      s0 = s1 = (uint32_t)reac[j][0];
+      kind = lhs[s0] == 1 ? 1u : 2u;
+    } else if (reac[j].size() == 2) {
+      s0 = (uint32_t)reac[j][0];
+      s1 = (uint32_t)reac[j][1];
+      kind = 3u;
+    }
+    tb.push_back((int32_t)(kind | (s0 << 2) | (s1 << 16)));
+  }
   // one trajectory's state must fit: 32 threads per block at least
   {
     FlatParams prm;

@@ -47,7 +47,7 @@ __device__ __forceinline__ long long grab_next(WorkspaceHeader* ws) {
 // Shared-memory table region: rules, dependents, e*ln2 table (doubles last,
 // 16-byte aligned).  Must match on host and device.
 __host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
-  int words = M * RULE_WORDS + n_deps;
+  int words = M * RULE_WORDS + n_deps + M;
   int bytes = ((words * 4 + 15) / 16) * 16;
   return bytes + 54 * 8;
 }
@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
 
   int32_t* s_rules = reinterpret_cast<int32_t*>(smem);
   int32_t* s_deps = s_rules + M * RULE_WORDS;
-  const int tbl_words = M * RULE_WORDS + prm.n_deps;
+  const uint32_t* s_desc = reinterpret_cast<const uint32_t*>(s_deps + prm.n_deps);
+  const int tbl_words = M * RULE_WORDS + prm.n_deps + M;
   double* s_eln2 = reinterpret_cast<double*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
   // Per-thread arrays [index][T]: each pointer below already points at this
   // thread's column, so element i of the array is ptr[i * T].
@@ -171,17 +172,18 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   // binomials).  Models whose rules all have order <= 2 cannot overflow
   // (n*m < 2^62 for counts < 2^31) and take 32x32->64-bit products only.
   auto count_h = [&](int i) -> unsigned long long {
+    if (!checked) {
+      // one descriptor load, both count loads in flight together, no branches
+      const uint32_t d = s_desc[i];
+      const uint32_t kind = d & 3u;
+      const unsigned n0 = (unsigned)CNT((d >> 2) & 0x3fffu);
+      const unsigned n1 = (unsigned)CNT((d >> 16) & 0x3fffu);
+      const unsigned m = kind == 3u ? n1 : (kind == 2u ? n0 - 1u : 1u);
+      const unsigned long long prod = (unsigned long long)(kind == 0u ? 1u : n0) * m;
+      return kind == 2u ? prod >> 1 : prod;
+    }
     const int32_t* rec = s_rules + i * RULE_WORDS;
     const int nr = rec[R_NREAC];
-    if (!checked) {
-      if (nr == 0) return 1ull;
-      const int v0 = rec[R_REAC];
-      const unsigned n0 = (unsigned)CNT(v0 & 0xffff);
-      if (nr == 1)
-        return (v0 >> 16) == 1 ? (unsigned long long)n0 : ((unsigned long long)n0 * (n0 - 1u)) >> 1;
-      const int v1 = rec[R_REAC + 1];
-      return (unsigned long long)n0 * (unsigned)CNT(v1 & 0xffff);
-    }
     unsigned long long hh = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[R_REAC + a];

@@ -109,7 +109,12 @@ constexpr unsigned long long FNV_OFFSET = 0xcbf29ce484222325ull;
 // the dropped low bits decide the rounding (ties to even), and a carry out of
 // the 53-bit significand bumps the exponent.
 __device__ __forceinline__ double u63_to_double_rn(unsigned long long x) {
-  if (x == 0ull) return 0.0;
+  if ((x >> 53) == 0ull) {
+    // exact: shift the leading one to bit 52 and add the exponent (x = 0 -> +0)
+    const int lead = 63 - __clzll((long long)x);
+    const unsigned long long bits = ((unsigned long long)(1023 + lead) << 52) + ((x << (52 - lead)) - (1ull << 52));
+    return x == 0ull ? 0.0 : __longlong_as_double((long long)bits);
+  }
   int lead = 63 - __clzll((long long)x);
   unsigned long long m;
   if (lead <= 52) {
