@@ -268,6 +268,8 @@ def main():
     ap.add_argument("--replicas", type=int, default=0, help="smaller case for profiling (default: 65536)")
     ap.add_argument("--horizon-scale", type=float, default=1.0, help="scale the time grid (profiling only)")
     ap.add_argument("--grid-points", type=int, default=0, help="grid points (profiling only; default 1000)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "cwc3x24"],
+                    help="profiling only: run the compartment workload as the timed step")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -286,7 +288,10 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.device("cuda", torch.cuda.current_device())
     lib_build.build()
-    batch = W.flat32x64(R=args.replicas or 65536, G=args.grid_points or 1000)
+    if args.workload == "cwc3x24":
+        batch = W.cwc3x24(R=args.replicas or 16384, G=args.grid_points or 500)
+    else:
+        batch = W.flat32x64(R=args.replicas or 65536, G=args.grid_points or 1000)
     if args.horizon_scale != 1.0:
         batch = W.Batch(batch.model, batch.rates, batch.init, batch.grid * args.horizon_scale, batch.R, batch.seed,
                         name=batch.name)
@@ -386,8 +391,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD if not (args.replicas or args.grid_points or args.horizon_scale != 1.0)
-                       else "%s (profiling case: R=%d, G=%d, horizon x%g)" % (WORKLOAD, R, batch.G, args.horizon_scale),
+                "config": {"workload": WORKLOAD if not (args.replicas or args.grid_points or args.horizon_scale != 1.0
+                                                    or args.workload != WORKLOAD)
+                       else "%s (profiling case: R=%d, G=%d, horizon x%g)" % (args.workload, R, batch.G,
+                                                                               args.horizon_scale),
                        "description": WORKLOAD_DESC, "P": batch.P, "R": R,
                            "G": batch.G, "S": batch.model.n_species, "M": batch.model.n_rules,
                            "events_per_step_per_gpu": events, "statuses": statuses,

@@ -149,6 +149,17 @@ enum {
  *   sums          int64 [P][G][O]      exact sums over replicas (zeroed by
  *                                      the call before accumulation)
  *   means         double [P][G][O]     sums / R (one IEEE division)
+ *   sumsq         uint64 [P][G][O][2]  exact 128-bit sums of squares over
+ *                                      replicas, (low word, high word); zeroed
+ *                                      by the call
+ *   variance      double [P][G][O]     sample variance over replicas:
+ *                                      RN(R*sumsq - sums^2) / (R * (R - 1)),
+ *                                      0 when R = 1 (the numerator is exact)
+ *   ci90          double [P][G][O]     half-width of the 90 % normal-
+ *                                      approximation confidence interval of
+ *                                      the mean: z * sqrt(variance / R),
+ *                                      z = 1.6448536269514722 (Sec. 5.2:
+ *                                      on-line mean, variance, confidence)
  *   traj_status   int32 [P][R]         CWC_TRAJ_* codes
  *   traj_events   int64 [P][R]         applied events
  *   traj_hash     uint64 [P][R]        FNV-1a-64 over (rule, slot) of every
@@ -187,6 +198,9 @@ typedef struct {
   int32_t* states;
   int64_t* sums;
   double* means;
+  uint64_t* sumsq;
+  double* variance;
+  double* ci90;
   int32_t* traj_status;
   int64_t* traj_events;
   uint64_t* traj_hash;

@@ -215,6 +215,29 @@ def sums(states: np.ndarray, P: int, R: int) -> np.ndarray:
     return states.reshape(P, R, G, O).astype(np.int64).sum(axis=1)
 
 
+Z90 = 1.6448536269514722   # the double nearest the 0.95 quantile of N(0, 1)
+
+
+def replica_stats(states: np.ndarray, P: int, R: int):
+    """Per (p, g, o): exact sum and sum of squares over replicas (Python
+    integers), sample variance RN(R*sumsq - sum^2) / (R*(R-1)) and the 90 %
+    normal-approximation half-width Z90 * sqrt(variance / R), each a single
+    IEEE double operation (the on-line mean / variance / confidence reduction
+    of the multi-instance simulator, Sec. 5.2)."""
+    nq, G, O = states.shape
+    x = states.reshape(P, R, G, O).astype(object)
+    s = x.sum(axis=1)
+    q = (x * x).sum(axis=1)
+    num = R * q - s * s
+    numf = np.array([float(v) for v in num.ravel()], dtype=np.float64).reshape(num.shape)
+    if R > 1:
+        var = numf / (np.float64(R) * np.float64(R - 1))
+    else:
+        var = np.zeros(num.shape, np.float64)
+    ci = np.float64(Z90) * np.sqrt(var / np.float64(R))
+    return s, q, var, ci
+
+
 def mean_observables(batch, threads: int = 1) -> np.ndarray:
     """E[X(g)] estimate per sweep point: exact int64 sum over R, one division."""
     st = simulate(batch, states=True, threads=threads)["states"]

@@ -93,6 +93,7 @@ def _aligned(ws: Optional[torch.Tensor]) -> int:
 
 def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: torch.Tensor, R: int, seed: int,
              max_events: int = (1 << 32) - 1, *, states: bool = True, sums: bool = False, means: bool = False,
+             sumsq: bool = False, variance: bool = False, ci90: bool = False,
              traj: bool = True, log_cap: int = 0, layout: int = capi.CWC_LAYOUT_AUTO, block_threads: int = 0,
              deadline_ns: int = 0, replica_offset: int = 0, stream: Optional[torch.cuda.Stream] = None,
              out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
@@ -120,6 +121,12 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
         a.sums = _p(get("sums", (P, G, O), torch.int64))
     if means:
         a.means = _p(get("means", (P, G, O), torch.float64))
+    if sumsq:
+        a.sumsq = _p(get("sumsq", (P, G, O, 2), torch.int64))
+    if variance:
+        a.variance = _p(get("variance", (P, G, O), torch.float64))
+    if ci90:
+        a.ci90 = _p(get("ci90", (P, G, O), torch.float64))
     if traj:
         a.traj_status = _p(get("status", (P, R), torch.int32))
         a.traj_events = _p(get("events", (P, R), torch.int64))

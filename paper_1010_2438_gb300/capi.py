@@ -42,7 +42,7 @@ class cwc_model_desc(ctypes.Structure):
 class cwc_sim_args(ctypes.Structure):
     _fields_ = [("P", _i32), ("R", _i32), ("G", _i32), ("Pi", _i32), ("replica_offset", ctypes.c_uint32),
                 ("rates", _vp), ("init", _vp), ("grid", _vp), ("seed", _u64), ("max_events", _i64),
-                ("states", _vp), ("sums", _vp), ("means", _vp),
+                ("states", _vp), ("sums", _vp), ("means", _vp), ("sumsq", _vp), ("variance", _vp), ("ci90", _vp),
                 ("traj_status", _vp), ("traj_events", _vp), ("traj_hash", _vp), ("traj_final_t", _vp),
                 ("log_cap", _i32), ("log_rule", _vp), ("log_slot", _vp), ("log_t", _vp),
                 ("layout", _i32), ("block_threads", _i32), ("deadline_ns", _i64),

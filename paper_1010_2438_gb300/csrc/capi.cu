@@ -24,6 +24,8 @@ int flat_table_bytes_host(int M, int n_deps);
 int flat_best_threads(const FlatParams& prm, bool queue, bool sens);
 cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order, cudaStream_t stream);
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
+cudaError_t launch_stats(const unsigned long long* sums, const unsigned long long* sumsq, double* variance,
+                         double* ci90, long long n, int R, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, double* grad, int P, int R, int M, cudaStream_t st);
 cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, cudaStream_t stream);
 cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int T, int* blocks);
@@ -76,7 +78,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout: [header 256 B][sums P*G*O int64 if needed][partials Q*M double if needed]
 struct WsLayout {
-  size_t header = 0, sums = 0, partials = 0, slabs = 0, order = 0, total = 0;
+  size_t header = 0, sums = 0, sumsq = 0, partials = 0, slabs = 0, order = 0, total = 0;
+  bool need_sumsq = false;
   bool need_order = false;        // flat queue layout over several sweep points
   bool need_header = false, need_sums = false, need_partials = false;
   int T = 0, blocks = 0;          // compartmentalised launch shape (its slabs are per thread)
@@ -125,11 +128,24 @@ cwc_sim_args resolve_auto(const cwc_model* m, const cwc_sim_args* a) {
   return b;
 }
 
+// Shrink an automatically chosen block size until the grid (one thread per
+// trajectory at most) has at least one block per SM: a small batch would
+// otherwise leave SMs idle with the largest block that fits.
+int cover_sms(int T, long long Q) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return T;
+  while (T > 32 && (Q + T - 1) / T < sms) T -= 32;
+  return T;
+}
+
 WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool sens_partials_given) {
   WsLayout w;
   const int O = m->flat ? m->S : (m->L * m->S + (m->L - 1) * m->S + m->L);
   w.need_header = chosen_layout(a) == CWC_LAYOUT_QUEUE || a->deadline_ns > 0;
-  w.need_sums = !sens && a->means != nullptr && a->sums == nullptr;
+  const bool stats = a->variance != nullptr || a->ci90 != nullptr;
+  w.need_sums = !sens && (a->means != nullptr || stats) && a->sums == nullptr;
+  w.need_sumsq = !sens && stats && a->sumsq == nullptr;
   w.need_partials = sens && !sens_partials_given;
   size_t off = 0;
   if (w.need_header) {
@@ -139,6 +155,10 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
   if (w.need_sums) {
     w.sums = off;
     off = align256(off + (size_t)a->P * a->G * O * sizeof(long long));
+  }
+  if (w.need_sumsq) {
+    w.sumsq = off;
+    off = align256(off + (size_t)a->P * a->G * O * 2 * sizeof(unsigned long long));
   }
   if (w.need_partials) {
     w.partials = off;
@@ -152,7 +172,7 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
   if (!m->flat) {
     const CwcParams prm = cwc_shape_params(m, a);
     const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
-    w.T = a->block_threads > 0 ? a->block_threads : cwc_best_threads(prm, queue);
+    w.T = a->block_threads > 0 ? a->block_threads : cover_sms(cwc_best_threads(prm, queue), prm.Q);
     if (cwc_launch_shape(prm, queue, w.T, &w.blocks) != cudaSuccess) w.blocks = 0;
     w.slab_words = prm.slab_words;
     w.slabs = off;
@@ -214,7 +234,7 @@ FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
 
 int pick_threads(const cwc_model* m, const cwc_sim_args* a, const FlatParams& prm, bool queue, bool sens) {
   if (a->block_threads > 0) return a->block_threads;
-  return flat_best_threads(prm, queue, sens);
+  return cover_sms(flat_best_threads(prm, queue, sens), prm.Q);
 }
 
 }  // namespace
@@ -546,6 +566,13 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
       e = cudaMemsetAsync(sums, 0, (size_t)a->P * a->G * O * sizeof(long long), st);
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sums)");
     }
+    unsigned long long* sumsq = reinterpret_cast<unsigned long long*>(a->sumsq);
+    if (w.need_sumsq) sumsq = reinterpret_cast<unsigned long long*>(ws + w.sumsq);
+    prm.sumsq = sumsq;
+    if (sumsq != nullptr) {
+      e = cudaMemsetAsync(sumsq, 0, (size_t)a->P * a->G * O * 2 * sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sumsq)");
+    }
     prm.traj_status = a->traj_status;
     prm.traj_events = reinterpret_cast<long long*>(a->traj_events);
     prm.traj_hash = reinterpret_cast<unsigned long long*>(a->traj_hash);
@@ -576,6 +603,10 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
   if (!is_sens && a->means != nullptr) {
     e = launch_means(prm.sums, a->means, (long long)a->P * a->G * O, a->R, st);
     if (e != cudaSuccess) return cuda_fail(e, "means kernel launch");
+  }
+  if (!is_sens && (a->variance != nullptr || a->ci90 != nullptr)) {
+    e = launch_stats(prm.sums, prm.sumsq, a->variance, a->ci90, (long long)a->P * a->G * O, a->R, st);
+    if (e != cudaSuccess) return cuda_fail(e, "statistics kernel launch");
   }
   if (is_sens) {
     e = launch_reduce_partials(prm.partials, sens->grad_rates, a->P, a->R, m->M, st);
@@ -673,6 +704,13 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_
     e = cudaMemsetAsync(sums, 0, (size_t)a->P * a->G * m->O * sizeof(long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sums)");
   }
+  unsigned long long* sumsq = reinterpret_cast<unsigned long long*>(a->sumsq);
+  if (w.need_sumsq) sumsq = reinterpret_cast<unsigned long long*>(ws + w.sumsq);
+  prm.sumsq = sumsq;
+  if (sumsq != nullptr) {
+    e = cudaMemsetAsync(sumsq, 0, (size_t)a->P * a->G * m->O * 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sumsq)");
+  }
   const LogConstants lc = make_log_constants();
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
   e = launch_cwc(prm, lc, queue, w.T, w.blocks, st);
@@ -680,6 +718,10 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_
   if (a->means != nullptr) {
     e = launch_means(sums, a->means, (long long)a->P * a->G * m->O, a->R, st);
     if (e != cudaSuccess) return cuda_fail(e, "means kernel launch");
+  }
+  if (a->variance != nullptr || a->ci90 != nullptr) {
+    e = launch_stats(sums, sumsq, a->variance, a->ci90, (long long)a->P * a->G * m->O, a->R, st);
+    if (e != cudaSuccess) return cuda_fail(e, "statistics kernel launch");
   }
   return CWC_OK;
 }
@@ -707,6 +749,9 @@ cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_
   c.states = nullptr;
   c.sums = nullptr;
   c.means = nullptr;
+  c.sumsq = nullptr;
+  c.variance = nullptr;
+  c.ci90 = nullptr;
   c.traj_status = nullptr;
   c.traj_events = nullptr;
   c.traj_hash = nullptr;

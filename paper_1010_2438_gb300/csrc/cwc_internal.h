@@ -84,6 +84,7 @@ struct FlatParams {
   // outputs
   int32_t* states;                 // [Q][G][S]
   unsigned long long* sums;        // [P][G][S]
+  unsigned long long* sumsq;       // [P][G][S][2] 128-bit sums of squares (low, high)
   int32_t* traj_status;
   long long* traj_events;
   unsigned long long* traj_hash;
@@ -118,6 +119,7 @@ struct CwcParams {
   long long max_events;
   int32_t* states;                 // [Q][G][O]
   unsigned long long* sums;        // [P][G][O]
+  unsigned long long* sumsq;       // [P][G][O][2]
   int32_t* traj_status;
   long long* traj_events;
   unsigned long long* traj_hash;

@@ -198,11 +198,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   auto record = [&](int g) {
     int32_t* dst = prm.states != nullptr ? prm.states + ((size_t)q * G + g) * O : nullptr;
     unsigned long long* sdst = prm.sums != nullptr ? prm.sums + ((size_t)p * G + g) * O : nullptr;
+    unsigned long long* qdst = prm.sumsq != nullptr ? prm.sumsq + ((size_t)p * G + g) * O * 2 : nullptr;
     for (int o = 0; o < O; ++o) {
       const long long v = tot[o];
       const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
       if (dst) dst[o] = sv;
       if (sdst) atomicAdd(sdst + o, (unsigned long long)(long long)sv);
+      if (qdst) add_square_u128(qdst + 2 * o, sv);
     }
   };
   auto fill = [&]() {

@@ -149,6 +149,10 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       unsigned long long* dst = prm.sums + ((size_t)p * G + g) * S;
       for (int s = 0; s < S; ++s) atomicAdd(dst + s, (unsigned long long)(long long)CNT(s));
     }
+    if (prm.sumsq != nullptr) {
+      unsigned long long* dst = prm.sumsq + ((size_t)p * G + g) * S * 2;
+      for (int s = 0; s < S; ++s) add_square_u128(dst + 2 * s, CNT(s));
+    }
     if (kSens) {
       const double* gm = prm.grad_means + ((size_t)p * G + g) * S;
       const double* mm = prm.means + ((size_t)p * G + g) * S;

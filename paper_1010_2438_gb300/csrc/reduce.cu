@@ -32,6 +32,53 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double* __re
   if (t == 0) grad[(size_t)p * M + j] = __ddiv_rn(s[0], (double)R);
 }
 
+// Variance and 90 % confidence half-width per (p, g, o) from the exact sums:
+// num = R * sumsq - sum^2 (exact, unsigned 128-bit), variance =
+// RN(num) / (R * (R - 1)), ci90 = z * sqrt(variance / R), each operation
+// rounded to nearest.  RN(num) is assembled with integer operations.
+__device__ double u128_to_double_rn(unsigned __int128 x) {
+  if (x == 0) return 0.0;
+  const unsigned long long hi = (unsigned long long)(x >> 64), lo = (unsigned long long)x;
+  int lead = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long m;
+  if (lead <= 52) {
+    m = lo << (52 - lead);
+  } else {
+    const int sh = lead - 52;
+    m = (unsigned long long)(x >> sh);
+    const unsigned __int128 rem = x & ((((unsigned __int128)1) << sh) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) m += 1ull;
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      lead += 1;
+    }
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(1023 + lead) << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+}
+
+__global__ void stats_kernel(const unsigned long long* __restrict__ sums, const unsigned long long* __restrict__ sumsq,
+                             double* __restrict__ variance, double* __restrict__ ci90, long long n, long long R) {
+  const double Z90 = 1.6448536269514722;   // the double nearest the 0.95 quantile of N(0, 1)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned __int128 s = sums[i];
+    const unsigned __int128 q = ((unsigned __int128)sumsq[2 * i + 1] << 64) | sumsq[2 * i];
+    const unsigned __int128 num = (unsigned __int128)R * q - s * s;
+    const double var = R > 1 ? __ddiv_rn(u128_to_double_rn(num), __dmul_rn((double)R, (double)(R - 1))) : 0.0;
+    if (variance) variance[i] = var;
+    if (ci90) ci90[i] = __dmul_rn(Z90, __dsqrt_rn(__ddiv_rn(var, (double)R)));
+  }
+}
+
+cudaError_t launch_stats(const unsigned long long* sums, const unsigned long long* sumsq, double* variance,
+                         double* ci90, long long n, int R, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  stats_kernel<<<(unsigned)blocks, 256, 0, st>>>(sums, sumsq, variance, ci90, n, (long long)R);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   long long blocks = (n + 255) / 256;

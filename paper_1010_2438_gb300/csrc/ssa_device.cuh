@@ -148,6 +148,15 @@ __device__ __forceinline__ unsigned long long mul_checked(unsigned long long a, 
   return lo;
 }
 
+// Exact 128-bit accumulation of x^2 (x < 2^31) into (low, high): the thread
+// whose add wraps the low word, seen from the value it replaced, carries one
+// into the high word, so the sum is exact whatever the order of the adds.
+__device__ __forceinline__ void add_square_u128(unsigned long long* lohi, int x) {
+  const unsigned long long v = (unsigned long long)(unsigned)x * (unsigned)x;
+  const unsigned long long old = atomicAdd(lohi, v);
+  if (old + v < old) atomicAdd(lohi + 1, 1ull);
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

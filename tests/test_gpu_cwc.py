@@ -139,3 +139,13 @@ def test_cwc3x24_full_size_sampled():
     check_sampled(b, res, sample_indices(b.n_traj, 10, 7))
     col = res["states"].reshape(b.R, b.G, -1).sum(dim=0, dtype=torch.int64)
     assert torch.equal(col, res["sums"][0])
+
+
+def test_cwc_replica_variance_and_interval_bit_exact():
+    b0 = W.cwc3x24(R=40, G=10)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.2, b0.R, b0.seed)
+    g = gpu_run(b, variance=True, ci90=True, means=True)
+    o = oracle.simulate(b, threads=8)
+    s, q, var, ci = oracle.replica_stats(o["states"], b.P, b.R)
+    assert np.array_equal(g["variance"].view(np.int64), var.view(np.int64))
+    assert np.array_equal(g["ci90"].view(np.int64), ci.view(np.int64))

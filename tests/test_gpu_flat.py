@@ -293,3 +293,20 @@ def test_replica_offset_shards_reproduce_one_batch():
         g = gpu_run(b, replica_offset=off)
         sub = {k: v[off:off + cnt] for k, v in o.items()}
         assert_same(g, sub)
+
+
+def test_replica_variance_and_interval_bit_exact():
+    for b in (W.sweep256x256(P=3, R=50), W.flat8x12(R=1), W.flat8x12(R=33)):
+        b = W.Batch(b.model, b.rates, b.init, b.grid * 0.05, b.R, b.seed)
+        g = gpu_run(b, sums=True, means=True, sumsq=True, variance=True, ci90=True)
+        o = oracle.simulate(b, threads=8)
+        s, q, var, ci = oracle.replica_stats(o["states"], b.P, b.R)
+        assert np.array_equal(g["sums"], s.astype(np.int64))
+        qq = g["sumsq"].view(np.uint64)
+        got_q = qq[..., 0].astype(object) + (qq[..., 1].astype(object) << 64)
+        assert np.array_equal(got_q, q)
+        assert np.array_equal(g["variance"].view(np.int64), var.view(np.int64))
+        assert np.array_equal(g["ci90"].view(np.int64), ci.view(np.int64))
+        # variance and the interval alone (sums and squares in the workspace)
+        g2 = gpu_run(b, variance=True, ci90=True)
+        assert np.array_equal(g2["variance"].view(np.int64), var.view(np.int64))
