@@ -31,7 +31,7 @@ cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue,
 cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int T, int* blocks);
 int cwc_best_threads(const CwcParams& prm, bool queue);
 int cwc_table_bytes_host(int M, int n_deps);
-long long cwc_slab_words_host(int S, int L, int C);
+long long cwc_slab_words_host(int S, int L, int C, int M, bool sens);
 }  // namespace cwcgpu
 
 using namespace cwcgpu;
@@ -86,7 +86,7 @@ struct WsLayout {
   long long slab_words = 0;
 };
 
-CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a) {
+CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a, bool sens) {
   CwcParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.S = m->S;
@@ -98,7 +98,8 @@ CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a) {
   prm.n_deps = m->c_n_deps;
   prm.Q = (long long)a->P * a->R;
   prm.smem_table_bytes = cwc_table_bytes_host(m->M, m->c_n_deps);
-  prm.slab_words = cwc_slab_words_host(m->S, m->L, m->C);
+  prm.sens = sens ? 1 : 0;
+  prm.slab_words = cwc_slab_words_host(m->S, m->L, m->C, m->M, sens);
   return prm;
 }
 
@@ -170,7 +171,7 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
     off = align256(off + (size_t)a->P * (sizeof(double) + sizeof(int32_t)));
   }
   if (!m->flat) {
-    const CwcParams prm = cwc_shape_params(m, a);
+    const CwcParams prm = cwc_shape_params(m, a, sens);
     const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
     w.T = a->block_threads > 0 ? a->block_threads : cover_sms(cwc_best_threads(prm, queue), prm.Q);
     if (cwc_launch_shape(prm, queue, w.T, &w.blocks) != cudaSuccess) w.blocks = 0;
@@ -615,7 +616,7 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
   return CWC_OK;
 }
 
-static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_t st);
+static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* sens, cudaStream_t st);
 
 // Scratch of cwc_simulate_noalloc: one statically sized array per device that
 // loads the library.  In host code its name is only a stand-in; the device
@@ -655,19 +656,20 @@ cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void*
   cwc_sim_args b = ra;
   b.workspace = scratch;
   b.workspace_bytes = CWC_NOALLOC_SCRATCH_BYTES;
-  if (!m->flat) return run_cwc(m, &b, static_cast<cudaStream_t>(stream));
+  if (!m->flat) return run_cwc(m, &b, nullptr, static_cast<cudaStream_t>(stream));
   return run_flat(m, &b, nullptr, static_cast<cudaStream_t>(stream));
 }
 
-static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_t st) {
-  const WsLayout w = ws_layout(m, a, false, false);
+static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* sens, cudaStream_t st) {
+  const bool is_sens = sens != nullptr;
+  const WsLayout w = ws_layout(m, a, is_sens, is_sens && sens->partials != nullptr);
   if (w.blocks < 1) return fail(CWC_ERR_CUDA, "could not size the compartmentalised launch");
   if (a->workspace == nullptr || a->workspace_bytes < w.total)
     return fail(CWC_ERR_WORKSPACE, "workspace of " + std::to_string(w.total) + " bytes required");
   if ((reinterpret_cast<uintptr_t>(a->workspace) & 255) != 0)
     return fail(CWC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   unsigned char* ws = static_cast<unsigned char*>(a->workspace);
-  CwcParams prm = cwc_shape_params(m, a);
+  CwcParams prm = cwc_shape_params(m, a, is_sens);
   prm.rules = m->d_ctables;
   prm.P = a->P;
   prm.R = a->R;
@@ -681,15 +683,21 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_
   prm.key1 = (uint32_t)(a->seed >> 32);
   prm.max_events = a->max_events;
   prm.deadline_ns = a->deadline_ns;
-  prm.states = a->states;
-  prm.traj_status = a->traj_status;
-  prm.traj_events = reinterpret_cast<long long*>(a->traj_events);
-  prm.traj_hash = reinterpret_cast<unsigned long long*>(a->traj_hash);
-  prm.traj_final_t = a->traj_final_t;
-  prm.log_cap = a->log_cap;
-  prm.log_rule = a->log_rule;
-  prm.log_slot = a->log_slot;
-  prm.log_t = a->log_t;
+  if (!is_sens) {
+    prm.states = a->states;
+    prm.traj_status = a->traj_status;
+    prm.traj_events = reinterpret_cast<long long*>(a->traj_events);
+    prm.traj_hash = reinterpret_cast<unsigned long long*>(a->traj_hash);
+    prm.traj_final_t = a->traj_final_t;
+    prm.log_cap = a->log_cap;
+    prm.log_rule = a->log_rule;
+    prm.log_slot = a->log_slot;
+    prm.log_t = a->log_t;
+  } else {
+    prm.means = sens->means;
+    prm.grad_means = sens->grad_means;
+    prm.partials = sens->partials != nullptr ? sens->partials : reinterpret_cast<double*>(ws + w.partials);
+  }
   prm.slabs = reinterpret_cast<int32_t*>(ws + w.slabs);
   cudaError_t e;
   if (w.need_header) {
@@ -697,14 +705,14 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_
     e = cudaMemsetAsync(prm.ws, 0, sizeof(WorkspaceHeader), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
   }
-  unsigned long long* sums = reinterpret_cast<unsigned long long*>(a->sums);
+  unsigned long long* sums = is_sens ? nullptr : reinterpret_cast<unsigned long long*>(a->sums);
   if (w.need_sums) sums = reinterpret_cast<unsigned long long*>(ws + w.sums);
   prm.sums = sums;
   if (sums != nullptr) {
     e = cudaMemsetAsync(sums, 0, (size_t)a->P * a->G * m->O * sizeof(long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sums)");
   }
-  unsigned long long* sumsq = reinterpret_cast<unsigned long long*>(a->sumsq);
+  unsigned long long* sumsq = is_sens ? nullptr : reinterpret_cast<unsigned long long*>(a->sumsq);
   if (w.need_sumsq) sumsq = reinterpret_cast<unsigned long long*>(ws + w.sumsq);
   prm.sumsq = sumsq;
   if (sumsq != nullptr) {
@@ -715,6 +723,11 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, cudaStream_
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
   e = launch_cwc(prm, lc, queue, w.T, w.blocks, st);
   if (e != cudaSuccess) return cuda_fail(e, "CWC SSA kernel launch");
+  if (is_sens) {
+    e = launch_reduce_partials(prm.partials, sens->grad_rates, a->P, a->R, m->M, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce kernel launch");
+    return CWC_OK;
+  }
   if (a->means != nullptr) {
     e = launch_means(sums, a->means, (long long)a->P * a->G * m->O, a->R, st);
     if (e != cudaSuccess) return cuda_fail(e, "means kernel launch");
@@ -731,7 +744,7 @@ cwc_status cwc_simulate(const cwc_model* m, const cwc_sim_args* a, void* stream)
   cwc_status st = check_sim_args(m, a);
   if (st != CWC_OK) return st;
   const cwc_sim_args b = resolve_auto(m, a);
-  if (!m->flat) return run_cwc(m, &b, static_cast<cudaStream_t>(stream));
+  if (!m->flat) return run_cwc(m, &b, nullptr, static_cast<cudaStream_t>(stream));
   return run_flat(m, &b, nullptr, static_cast<cudaStream_t>(stream));
 }
 
@@ -782,7 +795,7 @@ cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_
       float ms_best = -1.0f;
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, s);
-        st = m->flat ? run_flat(m, &c, nullptr, s) : run_cwc(m, &c, s);
+        st = m->flat ? run_flat(m, &c, nullptr, s) : run_cwc(m, &c, nullptr, s);
         cudaEventRecord(e1, s);
         if (st != CWC_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -825,7 +838,7 @@ cwc_status cwc_sensitivity(const cwc_model* m, const cwc_sim_args* a, const cwc_
   if (st != CWC_OK) return st;
   if (s == nullptr || s->means == nullptr || s->grad_means == nullptr || s->grad_rates == nullptr)
     return fail(CWC_ERR_INVALID_ARG, "means, grad_means and grad_rates must not be NULL");
-  if (!m->flat) return fail(CWC_ERR_UNSUPPORTED, "sensitivities are implemented for flat models only");
+  if (!m->flat) return run_cwc(m, a, s, static_cast<cudaStream_t>(stream));
   return run_flat(m, a, s, static_cast<cudaStream_t>(stream));
 }
 

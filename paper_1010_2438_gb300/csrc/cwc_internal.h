@@ -128,6 +128,10 @@ struct CwcParams {
   int32_t* log_rule;
   int32_t* log_slot;
   double* log_t;
+  int sens;                        // 1: score replay variant
+  const double* means;             // score replay: [P][G][O]
+  const double* grad_means;        // score replay: [P][G][O]
+  double* partials;                // score replay: [Q][M]
   int32_t* slabs;                  // per launched thread, slab_words each
   long long slab_words;
   WorkspaceHeader* ws;

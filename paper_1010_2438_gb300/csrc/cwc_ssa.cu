@@ -46,13 +46,13 @@ __host__ __device__ inline int cwc_table_bytes(int M, int n_deps) {
 
 __host__ __device__ inline int cwc_thread_bytes(int M) { return (32 + TREE_NODES + M) * 8; }
 
-__host__ __device__ inline long long cwc_slab_words(int S, int L, int C) {
+__host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, bool sens) {
   const long long O = (long long)L * S + (long long)(L - 1) * S + L;
-  long long w = 2LL * C + 2LL * L + 2 + 2 * O + C + 2LL * C * S;
+  long long w = 2LL * C + 2LL * L + 2 + 2 * O + (sens ? 7LL * M : 0) + C + 2LL * C * S;
   return (w + 31) / 32 * 32;
 }
 
-template <bool kQueue>
+template <bool kQueue, bool kSens>
 __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ CwcParams prm,
                                                       const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -107,7 +107,12 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   unsigned long long* labmask = chmask + C;                                       // [L]
   unsigned long long* alive_p = labmask + L;                                      // [1]
   long long* tot = reinterpret_cast<long long*>(alive_p + 1);                     // [O]
-  int32_t* meta = reinterpret_cast<int32_t*>(tot + O);                            // [C]
+  // score replay: int_0^t H_i dt up to tl_i, tl_i, the partials, firings N_i
+  double* Iac = reinterpret_cast<double*>(tot + O);                               // [M]
+  double* tl = Iac + (kSens ? M : 0);                                             // [M]
+  double* part = tl + (kSens ? M : 0);                                            // [M]
+  int32_t* Nf = reinterpret_cast<int32_t*>(part + (kSens ? M : 0));               // [M]
+  int32_t* meta = Nf + (kSens ? M : 0);                                           // [C]
   int32_t* wrap = meta + C;                                                       // [C][S]
   int32_t* content = wrap + (size_t)C * S;                                        // [C][S]
 
@@ -206,6 +211,22 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       if (sdst) atomicAdd(sdst + o, (unsigned long long)(long long)sv);
       if (qdst) add_square_u128(qdst + 2 * o, sv);
     }
+    if (kSens) {
+      const double* gm = prm.grad_means + ((size_t)p * G + g) * O;
+      const double* mm = prm.means + ((size_t)p * G + g) * O;
+      double cg = 0.0;
+      for (int o = 0; o < O; ++o) {
+        const long long v = tot[o];
+        const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
+        cg = __dadd_rn(cg, __dmul_rn(gm[o], __dadd_rn((double)sv, -mm[o])));
+      }
+      const double gt = prm.grid[g];
+      for (int i = 0; i < M; ++i) {
+        const double Ig = __dadd_rn(Iac[i], __dmul_rn(u63_to_double_rn(HV(i)), __dadd_rn(gt, -tl[i])));
+        const double Si = __dadd_rn(__ddiv_rn((double)Nf[i], kp[i]), -Ig);
+        part[i] = __dadd_rn(part[i], __dmul_rn(cg, Si));
+      }
+    }
   };
   auto fill = [&]() {
     for (; gi < G; ++gi) record(gi);
@@ -216,6 +237,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     if (prm.traj_events) prm.traj_events[q] = (long long)n;
     if (prm.traj_hash) prm.traj_hash[q] = h;
     if (prm.traj_final_t) prm.traj_final_t[q] = t;
+    if (kSens)
+      for (int i = 0; i < M; ++i) prm.partials[(size_t)q * M + i] = part[i];
+  };
+  // fold H_i's contribution since tl_i into the integral before H_i changes
+  auto integrate = [&](int i, double tnow) {
+    Iac[i] = __dadd_rn(Iac[i], __dmul_rn(u63_to_double_rn(HV(i)), __dadd_rn(tnow, -tl[i])));
+    tl[i] = tnow;
   };
 
   // load and validate the initial term (slot image), build masks, H and tree
@@ -234,6 +262,14 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     for (int j = 0; j < M; ++j) {
       const long long kb = dbits(kp[j]);
       if (!(kb > 0 && kb < 0x7FF0000000000000ll)) bad = true;
+    }
+    if (kSens) {
+      for (int i = 0; i < M; ++i) {
+        Iac[i] = 0.0;
+        tl[i] = 0.0;
+        part[i] = 0.0;
+        Nf[i] = 0;
+      }
     }
     const int W = 3 + 2 * S;
     const int32_t* img = prm.init + (size_t)(prm.Pi == 1 ? 0 : p) * C * W;
@@ -470,6 +506,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   auto step = [&]() -> bool {
     if (ovf) {
       status = TS_PROP_OVERFLOW;
+      if (kSens)
+        for (int i = 0; i < M; ++i) HV(i) = 0ull;
       fill();
       return true;
     }
@@ -487,6 +525,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     if (a0b >= 0x7FF0000000000000ll) {
       status = TS_PROP_OVERFLOW;
+      if (kSens)
+        for (int i = 0; i < M; ++i) HV(i) = 0ull;
       fill();
       return true;
     }
@@ -588,13 +628,18 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       return true;
     }
     const bool structural = rec[CR_KIND] >= 2;
+    if (kSens) Nf[j] += 1;
     if (structural) {
-      for (int i = 0; i < M; ++i) HV(i) = total_h(i);
+      for (int i = 0; i < M; ++i) {
+        if (kSens) integrate(i, tn);
+        HV(i) = total_h(i);
+      }
       rebuild_tree();
     } else {
       const int doff = rec[CR_DEPOFF], dcnt = rec[CR_DEPCNT];
       for (int e = 0; e < dcnt; ++e) {
         const int i = s_deps[doff + e];
+        if (kSens) integrate(i, tn);
         HV(i) = total_h(i);
       }
       if (B == 1) {
@@ -659,9 +704,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
 
 // ---------------------------------------------------------------------------
 
-template <bool kQueue>
+template <bool kQueue, bool kSens>
 static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, size_t* smem_out) {
-  auto kern = cwc_ssa_kernel<kQueue>;
+  auto kern = cwc_ssa_kernel<kQueue, kSens>;
   const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * cwc_thread_bytes(prm.M);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -684,7 +729,10 @@ static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, si
 // the resident capacity, so the term slabs number threads, not trajectories.
 cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int T, int* blocks) {
   size_t smem = 0;
-  return queue ? cwc_config_t<true>(prm, T, blocks, &smem) : cwc_config_t<false>(prm, T, blocks, &smem);
+  const bool sens = prm.sens != 0;
+  if (queue)
+    return sens ? cwc_config_t<true, true>(prm, T, blocks, &smem) : cwc_config_t<true, false>(prm, T, blocks, &smem);
+  return sens ? cwc_config_t<false, true>(prm, T, blocks, &smem) : cwc_config_t<false, false>(prm, T, blocks, &smem);
 }
 
 int cwc_best_threads(const CwcParams& prm, bool queue) {
@@ -693,11 +741,11 @@ int cwc_best_threads(const CwcParams& prm, bool queue) {
     const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * cwc_thread_bytes(prm.M);
     if (smem > 227 * 1024) break;
     int per_sm = 0;
-    cudaError_t e = queue ? cudaFuncSetAttribute(cwc_ssa_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                          : cudaFuncSetAttribute(cwc_ssa_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = queue ? cudaFuncSetAttribute(cwc_ssa_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(cwc_ssa_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) break;
-    e = queue ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<true>, T, smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<false>, T, smem);
+    e = queue ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<true, false>, T, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<false, false>, T, smem);
     if (e != cudaSuccess) break;
     const int warps = per_sm * T / 32;
     if (warps >= best_warps) {
@@ -709,18 +757,30 @@ int cwc_best_threads(const CwcParams& prm, bool queue) {
 }
 
 int cwc_table_bytes_host(int M, int n_deps) { return cwc_table_bytes(M, n_deps); }
-long long cwc_slab_words_host(int S, int L, int C) { return cwc_slab_words(S, L, C); }
+long long cwc_slab_words_host(int S, int L, int C, int M, bool sens) { return cwc_slab_words(S, L, C, M, sens); }
 
 cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks,
                        cudaStream_t stream) {
   size_t smem = 0;
   int b = 0;
-  cudaError_t e = queue ? cwc_config_t<true>(prm, T, &b, &smem) : cwc_config_t<false>(prm, T, &b, &smem);
-  if (e != cudaSuccess) return e;
+  const bool sens = prm.sens != 0;
+  cudaError_t e;
   if (queue)
-    cwc_ssa_kernel<true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+    e = sens ? cwc_config_t<true, true>(prm, T, &b, &smem) : cwc_config_t<true, false>(prm, T, &b, &smem);
   else
-    cwc_ssa_kernel<false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+    e = sens ? cwc_config_t<false, true>(prm, T, &b, &smem) : cwc_config_t<false, false>(prm, T, &b, &smem);
+  if (e != cudaSuccess) return e;
+  if (queue) {
+    if (sens)
+      cwc_ssa_kernel<true, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+    else
+      cwc_ssa_kernel<true, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  } else {
+    if (sens)
+      cwc_ssa_kernel<false, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+    else
+      cwc_ssa_kernel<false, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  }
   return cudaGetLastError();
 }
 

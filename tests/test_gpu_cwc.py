@@ -149,3 +149,40 @@ def test_cwc_replica_variance_and_interval_bit_exact():
     s, q, var, ci = oracle.replica_stats(o["states"], b.P, b.R)
     assert np.array_equal(g["variance"].view(np.int64), var.view(np.int64))
     assert np.array_equal(g["ci90"].view(np.int64), ci.view(np.int64))
+
+
+def test_cwc_sensitivity_partials_match_oracle():
+    """Score replay on a compartment model (structural events included):
+    per-trajectory partials within 1e-9 * (|x| + mean |x|) of the oracle (the
+    integral of H_j is accumulated lazily on the GPU and at every event in the
+    oracle, so they differ by FP64 rounding only)."""
+    b0 = W.cwc3x24(R=32, G=8)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.5, b0.R, b0.seed)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    means = torch.from_numpy(oracle.mean_observables(b, threads=8)).cuda()
+    rng = np.random.default_rng(11)
+    gm = torch.from_numpy(rng.standard_normal((1, b.G, cm.n_observables)) * 1e-3).cuda()
+    res = api.sensitivity(cm, rates, init, grid, b.R, b.seed, means, gm, partials=True)
+    torch.cuda.synchronize()
+    gp = res["partials"].cpu().numpy().reshape(b.R, -1)
+    ograd, op = oracle.sensitivity(b, means.cpu().numpy(), gm.cpu().numpy(), threads=8)
+    scale = np.mean(np.abs(op))
+    assert scale > 0
+    assert np.all(np.abs(gp - op) <= 1e-9 * (np.abs(op) + scale))
+    gg = res["grad_rates"].cpu().numpy()
+    assert np.all(np.abs(gg - ograd) <= 1e-9 * (np.abs(ograd) + scale))
+
+
+def test_cwc_autograd_function():
+    b0 = W.cwc3x24(R=64, G=6)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.2, b0.R, b0.seed)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    k = rates.clone().requires_grad_(True)
+    m = api.mean_observables(k, cm, init, grid, b.R, b.seed)
+    om = oracle.mean_observables(b, threads=8)
+    assert np.array_equal(m.detach().cpu().numpy().view(np.int64), om.view(np.int64))
+    (m * 0.001).sum().backward()
+    og, _ = oracle.sensitivity(b, om, np.full(om.shape, 0.001), threads=8)
+    assert np.allclose(k.grad.cpu().numpy(), og, rtol=1e-9, atol=1e-9 * np.abs(og).max())
