@@ -205,6 +205,24 @@ def measure_extras(dev):
                               "length_spread": float((evp.max() / evp.min()).item()),
                               "workload": "256 rate vectors x 256 replicas, flat32x64 network, 1000-point grid"}
     del g, out
+    # the paper's n-species Lotka-Volterra family (its single-instance table runs n = 2 ... 32)
+    lv = {}
+    for nsp in (2, 4, 8, 16, 32):
+        b = W.lotka_volterra(nsp, R=32768, G=100, T=1.0)
+        cm = api.CompiledModel(b.model)
+        rates, init, grid = api.device_inputs(b, dev)
+        keep = {}
+
+        def run_lv():
+            keep["o"] = api.simulate(cm, rates, init, grid, b.R, b.seed, states=True, out=keep.get("o"))
+            return keep["o"]
+
+        out, sec = _timed(run_lv)
+        ev = int(out["events"].sum().item())
+        lv[str(nsp)] = {"events_per_s": ev / sec, "events": ev, "seconds": sec}
+        del keep, out
+    extras["lotka_volterra"] = {"by_species": lv, "workload": "n-species Lotka-Volterra chain, 32768 replicas, "
+                                                            "horizon 1, 100-point grid (Gillespie 1977 constants)"}
     # likelihood-ratio sensitivities: 16 species x 24 reactions, 131,072 replicas, 100-point grid
     b = W.flat16x24()
     cm = api.CompiledModel(b.model)

@@ -168,6 +168,18 @@ enum {
  *   log_rule/log_slot int32, log_t double [P][R][log_cap]: the first log_cap
  *                                      events of each trajectory
  *
+ *   checkpoint    int32 [P][R][cwc_checkpoint_words()]  flat models: the
+ *                 state of each trajectory when it stops (time, event hash,
+ *                 event count, next grid point, status, counts).  With a
+ *                 checkpoint buffer a trajectory stopped by the deadline
+ *                 leaves its remaining grid points unrecorded, and a later
+ *                 call with resume = 1 (same batch, seed, grid and outputs)
+ *                 continues every trajectory whose saved status is
+ *                 CWC_TRAJ_TIMEOUT from where it stopped and leaves the others
+ *                 untouched; the result equals an uninterrupted run bit for
+ *                 bit, because the random streams are keyed by the event
+ *                 index (the stop / restart of instances in Sec. 5.2).  Not
+ *                 combinable with sums, means, sumsq, variance or ci90.
  *   layout, block_threads (0 = automatic), deadline_ns (0 = none: a
  *   trajectory still running when this many nanoseconds of device time have
  *   passed since the launch stops with CWC_TRAJ_TIMEOUT).
@@ -209,6 +221,8 @@ typedef struct {
   int32_t* log_rule;
   int32_t* log_slot;
   double* log_t;
+  int32_t* checkpoint;
+  int32_t resume;
   int32_t layout;
   int32_t block_threads;
   int64_t deadline_ns;
@@ -240,6 +254,9 @@ typedef struct {
  */
 #define CWC_NOALLOC_SCRATCH_BYTES (1u << 20)
 cwc_status cwc_simulate_noalloc(const cwc_model* model, const cwc_sim_args* args, void* stream);
+
+/* int32 words of one trajectory's checkpoint record (flat models; -1 otherwise). */
+int32_t cwc_checkpoint_words(const cwc_model* model);
 
 /* Workspace bytes cwc_simulate needs for these arguments (0 if none). */
 cwc_status cwc_simulate_workspace_size(const cwc_model* model, const cwc_sim_args* args, size_t* bytes);

@@ -95,7 +95,8 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
              max_events: int = (1 << 32) - 1, *, states: bool = True, sums: bool = False, means: bool = False,
              sumsq: bool = False, variance: bool = False, ci90: bool = False,
              traj: bool = True, log_cap: int = 0, layout: int = capi.CWC_LAYOUT_AUTO, block_threads: int = 0,
-             deadline_ns: int = 0, replica_offset: int = 0, stream: Optional[torch.cuda.Stream] = None,
+             deadline_ns: int = 0, replica_offset: int = 0, checkpoint: bool = False, resume: bool = False,
+             stream: Optional[torch.cuda.Stream] = None,
              out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
     """Run P x R trajectories (cwc_simulate) and return the requested outputs.
 
@@ -137,6 +138,12 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
         a.log_rule = _p(get("log_rule", (P, R, log_cap), torch.int32))
         a.log_slot = _p(get("log_slot", (P, R, log_cap), torch.int32))
         a.log_t = _p(get("log_t", (P, R, log_cap), torch.float64))
+    if checkpoint or resume:
+        words = capi.cwc_checkpoint_words(cm.handle)
+        if words < 0:
+            raise ValueError("checkpoints are implemented for flat models only")
+        a.checkpoint = _p(get("checkpoint", (P, R, words), torch.int32))
+        a.resume = 1 if resume else 0
     nbytes = capi.cwc_simulate_workspace_size(cm.handle, a)
     ws = res.get("_workspace")
     if nbytes and (ws is None or ws.numel() < nbytes + 256):

@@ -25,7 +25,7 @@ CWC_LAYOUT_AUTO, CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE = range(3)
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = ("cwc_model_create", "cwc_model_destroy", "cwc_model_num_observables", "cwc_simulate_workspace_size",
             "cwc_simulate", "cwc_simulate_noalloc", "cwc_sensitivity_workspace_size", "cwc_sensitivity",
-            "cwc_autotune", "cwc_last_error", "cwc_version")
+            "cwc_autotune", "cwc_checkpoint_words", "cwc_last_error", "cwc_version")
 CWC_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 _vp = ctypes.c_void_p
@@ -45,6 +45,7 @@ class cwc_sim_args(ctypes.Structure):
                 ("states", _vp), ("sums", _vp), ("means", _vp), ("sumsq", _vp), ("variance", _vp), ("ci90", _vp),
                 ("traj_status", _vp), ("traj_events", _vp), ("traj_hash", _vp), ("traj_final_t", _vp),
                 ("log_cap", _i32), ("log_rule", _vp), ("log_slot", _vp), ("log_t", _vp),
+                ("checkpoint", _vp), ("resume", _i32),
                 ("layout", _i32), ("block_threads", _i32), ("deadline_ns", _i64),
                 ("workspace", _vp), ("workspace_bytes", ctypes.c_size_t)]
 
@@ -94,6 +95,8 @@ def lib() -> ctypes.CDLL:
         L.cwc_autotune.argtypes = [_vp, ctypes.POINTER(cwc_sim_args), _i64, _vp, ctypes.POINTER(_i32),
                                    ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]
         L.cwc_autotune.restype = ctypes.c_int
+        L.cwc_checkpoint_words.argtypes = [_vp]
+        L.cwc_checkpoint_words.restype = _i32
         L.cwc_last_error.argtypes = []
         L.cwc_last_error.restype = ctypes.c_char_p
         L.cwc_version.argtypes = []
@@ -124,6 +127,10 @@ def cwc_model_create(desc: cwc_model_desc) -> int:
 def cwc_model_destroy(handle: Optional[int]) -> None:
     if handle:
         lib().cwc_model_destroy(handle)
+
+
+def cwc_checkpoint_words(handle: int) -> int:
+    return lib().cwc_checkpoint_words(handle)
 
 
 def cwc_model_num_observables(handle: int) -> int:

@@ -199,6 +199,13 @@ cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
   if (a->block_threads != 0 && (a->block_threads < 32 || a->block_threads > 256 || a->block_threads % 32 != 0))
     return fail(CWC_ERR_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 256]");
   if (a->deadline_ns < 0) return fail(CWC_ERR_INVALID_ARG, "deadline_ns must be >= 0");
+  if (a->resume != 0 && a->resume != 1) return fail(CWC_ERR_INVALID_ARG, "resume must be 0 or 1");
+  if (a->resume && a->checkpoint == nullptr) return fail(CWC_ERR_INVALID_ARG, "resume needs the checkpoint buffer");
+  if (a->checkpoint != nullptr &&
+      (a->sums != nullptr || a->means != nullptr || a->sumsq != nullptr || a->variance != nullptr || a->ci90 != nullptr))
+    return fail(CWC_ERR_INVALID_ARG, "checkpoints cannot be combined with reductions over replicas");
+  if (a->checkpoint != nullptr && !m->flat)
+    return fail(CWC_ERR_UNSUPPORTED, "checkpoints are implemented for flat models only");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -229,6 +236,8 @@ FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
   prm.key1 = (uint32_t)(a->seed >> 32);
   prm.max_events = a->max_events;
   prm.deadline_ns = a->deadline_ns;
+  prm.ckpt = a->checkpoint;
+  prm.resume = a->resume;
   prm.smem_table_bytes = flat_table_bytes_host(m->M, m->n_deps);
   return prm;
 }
@@ -515,6 +524,11 @@ void cwc_model_destroy(cwc_model* m) {
   delete m;
 }
 
+int32_t cwc_checkpoint_words(const cwc_model* m) {
+  if (m == nullptr || !m->flat) return -1;
+  return m->S + CKPT_HEADER_WORDS;
+}
+
 int32_t cwc_model_num_observables(const cwc_model* m) {
   if (m == nullptr) return -1;
   return m->O;
@@ -773,6 +787,8 @@ cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_
   c.log_rule = nullptr;
   c.log_slot = nullptr;
   c.log_t = nullptr;
+  c.checkpoint = nullptr;
+  c.resume = 0;
   c.deadline_ns = 0;
   const int64_t cap = tune_events == 0 ? 2048 : tune_events;
   c.max_events = std::min<int64_t>(a->max_events, cap);
@@ -838,6 +854,8 @@ cwc_status cwc_sensitivity(const cwc_model* m, const cwc_sim_args* a, const cwc_
   if (st != CWC_OK) return st;
   if (s == nullptr || s->means == nullptr || s->grad_means == nullptr || s->grad_rates == nullptr)
     return fail(CWC_ERR_INVALID_ARG, "means, grad_means and grad_rates must not be NULL");
+  if (a->checkpoint != nullptr || a->resume != 0)
+    return fail(CWC_ERR_INVALID_ARG, "sensitivities do not take checkpoints");
   if (!m->flat) return run_cwc(m, a, s, static_cast<cudaStream_t>(stream));
   return run_flat(m, a, s, static_cast<cudaStream_t>(stream));
 }

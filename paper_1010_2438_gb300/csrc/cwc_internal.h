@@ -49,6 +49,11 @@ constexpr int CR_KIND = 0, CR_CTX = 1, CR_CHILD = 2, CR_NREAC = 3, CR_REAC = 4, 
               CR_D1 = 18, CR_ND2 = 26, CR_D2 = 27, CR_DEPOFF = 35, CR_DEPCNT = 36, CR_LEAFMASK = 37, CR_NODEMASK = 38;
 constexpr int CWC_MAX_SLOTS = 64;
 
+// Checkpoint record of a flat trajectory (int32 words): time (double, words
+// 0-1), event hash (words 2-3), event count, next grid point, status, unused,
+// then the S counts.
+constexpr int CKPT_HEADER_WORDS = 8;
+
 // Trajectory status codes (same values as CWC_TRAJ_* in the C header).
 enum : int32_t {
   TS_OK = 0, TS_ABSORBED = 1, TS_INT_OVERFLOW = 2, TS_PROP_OVERFLOW = 3, TS_CAPACITY = 4,
@@ -99,6 +104,8 @@ struct FlatParams {
   double* partials;                // [Q][M]
   // scheduling
   WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)
+  int32_t* ckpt;                   // [Q][S + CKPT_HEADER_WORDS] trajectory checkpoints (or null)
+  int resume;                      // 1: continue the TIMEOUT trajectories of ckpt
   const int32_t* order;            // queue mode: sweep points, longest expected first (or null)
   long long deadline_ns;
   int smem_table_bytes;            // bytes of the shared-memory table region

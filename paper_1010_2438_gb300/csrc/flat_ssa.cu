@@ -206,6 +206,16 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   };
 
   auto finalize = [&]() {
+    if (prm.ckpt != nullptr) {
+      int32_t* rec = prm.ckpt + (size_t)q * (S + CKPT_HEADER_WORDS);
+      *reinterpret_cast<double*>(rec) = t;
+      *reinterpret_cast<unsigned long long*>(rec + 2) = h;
+      rec[4] = (int32_t)n;
+      rec[5] = gi;
+      rec[6] = status;
+      rec[7] = 0;
+      for (int s = 0; s < S; ++s) rec[CKPT_HEADER_WORDS + s] = CNT(s);
+    }
     if (prm.traj_status) prm.traj_status[q] = status;
     if (prm.traj_events) prm.traj_events[q] = (long long)n;
     if (prm.traj_hash) prm.traj_hash[q] = h;
@@ -215,8 +225,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     }
   };
 
-  // set up trajectory q; returns true if it ends immediately (bad input)
-  auto start = [&]() -> bool {
+  // set up trajectory q: 0 = running, 1 = ended at once (bad input),
+  // 2 = nothing to do (resuming, and this trajectory did not stop on the deadline)
+  auto start = [&]() -> int {
     p = (int)(q / prm.R);
     r = (int)(q - (long long)p * prm.R);
     kp = prm.rates + (size_t)p * M;
@@ -233,6 +244,17 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       if (!(kb > 0 && kb < 0x7FF0000000000000ll)) bad = true;
     }
     const int32_t* x0 = prm.init + (size_t)(prm.Pi == 1 ? 0 : p) * S;
+    if (prm.resume) {
+      const int32_t* rec = prm.ckpt + (size_t)q * (S + CKPT_HEADER_WORDS);
+      if (rec[6] != TS_TIMEOUT) return 2;
+      t = *reinterpret_cast<const double*>(rec);
+      h = *reinterpret_cast<const unsigned long long*>(rec + 2);
+      n = (unsigned)rec[4];
+      gi = rec[5];
+      if (gi < 0 || gi > G) bad = true;
+      gbits = gi < G && gi >= 0 ? dbits(prm.grid[gi]) : 0;
+      x0 = rec + CKPT_HEADER_WORDS;
+    }
     for (int s = 0; s < S; ++s) {
       const int v = x0[s];
       if (v < 0) bad = true;
@@ -247,7 +269,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
         int32_t* dst = prm.states + (size_t)q * G * S;
         for (long long e = 0; e < (long long)G * S; ++e) dst[e] = 0;
       }
-      return true;
+      return 1;
     }
     if (kSens) {
       for (int i = 0; i < M; ++i) {
@@ -263,7 +285,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       const double b = nd < 16 ? LEAF(2 * nd + 1) : NODE(2 * nd - 31);
       NODE(nd) = __dadd_rn(a, b);
     }
-    return false;
+    return 0;
   };
 
   // one event (or the end of the trajectory); returns true when it ended
@@ -296,7 +318,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     }
     if ((n & 1023u) == 0u && deadline != ~0ull && globaltimer_ns() > deadline) {
       status = TS_TIMEOUT;
-      fill();
+      if (prm.ckpt == nullptr) fill();   // with a checkpoint the rest is recorded on resume
       return true;
     }
     const uint4 w = philox4x32_10(make_uint4(n, 0u, (uint32_t)r + prm.r_offset, (uint32_t)p), prm.key0, prm.key1);
@@ -436,10 +458,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
         first = false;
       }
       if (q >= Q) break;
-      if (start()) {
-        finalize();
-        continue;
-      }
+      const int st0 = start();
+      if (st0 == 1) finalize();
+      if (st0 != 0) continue;
       need_new = false;
     }
     if (step()) {

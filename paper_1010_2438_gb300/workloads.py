@@ -523,3 +523,27 @@ def cwc3x24(R: int = 16384, G: int = 500, use_calibrated: bool = True) -> Batch:
         if Tc is not None:
             T = Tc
     return Batch(model, rates[None, :], img[None], uniform_grid(T, G), R, 103, name="cwc3x24")
+
+
+# ----------------------------------------------------------------------------
+# n-species Lotka-Volterra chain: the model family of the paper's single-
+# instance experiments (Sec. 5.1, n = 2 ... 32; n = 2 is prey-predator).  The
+# paper gives neither rates nor counts; the reading here is the chain
+# S1 -> 2 S1, S_i + S_(i+1) -> 2 S_(i+1) (i < n), S_n -> 0, with the constants
+# of Gillespie's 1977 prey-predator example (c1 = 10 per prey, c2 = 0.01,
+# c3 = 10) and 1000 molecules of every species.
+# ----------------------------------------------------------------------------
+
+def lotka_volterra_model(n: int) -> Model:
+    reactions: List[Reaction] = [({0: 1}, {0: 2})]
+    for i in range(n - 1):
+        reactions.append(({i: 1, i + 1: 1}, {i + 1: 2}))
+    reactions.append(({n - 1: 1}, {}))
+    return flat_model(n, reactions, "lotka_volterra_%d" % n)
+
+
+def lotka_volterra(n: int, R: int = 65536, G: int = 100, T: float = 1.0, seed: int = 300) -> Batch:
+    model = lotka_volterra_model(n)
+    rates = np.array([[10.0] + [0.01] * (n - 1) + [10.0]], np.float64)
+    init = np.full((1, n), 1000, np.int32)
+    return Batch(model, rates, init, uniform_grid(T, G), R, seed + n, name="lotka_volterra_%d" % n)

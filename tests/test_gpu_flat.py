@@ -310,3 +310,53 @@ def test_replica_variance_and_interval_bit_exact():
         # variance and the interval alone (sums and squares in the workspace)
         g2 = gpu_run(b, variance=True, ci90=True)
         assert np.array_equal(g2["variance"].view(np.int64), var.view(np.int64))
+
+
+@pytest.mark.parametrize("n", [2, 5, 32, 33])
+def test_lotka_volterra_chain_bit_exact(n):
+    """The paper's n-species Lotka-Volterra family; n = 33 gives 34 rules,
+    i.e. two-rule leaf blocks with a ragged last block."""
+    b = W.lotka_volterra(n, R=48, G=20, T=0.05)
+    g = gpu_run(b, log_cap=64)
+    o = oracle.simulate(b, threads=8, log_cap=64)
+    assert_same(g, o)
+    assert np.array_equal(g["log_rule"], o["log_rule"])
+
+
+def test_checkpoint_resume_reproduces_the_uninterrupted_run():
+    """Stop every trajectory on a short deadline, then resume from the
+    checkpoints until none is left: states, hashes, event counts and final
+    times equal an uninterrupted run bit for bit (Sec. 5.2: instances that can
+    be stopped and restarted)."""
+    b0 = W.flat32x64(R=2048)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.3, b0.R, b0.seed)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    ref = api.simulate(cm, rates, init, grid, b.R, b.seed)
+    out = api.simulate(cm, rates, init, grid, b.R, b.seed, checkpoint=True, deadline_ns=3_000_000,
+                       layout=capi.CWC_LAYOUT_QUEUE)
+    torch.cuda.synchronize()
+    first = int((out["status"] == capi.CWC_TRAJ_TIMEOUT).sum())
+    assert first > 0
+    rounds = 0
+    while bool((out["status"] == capi.CWC_TRAJ_TIMEOUT).any()):
+        out = api.simulate(cm, rates, init, grid, b.R, b.seed, resume=True, deadline_ns=3_000_000,
+                           layout=capi.CWC_LAYOUT_QUEUE, out=out)
+        torch.cuda.synchronize()
+        rounds += 1
+        assert rounds < 400
+    assert rounds > 0
+    for k in ("states", "events", "hash", "status", "final_t"):
+        assert torch.equal(out[k], ref[k]), k
+
+
+def test_checkpoint_argument_rules():
+    b = W.flat8x12(R=4)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    with pytest.raises(capi.CwcError, match="reductions"):
+        api.simulate(cm, rates, init, grid, b.R, b.seed, checkpoint=True, sums=True)
+    a = api._sim_args(cm, rates, init, grid, b.R, b.seed, 10, capi.CWC_LAYOUT_STATIC, 0, 0)
+    a.resume = 1
+    with pytest.raises(capi.CwcError, match="checkpoint"):
+        capi.cwc_simulate(cm.handle, a, 0)
