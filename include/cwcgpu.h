@@ -168,9 +168,11 @@ enum {
  *   log_rule/log_slot int32, log_t double [P][R][log_cap]: the first log_cap
  *                                      events of each trajectory
  *
- *   checkpoint    int32 [P][R][cwc_checkpoint_words()]  flat models: the
- *                 state of each trajectory when it stops (time, event hash,
- *                 event count, next grid point, status, counts).  With a
+ *   checkpoint    int32 [P][R][cwc_checkpoint_words()]  the state of each
+ *                 trajectory when it stops: time, event hash, event count,
+ *                 next grid point, status, then the counts (flat models) or
+ *                 the term as a slot image in the layout of init
+ *                 (compartmentalised models).  With a
  *                 checkpoint buffer a trajectory stopped by the deadline
  *                 leaves its remaining grid points unrecorded, and a later
  *                 call with resume = 1 (same batch, seed, grid and outputs)
@@ -182,7 +184,9 @@ enum {
  *                 combinable with sums, means, sumsq, variance or ci90.
  *   layout, block_threads (0 = automatic), deadline_ns (0 = none: a
  *   trajectory still running when this many nanoseconds of device time have
- *   passed since the launch stops with CWC_TRAJ_TIMEOUT).
+ *   passed since the launch stops with CWC_TRAJ_TIMEOUT.  The clock is read
+ *   every 1024 events, and not before the trajectory has applied 1024 events
+ *   in this call, so every call advances each unfinished trajectory).
  *   workspace / workspace_bytes: caller-owned device scratch of at least
  *   cwc_simulate_workspace_size() bytes, 256-byte aligned (NULL if that size
  *   is 0).
@@ -255,7 +259,8 @@ typedef struct {
 #define CWC_NOALLOC_SCRATCH_BYTES (1u << 20)
 cwc_status cwc_simulate_noalloc(const cwc_model* model, const cwc_sim_args* args, void* stream);
 
-/* int32 words of one trajectory's checkpoint record (flat models; -1 otherwise). */
+/* int32 words of one trajectory's checkpoint record: 8 + S for flat models,
+ * 8 + C * (3 + 2S) for compartmentalised ones; -1 for a NULL model. */
 int32_t cwc_checkpoint_words(const cwc_model* model);
 
 /* Workspace bytes cwc_simulate needs for these arguments (0 if none). */

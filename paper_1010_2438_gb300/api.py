@@ -140,8 +140,6 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
         a.log_t = _p(get("log_t", (P, R, log_cap), torch.float64))
     if checkpoint or resume:
         words = capi.cwc_checkpoint_words(cm.handle)
-        if words < 0:
-            raise ValueError("checkpoints are implemented for flat models only")
         a.checkpoint = _p(get("checkpoint", (P, R, words), torch.int32))
         a.resume = 1 if resume else 0
     nbytes = capi.cwc_simulate_workspace_size(cm.handle, a)
@@ -153,6 +151,38 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
     a.workspace_bytes = nbytes
     capi.cwc_simulate(cm.handle, a, _stream_handle(stream))
     return res
+
+
+def simulate_sliced(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: torch.Tensor, R: int,
+                    seed: int, max_events: int = (1 << 32) - 1, *, slice_ns: int, max_slices: int = 1 << 20,
+                    on_slice=None, stream: Optional[torch.cuda.Stream] = None, **kw):
+    """Run the batch as a sequence of launches of at most ``slice_ns`` of
+    device time each: every launch stops the trajectories still running at
+    its deadline and saves them in the checkpoint buffer, the next resumes
+    them (the time-sliced, stoppable instances of Sec. 5.2).  Between slices
+    the GPU is free for other work on other streams, and ``on_slice(i,
+    remaining)`` sees the number of trajectories still to finish.  Returns
+    (outputs, slices); the outputs equal one uninterrupted ``simulate`` bit
+    for bit.  Takes ``simulate``'s keyword arguments except the reductions
+    over replicas (which checkpoints exclude)."""
+    if slice_ns <= 0:
+        raise ValueError("slice_ns must be > 0")
+    kw.pop("traj", None)
+    out = simulate(cm, rates, init, grid, R, seed, max_events, traj=True, checkpoint=True, deadline_ns=slice_ns,
+                   stream=stream, **kw)
+    slices = 1
+    while True:
+        (stream or torch.cuda.current_stream(rates.device)).synchronize()
+        remaining = int((out["status"] == capi.CWC_TRAJ_TIMEOUT).sum().item())
+        if on_slice is not None:
+            on_slice(slices, remaining)
+        if remaining == 0:
+            return out, slices
+        if slices >= max_slices:
+            raise RuntimeError("%d trajectories still running after %d slices" % (remaining, slices))
+        out = simulate(cm, rates, init, grid, R, seed, max_events, traj=True, resume=True, deadline_ns=slice_ns,
+                       stream=stream, out=out, **kw)
+        slices += 1
 
 
 def sensitivity(cm: CompiledModel, rates, init, grid, R: int, seed: int, means: torch.Tensor,

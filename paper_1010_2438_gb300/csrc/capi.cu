@@ -204,8 +204,6 @@ cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
   if (a->checkpoint != nullptr &&
       (a->sums != nullptr || a->means != nullptr || a->sumsq != nullptr || a->variance != nullptr || a->ci90 != nullptr))
     return fail(CWC_ERR_INVALID_ARG, "checkpoints cannot be combined with reductions over replicas");
-  if (a->checkpoint != nullptr && !m->flat)
-    return fail(CWC_ERR_UNSUPPORTED, "checkpoints are implemented for flat models only");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -367,11 +365,24 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       rec[CR_DEPOFF] = (int32_t)deps_all.size();
       uint32_t leafmask = 0, nodemask = 0;
       int cnt = 0;
-      if (d->kind[j] == CWC_RULE_LOCAL || d->kind[j] == CWC_RULE_PARENT_CHILD) {
+      // rule i depends on rule j when j writes a location i reads, or when j
+      // adds, removes or re-parents a compartment that can be a context of i
+      const int kj = d->kind[j], lj = d->ctx_label[j], cj = d->child_label[j];
+      {
         for (int i = 0; i < M; ++i) {
+          const int ki = d->kind[i], li = d->ctx_label[i], ci = d->child_label[i];
+          const bool local_i = ki == CWC_RULE_LOCAL || ki == CWC_RULE_CREATE;
           bool hit = false;
           for (long long w : writes[j])
             for (long long r : reads[i]) hit |= (w == r);
+          if (kj == CWC_RULE_CREATE)   // a new compartment of label cj under one of label lj
+            hit |= local_i ? li == cj : (ci == cj && li == lj);
+          if (kj == CWC_RULE_DISSOLVE) {
+            // any species of the parent content (label lj) may change
+            for (long long r : reads[i]) hit |= (r / S) == (long long)lj;   // key(0, lj, *)
+            // the dissolved compartment was a context; its children get a new parent
+            hit |= local_i ? li == cj : (ci == cj || li == cj || li == lj);
+          }
           if (!hit) continue;
           deps_all.push_back(i);
           ++cnt;
@@ -525,8 +536,8 @@ void cwc_model_destroy(cwc_model* m) {
 }
 
 int32_t cwc_checkpoint_words(const cwc_model* m) {
-  if (m == nullptr || !m->flat) return -1;
-  return m->S + CKPT_HEADER_WORDS;
+  if (m == nullptr) return -1;
+  return m->flat ? m->S + CKPT_HEADER_WORDS : CKPT_HEADER_WORDS + m->C * (3 + 2 * m->S);
 }
 
 int32_t cwc_model_num_observables(const cwc_model* m) {
@@ -697,6 +708,8 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_s
   prm.key1 = (uint32_t)(a->seed >> 32);
   prm.max_events = a->max_events;
   prm.deadline_ns = a->deadline_ns;
+  prm.ckpt = is_sens ? nullptr : a->checkpoint;
+  prm.resume = is_sens ? 0 : a->resume;
   if (!is_sens) {
     prm.states = a->states;
     prm.traj_status = a->traj_status;

@@ -141,6 +141,8 @@ struct CwcParams {
   double* partials;                // score replay: [Q][M]
   int32_t* slabs;                  // per launched thread, slab_words each
   long long slab_words;
+  int32_t* ckpt;                   // [Q][CKPT_HEADER_WORDS + C * (3 + 2S)] checkpoints (or null)
+  int resume;                      // 1: continue the TIMEOUT trajectories of ckpt
   WorkspaceHeader* ws;
   long long deadline_ns;
   int smem_table_bytes;

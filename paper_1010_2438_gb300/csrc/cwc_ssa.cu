@@ -18,10 +18,13 @@
 // The observable totals (content per label, wrap per label, alive compartments
 // per label) are kept up to date by every rewrite, so recording a grid point
 // is O stores.
-// After an event, the totals H_i of the rules that read a location (content
-// or wrap of a label, a species) the fired rule wrote are recomputed from
-// scratch over their contexts (all rules after CREATE / DISSOLVE), so H is
-// always exactly the sum the oracle re-matches every step.
+// After an event only the contexts of the rewritten compartments, of their
+// children (which read the parent content) and of the free slots (CREATE
+// fills one) can change their counts.  Each rule that reads a written
+// location, or whose contexts the event adds, removes or re-parents, drops
+// the old counts of those contexts from H_i before the rewrite and adds the
+// new ones after it, so H is always exactly the sum the oracle re-matches
+// every step.
 #include <cuda_runtime.h>
 
 #include "cwc_internal.h"
@@ -124,6 +127,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   const double* kp = nullptr;
   double t = 0.0;
   unsigned int n = 0;
+  unsigned int n_launch = 0;   // n when this launch took the trajectory up
   int gi = 0;
   long long gbits = 0;
   unsigned long long h = FNV_OFFSET;
@@ -163,10 +167,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     if (kind == 0 || kind == 2) return true;
     return LABEL(PARENT(c)) == rec[CR_CTX];
   };
-  // H_i from scratch: sum over contexts (ascending slots), overflow-checked
-  auto total_h = [&](int i) -> unsigned long long {
-    const int32_t* rec = s_rules + i * CWC_RULE_WORDS;
-    unsigned long long m = ctx_mask(rec);
+  // sum of the counts of a rule over the contexts in m (ascending slots),
+  // overflow-checked like a from-scratch H
+  auto partial_h = [&](const int32_t* rec, unsigned long long m) -> unsigned long long {
     unsigned long long tot = 0ull;
     while (m) {
       const int c = __ffsll((long long)m) - 1;
@@ -179,6 +182,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     return tot;
   };
+  // H_i from scratch: sum over all its contexts
+  auto total_h = [&](int i) -> unsigned long long {
+    const int32_t* rec = s_rules + i * CWC_RULE_WORDS;
+    return partial_h(rec, ctx_mask(rec));
+  };
   auto prop_of = [&](int i) -> double { return __dmul_rn(kp[i], u63_to_double_rn(HV(i))); };
   auto leaf_sum = [&](int l) -> double {
     const int j0 = l * B, j1 = min(j0 + B, M);
@@ -186,13 +194,14 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, prop_of(jj));
     return s;
   };
+  auto node_val = [&](int nd) -> double {
+    const double a = nd < 16 ? LEAF(2 * nd) : NODE(2 * nd - 32);
+    const double b = nd < 16 ? LEAF(2 * nd + 1) : NODE(2 * nd - 31);
+    return __dadd_rn(a, b);
+  };
   auto rebuild_tree = [&]() {
     for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
-    for (int nd = 0; nd < TREE_NODES; ++nd) {
-      const double a = nd < 16 ? LEAF(2 * nd) : NODE(2 * nd - 32);
-      const double b = nd < 16 ? LEAF(2 * nd + 1) : NODE(2 * nd - 31);
-      NODE(nd) = __dadd_rn(a, b);
-    }
+    for (int nd = 0; nd < TREE_NODES; ++nd) NODE(nd) = node_val(nd);
   };
 
   // observable index of the content / wrap total of (label, species) and of the alive count
@@ -232,7 +241,29 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     for (; gi < G; ++gi) record(gi);
   };
 
+  const int W = 3 + 2 * S;   // slot image row: alive, label, parent, wrap[S], content[S]
   auto finalize = [&]() {
+    if (prm.ckpt != nullptr) {
+      int32_t* rec = prm.ckpt + (size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W);
+      *reinterpret_cast<double*>(rec) = t;
+      *reinterpret_cast<unsigned long long*>(rec + 2) = h;
+      rec[4] = (int32_t)n;
+      rec[5] = gi;
+      rec[6] = status;
+      rec[7] = 0;
+      const unsigned long long alive = *alive_p;
+      for (int c = 0; c < C; ++c) {
+        int32_t* row = rec + CKPT_HEADER_WORDS + (size_t)c * W;
+        const bool a = (alive >> c) & 1ull;
+        row[0] = a ? 1 : 0;
+        row[1] = a ? LABEL(c) : 0;
+        row[2] = a ? PARENT(c) : -1;
+        for (int x = 0; x < S; ++x) {
+          row[3 + x] = wrap[(size_t)c * S + x];
+          row[3 + S + x] = content[(size_t)c * S + x];
+        }
+      }
+    }
     if (prm.traj_status) prm.traj_status[q] = status;
     if (prm.traj_events) prm.traj_events[q] = (long long)n;
     if (prm.traj_hash) prm.traj_hash[q] = h;
@@ -246,8 +277,10 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     tl[i] = tnow;
   };
 
-  // load and validate the initial term (slot image), build masks, H and tree
-  auto start = [&]() -> bool {
+  // load and validate the initial term (slot image; on resume the saved one),
+  // build masks, H and tree.  0 = running, 1 = ended at once (bad input),
+  // 2 = nothing to do (resuming, and this trajectory did not stop on the deadline)
+  auto start = [&]() -> int {
     p = (int)(q / prm.R);
     r = (int)(q - (long long)p * prm.R);
     kp = prm.rates + (size_t)p * M;
@@ -271,8 +304,18 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         Nf[i] = 0;
       }
     }
-    const int W = 3 + 2 * S;
     const int32_t* img = prm.init + (size_t)(prm.Pi == 1 ? 0 : p) * C * W;
+    if (prm.resume) {
+      const int32_t* rec = prm.ckpt + (size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W);
+      if (rec[6] != TS_TIMEOUT) return 2;
+      t = *reinterpret_cast<const double*>(rec);
+      h = *reinterpret_cast<const unsigned long long*>(rec + 2);
+      n = (unsigned)rec[4];
+      gi = rec[5];
+      if (gi < 0 || gi > G) bad = true;
+      gbits = gi < G && gi >= 0 ? dbits(prm.grid[gi]) : 0;
+      img = rec + CKPT_HEADER_WORDS;
+    }
     unsigned long long alive = 0ull;
     for (int l = 0; l < L; ++l) labmask[l] = 0ull;
     for (int c = 0; c < C; ++c) {
@@ -322,7 +365,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         int32_t* dst = prm.states + (size_t)q * G * O;
         for (long long e = 0; e < (long long)G * O; ++e) dst[e] = 0;
       }
-      return true;
+      *alive_p = 0ull;
+      return 1;
     }
     *alive_p = alive;
     for (int c = 0; c < C; ++c) {
@@ -341,7 +385,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     for (int i = 0; i < M; ++i) HV(i) = total_h(i);
     rebuild_tree();
-    return false;
+    return 0;
   };
 
   auto fits_add = [](int32_t v, int d) -> bool {
@@ -349,29 +393,28 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     return s >= 0 && s <= 0x7FFFFFFFll;
   };
 
-  // the rewrite of rule j at context c; returns a status (TS_OK on success)
-  auto apply = [&](const int32_t* rec, int c) -> int {
+  // whether the rewrite of rule j at context c fits (TS_OK), else its status;
+  // nothing is changed
+  auto apply_check = [&](const int32_t* rec, int c) -> int {
     const int kind = rec[CR_KIND];
     const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
-    if (kind == 0) {
-      int32_t* x = content + (size_t)c * S;
+    if (kind == 0 || kind == 2) {
+      if (kind == 2) {
+        const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
+        if (freeslots == 0ull) return TS_CAPACITY;
+      }
+      const int32_t* x = content + (size_t)c * S;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
-      const int l = LABEL(c);
-      for (int d = 0; d < nd0; ++d) {
-        const int v = rec[CR_D0 + d];
-        x[v & 0xffff] += v >> 16;
-        tot[OC(l, v & 0xffff)] += v >> 16;
-      }
       return TS_OK;
     }
+    const int qq = PARENT(c);
+    const int32_t* xp = content + (size_t)qq * S;
+    const int32_t* w = wrap + (size_t)c * S;
+    const int32_t* xc = content + (size_t)c * S;
     if (kind == 1) {
-      const int qq = PARENT(c);
-      int32_t* xp = content + (size_t)qq * S;
-      int32_t* w = wrap + (size_t)c * S;
-      int32_t* xc = content + (size_t)c * S;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
@@ -384,6 +427,45 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int v = rec[CR_D2 + d];
         if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
+      return TS_OK;
+    }
+    // DISSOLVE: the parent content gains (rhs0 - lhs0) + (wrap - lhs1) + (content - lhs2)
+    for (int s = 0; s < S; ++s) {
+      long long dv = (long long)w[s] + xc[s];
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        if ((v & 0xffff) == s) dv += v >> 16;
+      }
+      const int nr = rec[CR_NREAC];
+      for (int a = 0; a < nr; ++a) {
+        const int v = rec[CR_REAC + a];
+        if (((v >> 24) & 3) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
+      }
+      const long long nv = (long long)xp[s] + dv;
+      if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
+    }
+    return TS_OK;
+  };
+
+  // the rewrite of rule j at context c, after apply_check accepted it
+  auto apply = [&](const int32_t* rec, int c) {
+    const int kind = rec[CR_KIND];
+    const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
+    if (kind == 0) {
+      int32_t* x = content + (size_t)c * S;
+      const int l = LABEL(c);
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        x[v & 0xffff] += v >> 16;
+        tot[OC(l, v & 0xffff)] += v >> 16;
+      }
+      return;
+    }
+    if (kind == 1) {
+      const int qq = PARENT(c);
+      int32_t* xp = content + (size_t)qq * S;
+      int32_t* w = wrap + (size_t)c * S;
+      int32_t* xc = content + (size_t)c * S;
       const int lq = LABEL(qq), lc = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
@@ -400,18 +482,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         xc[v & 0xffff] += v >> 16;
         tot[OC(lc, v & 0xffff)] += v >> 16;
       }
-      return TS_OK;
+      return;
     }
     if (kind == 2) {
       const unsigned long long alive = *alive_p;
       const unsigned long long freeslots = ~alive & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
-      if (freeslots == 0ull) return TS_CAPACITY;
       const int e = __ffsll((long long)freeslots) - 1;
       int32_t* x = content + (size_t)c * S;
-      for (int d = 0; d < nd0; ++d) {
-        const int v = rec[CR_D0 + d];
-        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
-      }
       const int lctx = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
@@ -447,7 +524,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       chmask[c] |= 1ull << e;
       labmask[lab] |= 1ull << e;
       *alive_p = alive | (1ull << e);
-      return TS_OK;
+      return;
     }
     // DISSOLVE: matched atoms rewritten, the rest of the wrap and content go
     // to the parent, children are reparented, the slot is freed
@@ -471,10 +548,6 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         }
         return dv;
       };
-      for (int s = 0; s < S; ++s) {
-        const long long nv = (long long)xp[s] + delta_at(s);
-        if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
-      }
       const int lq = LABEL(qq), ld = LABEL(c);
       for (int s = 0; s < S; ++s) {
         const long long dv = delta_at(s);
@@ -499,7 +572,6 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         w[s] = 0;
         xc[s] = 0;
       }
-      return TS_OK;
     }
   };
 
@@ -530,9 +602,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       fill();
       return true;
     }
-    if ((n & 1023u) == 0u && deadline != ~0ull && globaltimer_ns() > deadline) {
+    // the deadline is read every 1024 events, never before a trajectory has
+    // applied 1024 events in this launch, so every launch makes progress
+    if ((n & 1023u) == 0u && n != n_launch && deadline != ~0ull && globaltimer_ns() > deadline) {
       status = TS_TIMEOUT;
-      fill();
+      if (prm.ckpt == nullptr) fill();   // with a checkpoint the rest is recorded on resume
       return true;
     }
     const uint32_t rr = (uint32_t)r + prm.r_offset;
@@ -620,49 +694,61 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       if (ctx < 0) ctx = lastc;
       if (ctx < 0) ctx = 0;  // unreachable: H_j > 0 has a context with h > 0
     }
-    // 3. update
-    const int ast = apply(rec, ctx);
+    // 3. update.  Only contexts in `touched` can change their counts: the
+    // rewritten compartments, their children (which read the parent content),
+    // and the free slots (one of which CREATE fills).  Each dependent rule
+    // drops the old counts of its touched contexts and adds the new ones; a
+    // rule whose contexts all lie in `touched` is summed afresh.
+    const int ast = apply_check(rec, ctx);
     if (ast != TS_OK) {
       status = ast;
       fill();
       return true;
     }
-    const bool structural = rec[CR_KIND] >= 2;
-    if (kSens) Nf[j] += 1;
-    if (structural) {
-      for (int i = 0; i < M; ++i) {
-        if (kSens) integrate(i, tn);
-        HV(i) = total_h(i);
-      }
-      rebuild_tree();
+    const int kind_j = rec[CR_KIND];
+    unsigned long long touched = chmask[ctx];
+    if (kind_j == 0 || kind_j == 2) {
+      touched |= 1ull << ctx;
+      if (kind_j == 2) touched |= ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
     } else {
-      const int doff = rec[CR_DEPOFF], dcnt = rec[CR_DEPCNT];
+      const int qq = PARENT(ctx);
+      touched |= (1ull << qq) | chmask[qq];
+    }
+    if (kSens) Nf[j] += 1;
+    const int doff = rec[CR_DEPOFF], dcnt = rec[CR_DEPCNT];
+    for (int e = 0; e < dcnt; ++e) {
+      const int i = s_deps[doff + e];
+      const int32_t* ri = s_rules + i * CWC_RULE_WORDS;
+      if (kSens) integrate(i, tn);
+      const unsigned long long cm = ctx_mask(ri);
+      HV(i) = (cm & ~touched) == 0ull ? 0ull : HV(i) - partial_h(ri, cm & touched);
+    }
+    apply(rec, ctx);
+    for (int e = 0; e < dcnt; ++e) {
+      const int i = s_deps[doff + e];
+      const int32_t* ri = s_rules + i * CWC_RULE_WORDS;
+      const unsigned long long s2 = HV(i) + partial_h(ri, ctx_mask(ri) & touched);
+      if ((s2 >> 63) != 0ull) ovf = true;
+      HV(i) = s2;
+    }
+    if (B == 1) {
       for (int e = 0; e < dcnt; ++e) {
         const int i = s_deps[doff + e];
-        if (kSens) integrate(i, tn);
-        HV(i) = total_h(i);
+        LEAF(i) = prop_of(i);
       }
-      if (B == 1) {
-        for (int e = 0; e < dcnt; ++e) {
-          const int i = s_deps[doff + e];
-          LEAF(i) = prop_of(i);
-        }
-      } else {
-        unsigned lm = (unsigned)rec[CR_LEAFMASK];
-        while (lm) {
-          const int ll = __ffs(lm) - 1;
-          lm &= lm - 1u;
-          LEAF(ll) = leaf_sum(ll);
-        }
+    } else {
+      unsigned lm = (unsigned)rec[CR_LEAFMASK];
+      while (lm) {
+        const int ll = __ffs(lm) - 1;
+        lm &= lm - 1u;
+        LEAF(ll) = leaf_sum(ll);
       }
-      unsigned nm = (unsigned)rec[CR_NODEMASK];
-      while (nm) {
-        const int k = __ffs(nm) - 1;
-        nm &= nm - 1u;
-        const double a = k < 16 ? LEAF(2 * k) : NODE(2 * k - 32);
-        const double b = k < 16 ? LEAF(2 * k + 1) : NODE(2 * k - 31);
-        NODE(k) = __dadd_rn(a, b);
-      }
+    }
+    unsigned nm = (unsigned)rec[CR_NODEMASK];
+    while (nm) {
+      const int k = __ffs(nm) - 1;
+      nm &= nm - 1u;
+      NODE(k) = node_val(k);
     }
     if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
       const size_t at = (size_t)q * prm.log_cap + n;
@@ -686,10 +772,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         first = false;
       }
       if (q >= Q) break;
-      if (start()) {
+      const int st0 = start();
+      if (st0 == 2) continue;
+      if (st0 == 1) {
         finalize();
         continue;
       }
+      n_launch = n;
       need_new = false;
     }
     if (step()) {

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   const double* kp = nullptr;
   double t = 0.0;
   unsigned int n = 0;
+  unsigned int n_launch = 0;   // n when this launch took the trajectory up
   int gi = 0;
   long long gbits = 0;
   unsigned long long h = FNV_OFFSET;
@@ -316,7 +317,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       fill();
       return true;
     }
-    if ((n & 1023u) == 0u && deadline != ~0ull && globaltimer_ns() > deadline) {
+    // the deadline is read every 1024 events, never before a trajectory has
+    // applied 1024 events in this launch, so every launch makes progress
+    if ((n & 1023u) == 0u && n != n_launch && deadline != ~0ull && globaltimer_ns() > deadline) {
       status = TS_TIMEOUT;
       if (prm.ckpt == nullptr) fill();   // with a checkpoint the rest is recorded on resume
       return true;
@@ -461,6 +464,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       const int st0 = start();
       if (st0 == 1) finalize();
       if (st0 != 0) continue;
+      n_launch = n;
       need_new = false;
     }
     if (step()) {

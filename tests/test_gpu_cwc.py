@@ -186,3 +186,40 @@ def test_cwc_autograd_function():
     (m * 0.001).sum().backward()
     og, _ = oracle.sensitivity(b, om, np.full(om.shape, 0.001), threads=8)
     assert np.allclose(k.grad.cpu().numpy(), og, rtol=1e-9, atol=1e-9 * np.abs(og).max())
+
+
+def test_cwc_checkpoint_resume_reproduces_the_uninterrupted_run():
+    """Compartment terms stopped on a short deadline and resumed from their
+    saved slot images, until none is left, end bit-identical to an
+    uninterrupted run (Sec. 5.2: instances stopped and restarted); the saved
+    image of a finished trajectory is its final term."""
+    b0 = W.cwc3x24(R=512, G=50)
+    b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 1.5, b0.R, b0.seed)
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    ref = api.simulate(cm, rates, init, grid, b.R, b.seed)
+    out = api.simulate(cm, rates, init, grid, b.R, b.seed, checkpoint=True, deadline_ns=2_000_000,
+                       layout=capi.CWC_LAYOUT_QUEUE)
+    torch.cuda.synchronize()
+    assert int((out["status"] == capi.CWC_TRAJ_TIMEOUT).sum()) > 0
+    rounds = 0
+    while bool((out["status"] == capi.CWC_TRAJ_TIMEOUT).any()):
+        out = api.simulate(cm, rates, init, grid, b.R, b.seed, resume=True, deadline_ns=2_000_000,
+                           layout=capi.CWC_LAYOUT_QUEUE, out=out)
+        torch.cuda.synchronize()
+        rounds += 1
+        assert rounds < 2000
+    assert rounds > 0
+    for k in ("states", "events", "hash", "status", "final_t"):
+        assert torch.equal(out[k], ref[k]), k
+    # the saved terms give the last grid point's observables
+    S, C, L = b.model.n_species, b.model.max_compartments, b.model.n_labels
+    img = out["checkpoint"].cpu().numpy().reshape(b.R, 8 + C * (3 + 2 * S))[:, 8:].reshape(b.R, C, 3 + 2 * S)
+    alive = img[:, :, 0] == 1
+    lab = img[:, :, 1]
+    last = ref["states"].cpu().numpy()[0, :, -1, :] if ref["states"].dim() == 4 else ref["states"].cpu().numpy()[:, -1, :]
+    for l in range(L):
+        m = alive & (lab == l)
+        content = (img[:, :, 3 + S:] * m[:, :, None]).sum(axis=1)
+        assert np.array_equal(np.minimum(content, 2**31 - 1), last[:, l * S:(l + 1) * S])
+        assert np.array_equal(m.sum(axis=1), last[:, L * S + (L - 1) * S + l])
