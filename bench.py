@@ -178,7 +178,7 @@ def measure_extras(dev):
     b = W.cwc3x24()
     cm = api.CompiledModel(b.model)
     rates, init, grid = api.device_inputs(b, dev)
-    lay, thr, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=500)
+    lay, thr, lanes, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=500)
     keep = {}
 
     def run_cwc():
@@ -188,6 +188,7 @@ def measure_extras(dev):
     out, sec = _timed(run_cwc)
     ev = int(out["events"].sum().item())
     extras["cwc3x24"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay, "block_threads": thr,
+                         "lanes_per_trajectory": lanes,
                          "workload": "3 labels below the top, 24 species, 48 rules (transport, wrap binding, create, "
                                      "dissolve), <=64 compartments, 16384 replicas, 500-point grid"}
     del out, keep
@@ -195,7 +196,7 @@ def measure_extras(dev):
     b = W.sweep256x256()
     cm = api.CompiledModel(b.model)
     rates, init, grid = api.device_inputs(b, dev)
-    lay, thr, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=2000)
+    lay, thr, _, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=2000)
     g = api.GraphedSimulation(cm, rates, init, grid, b.R, b.seed, states=True)
     out, sec = _timed(g.replay)
     evp = out["events"].double().mean(dim=1)
@@ -283,6 +284,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads of the path")
     ap.add_argument("--layout", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory (compartment workload; 0 = automatic)")
     ap.add_argument("--replicas", type=int, default=0, help="smaller case for profiling (default: 65536)")
     ap.add_argument("--horizon-scale", type=float, default=1.0, help="scale the time grid (profiling only)")
     ap.add_argument("--grid-points", type=int, default=0, help="grid points (profiling only; default 1000)")
@@ -323,7 +325,8 @@ def main():
 
     def step(o):
         return api.simulate(cm, rates, init, grid, R, batch.seed, batch.max_events, states=True, traj=True,
-                            layout=args.layout, block_threads=args.threads, replica_offset=r_off, out=o)
+                            layout=args.layout, block_threads=args.threads, lanes=args.lanes, replica_offset=r_off,
+                            out=o)
 
     for _ in range(args.warmup):
         out = step(out)

@@ -182,6 +182,13 @@ enum {
  *                 bit, because the random streams are keyed by the event
  *                 index (the stop / restart of instances in Sec. 5.2).  Not
  *                 combinable with sums, means, sumsq, variance or ci90.
+ *   lanes         lanes of a warp per trajectory: 0 = automatic (the
+ *                 autotuner's choice for this batch shape, else 1 for flat
+ *                 models and 4 for compartment models), or 1, 4, 8
+ *                 (compartment models; flat models take 1).  A group of lanes
+ *                 computes one trajectory's scalar work identically and
+ *                 shares its context scans, totals updates and grid records;
+ *                 the results do not depend on this choice.
  *   layout, block_threads (0 = automatic), deadline_ns (0 = none: a
  *   trajectory still running when this many nanoseconds of device time have
  *   passed since the launch stops with CWC_TRAJ_TIMEOUT.  The clock is read
@@ -229,6 +236,7 @@ typedef struct {
   int32_t resume;
   int32_t layout;
   int32_t block_threads;
+  int32_t lanes;
   int64_t deadline_ns;
   void* workspace;
   size_t workspace_bytes;
@@ -307,21 +315,24 @@ cwc_status cwc_sensitivity(const cwc_model* model, const cwc_sim_args* sim, cons
                            void* stream);
 
 /*
- * Pick the launch layout (CWC_LAYOUT_STATIC or CWC_LAYOUT_QUEUE) and the
- * threads per block for these arguments by timing every candidate on this
- * batch with at most `tune_events` events per trajectory (0 = 2048) and no
- * outputs; all candidates do identical work because the random streams are
- * keyed by (event, replica, point), not by thread.  One thread always runs one
- * trajectory: on GB300 an FP64 instruction costs a full warp slot whatever the
- * number of active lanes, so sharing a trajectory among lanes only multiplies
- * the cost of its scalar FP64 work.  The winner is returned and cached for
- * this model and batch shape; later calls with layout CWC_LAYOUT_AUTO and
- * block_threads 0 use it.  Synchronises `stream`.  Uses args->workspace (a
- * candidate that needs more than workspace_bytes is skipped).
+ * Pick the launch layout (CWC_LAYOUT_STATIC or CWC_LAYOUT_QUEUE), the
+ * threads per block and the lanes per trajectory (1, 4, 8 for compartment
+ * models; 1 for flat ones) for these arguments by timing every candidate on
+ * this batch with at most `tune_events` events per trajectory (0 = 2048) and
+ * no outputs; all candidates do identical work because the random streams are
+ * keyed by (event, replica, point), not by thread.  On GB300 an FP64
+ * instruction costs a full warp slot whatever the number of active lanes, so
+ * several lanes per trajectory pay off only where the per-trajectory work
+ * beyond the FP64 step (context scans, totals over compartments) dominates
+ * or the batch is too small to fill the GPU one lane per trajectory.  The
+ * winner is returned (best_lanes may be NULL) and cached for this model and
+ * batch shape; later calls with layout CWC_LAYOUT_AUTO, block_threads 0 and
+ * lanes 0 use it.  Synchronises `stream`.  Uses args->workspace (a candidate
+ * that needs more than workspace_bytes is skipped).
  * Errors: as cwc_simulate; CWC_ERR_INTERNAL if no candidate could run.
  */
 cwc_status cwc_autotune(const cwc_model* model, const cwc_sim_args* args, int64_t tune_events, void* stream,
-                        int32_t* best_layout, int32_t* best_block_threads, double* best_ms);
+                        int32_t* best_layout, int32_t* best_block_threads, double* best_ms, int32_t* best_lanes);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* cwc_last_error(void);

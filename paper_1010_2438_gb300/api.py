@@ -28,6 +28,7 @@ class CompiledModel:
                                    m.lhs.ctypes.data, m.rhs.ctypes.data)
         self.handle = capi.cwc_model_create(desc)
         self.n_observables = capi.cwc_model_num_observables(self.handle)
+        self.flat = m.n_labels == 1 and m.max_compartments == 1
 
     def close(self) -> None:
         if getattr(self, "handle", None):
@@ -58,7 +59,7 @@ def device_inputs(batch: Batch, device="cuda"):
 
 
 def _sim_args(cm: CompiledModel, rates, init, grid, R, seed, max_events, layout, block_threads, deadline_ns,
-              replica_offset=0):
+              replica_offset=0, lanes=0):
     P = rates.shape[0]
     a = capi.cwc_sim_args()
     a.P, a.R, a.G, a.Pi = P, R, grid.shape[0], init.shape[0]
@@ -67,6 +68,7 @@ def _sim_args(cm: CompiledModel, rates, init, grid, R, seed, max_events, layout,
     a.seed = seed & 0xFFFFFFFFFFFFFFFF
     a.max_events = max_events
     a.layout, a.block_threads, a.deadline_ns = layout, block_threads, deadline_ns
+    a.lanes = lanes
     return a
 
 
@@ -95,7 +97,8 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
              max_events: int = (1 << 32) - 1, *, states: bool = True, sums: bool = False, means: bool = False,
              sumsq: bool = False, variance: bool = False, ci90: bool = False,
              traj: bool = True, log_cap: int = 0, layout: int = capi.CWC_LAYOUT_AUTO, block_threads: int = 0,
-             deadline_ns: int = 0, replica_offset: int = 0, checkpoint: bool = False, resume: bool = False,
+             lanes: int = 0, deadline_ns: int = 0, replica_offset: int = 0, checkpoint: bool = False,
+             resume: bool = False,
              stream: Optional[torch.cuda.Stream] = None,
              out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
     """Run P x R trajectories (cwc_simulate) and return the requested outputs.
@@ -115,7 +118,7 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
             res[name] = t
         return t
 
-    a = _sim_args(cm, rates, init, grid, R, seed, max_events, layout, block_threads, deadline_ns, replica_offset)
+    a = _sim_args(cm, rates, init, grid, R, seed, max_events, layout, block_threads, deadline_ns, replica_offset, lanes)
     if states:
         a.states = _p(get("states", (P, R, G, O), torch.int32))
     if sums:
@@ -187,7 +190,7 @@ def simulate_sliced(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, 
 
 def sensitivity(cm: CompiledModel, rates, init, grid, R: int, seed: int, means: torch.Tensor,
                 grad_means: torch.Tensor, max_events: int = (1 << 32) - 1, *, partials: bool = False,
-                layout: int = capi.CWC_LAYOUT_AUTO, block_threads: int = 0,
+                layout: int = capi.CWC_LAYOUT_AUTO, block_threads: int = 0, lanes: int = 0,
                 stream: Optional[torch.cuda.Stream] = None) -> Dict[str, torch.Tensor]:
     """d L / d k by likelihood-ratio replay (cwc_sensitivity); returns grad_rates [P, M]."""
     _check_inputs(cm, rates, init, grid)
@@ -195,7 +198,7 @@ def sensitivity(cm: CompiledModel, rates, init, grid, R: int, seed: int, means: 
     P, M = rates.shape
     means = means.contiguous()
     grad_means = grad_means.contiguous().to(torch.float64)
-    a = _sim_args(cm, rates, init, grid, R, seed, max_events, layout, block_threads, 0)
+    a = _sim_args(cm, rates, init, grid, R, seed, max_events, layout, block_threads, 0, 0, lanes)
     s = capi.cwc_sens_args()
     grad = torch.empty((P, M), dtype=torch.float64, device=dev)
     s.means, s.grad_means, s.grad_rates = _p(means), _p(grad_means), _p(grad)
@@ -264,17 +267,18 @@ def simulate_host(cm: CompiledModel, rates_h: torch.Tensor, init_h: torch.Tensor
 
 def autotune(cm: CompiledModel, rates, init, grid, R: int, seed: int, max_events: int = (1 << 32) - 1,
              tune_events: int = 0, stream: Optional[torch.cuda.Stream] = None):
-    """cwc_autotune on this batch: returns (layout, block_threads, ms) and
-    caches the choice for later CWC_LAYOUT_AUTO calls on the same shape."""
+    """cwc_autotune on this batch: returns (layout, block_threads, lanes, ms)
+    and caches the choice for later automatic calls on the same shape."""
     _check_inputs(cm, rates, init, grid)
     nbytes = 0
-    for lay in (capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE):
-        for T in range(32, 257, 32):
-            a = _sim_args(cm, rates, init, grid, R, seed, max_events, lay, T, 0)
-            try:
-                nbytes = max(nbytes, capi.cwc_simulate_workspace_size(cm.handle, a))
-            except capi.CwcError:
-                pass
+    for lanes in ((1,) if cm.flat else (1, 4, 8)):
+        for lay in (capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE):
+            for T in range(32, 257, 32):
+                a = _sim_args(cm, rates, init, grid, R, seed, max_events, lay, T, 0, 0, lanes)
+                try:
+                    nbytes = max(nbytes, capi.cwc_simulate_workspace_size(cm.handle, a))
+                except capi.CwcError:
+                    pass
     ws = _workspace(nbytes, rates.device)
     a = _sim_args(cm, rates, init, grid, R, seed, max_events, capi.CWC_LAYOUT_AUTO, 0, 0)
     a.workspace = _aligned(ws) if nbytes else None

@@ -46,7 +46,7 @@ class cwc_sim_args(ctypes.Structure):
                 ("traj_status", _vp), ("traj_events", _vp), ("traj_hash", _vp), ("traj_final_t", _vp),
                 ("log_cap", _i32), ("log_rule", _vp), ("log_slot", _vp), ("log_t", _vp),
                 ("checkpoint", _vp), ("resume", _i32),
-                ("layout", _i32), ("block_threads", _i32), ("deadline_ns", _i64),
+                ("layout", _i32), ("block_threads", _i32), ("lanes", _i32), ("deadline_ns", _i64),
                 ("workspace", _vp), ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -93,7 +93,7 @@ def lib() -> ctypes.CDLL:
         L.cwc_sensitivity.argtypes = [_vp, ctypes.POINTER(cwc_sim_args), ctypes.POINTER(cwc_sens_args), _vp]
         L.cwc_sensitivity.restype = ctypes.c_int
         L.cwc_autotune.argtypes = [_vp, ctypes.POINTER(cwc_sim_args), _i64, _vp, ctypes.POINTER(_i32),
-                                   ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]
+                                   ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32)]
         L.cwc_autotune.restype = ctypes.c_int
         L.cwc_checkpoint_words.argtypes = [_vp]
         L.cwc_checkpoint_words.restype = _i32
@@ -155,11 +155,11 @@ def cwc_simulate_noalloc(handle: int, args: cwc_sim_args, stream: int = 0) -> No
 
 
 def cwc_autotune(handle: int, args: cwc_sim_args, tune_events: int = 0, stream: int = 0):
-    """Time the launch candidates on this batch; returns (layout, block_threads, ms) and caches them."""
-    lay, thr, ms = _i32(), _i32(), ctypes.c_double()
+    """Time the launch candidates on this batch; returns (layout, block_threads, lanes, ms) and caches them."""
+    lay, thr, ms, lanes = _i32(), _i32(), ctypes.c_double(), _i32()
     _check(lib().cwc_autotune(handle, ctypes.byref(args), tune_events, stream, ctypes.byref(lay), ctypes.byref(thr),
-                              ctypes.byref(ms)))
-    return lay.value, thr.value, ms.value
+                              ctypes.byref(ms), ctypes.byref(lanes)))
+    return lay.value, thr.value, lanes.value, ms.value
 
 
 def cwc_sensitivity_workspace_size(handle: int, args: cwc_sim_args, sens: cwc_sens_args) -> int:

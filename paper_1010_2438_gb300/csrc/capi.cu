@@ -27,9 +27,12 @@ cudaError_t launch_means(const unsigned long long* sums, double* means, long lon
 cudaError_t launch_stats(const unsigned long long* sums, const unsigned long long* sumsq, double* variance,
                          double* ci90, long long n, int R, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, double* grad, int P, int R, int M, cudaStream_t st);
-cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, cudaStream_t stream);
-cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int T, int* blocks);
-int cwc_best_threads(const CwcParams& prm, bool queue);
+cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int lanes, int T, int blocks,
+                       cudaStream_t stream);
+cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int lanes, int T, int* blocks);
+int cwc_best_threads(const CwcParams& prm, bool queue, int lanes);
+bool cwc_lanes_supported(int lanes);
+int cwc_thread_bytes_host(int M);
 int cwc_table_bytes_host(int M, int n_deps);
 long long cwc_slab_words_host(int S, int L, int C, int M, bool sens);
 }  // namespace cwcgpu
@@ -82,7 +85,7 @@ struct WsLayout {
   bool need_sumsq = false;
   bool need_order = false;        // flat queue layout over several sweep points
   bool need_header = false, need_sums = false, need_partials = false;
-  int T = 0, blocks = 0;          // compartmentalised launch shape (its slabs are per thread)
+  int T = 0, blocks = 0, lanes = 1;   // compartmentalised launch shape (its slabs are per lane group)
   long long slab_words = 0;
 };
 
@@ -103,17 +106,29 @@ CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a, bool sens)
   return prm;
 }
 
-// Autotuner cache: (model, P, R, G, Pi) -> (layout, threads per block).
+// Autotuner cache: (model, P, R, G, Pi) -> (layout, threads per block, lanes per trajectory).
 std::mutex g_tune_mutex;
-std::map<std::tuple<const void*, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<const void*, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
 
-bool tuned_choice(const cwc_model* m, const cwc_sim_args* a, int* layout, int* threads) {
+bool tuned_choice(const cwc_model* m, const cwc_sim_args* a, int* layout, int* threads, int* lanes) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   auto it = g_tune_cache.find(std::make_tuple((const void*)m, a->P, a->R, a->G, a->Pi));
   if (it == g_tune_cache.end()) return false;
-  *layout = it->second.first;
-  *threads = it->second.second;
+  *layout = std::get<0>(it->second);
+  *threads = std::get<1>(it->second);
+  *lanes = std::get<2>(it->second);
   return true;
+}
+
+// Lanes per trajectory when the caller leaves it to the library (and the
+// autotuner has not chosen): one for flat networks, so that every FP64
+// instruction of the step serves 32 trajectories; four for compartment
+// terms, whose context scans and totals updates over compartments outweigh
+// their FP64 step (1.9e8 against 1.5e8 events/s with one lane on a
+// 16,384-term batch with 48 rules).
+int chosen_lanes(const cwc_model* m, const cwc_sim_args* a) {
+  if (m->flat) return 1;
+  return a->lanes > 0 ? a->lanes : 4;
 }
 
 int chosen_layout(const cwc_sim_args* a) { return a->layout == CWC_LAYOUT_AUTO ? CWC_LAYOUT_QUEUE : a->layout; }
@@ -121,10 +136,11 @@ int chosen_layout(const cwc_sim_args* a) { return a->layout == CWC_LAYOUT_AUTO ?
 // Resolve CWC_LAYOUT_AUTO / block_threads 0 through the autotuner cache.
 cwc_sim_args resolve_auto(const cwc_model* m, const cwc_sim_args* a) {
   cwc_sim_args b = *a;
-  int lay = 0, thr = 0;
-  if (a->layout == CWC_LAYOUT_AUTO && a->block_threads == 0 && tuned_choice(m, a, &lay, &thr)) {
+  int lay = 0, thr = 0, lanes = 0;
+  if (a->layout == CWC_LAYOUT_AUTO && a->block_threads == 0 && a->lanes == 0 && tuned_choice(m, a, &lay, &thr, &lanes)) {
     b.layout = lay;
     b.block_threads = thr;
+    b.lanes = lanes;
   }
   return b;
 }
@@ -173,11 +189,13 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
   if (!m->flat) {
     const CwcParams prm = cwc_shape_params(m, a, sens);
     const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
-    w.T = a->block_threads > 0 ? a->block_threads : cover_sms(cwc_best_threads(prm, queue), prm.Q);
-    if (cwc_launch_shape(prm, queue, w.T, &w.blocks) != cudaSuccess) w.blocks = 0;
+    w.lanes = chosen_lanes(m, a);
+    w.T = a->block_threads > 0 ? a->block_threads
+                               : cover_sms(cwc_best_threads(prm, queue, w.lanes), prm.Q * (long long)w.lanes);
+    if (cwc_launch_shape(prm, queue, w.lanes, w.T, &w.blocks) != cudaSuccess) w.blocks = 0;
     w.slab_words = prm.slab_words;
     w.slabs = off;
-    off = align256(off + (size_t)w.blocks * w.T * (size_t)prm.slab_words * sizeof(int32_t));
+    off = align256(off + (size_t)w.blocks * (size_t)(w.T / w.lanes) * (size_t)prm.slab_words * sizeof(int32_t));
   }
   w.total = off;
   return w;
@@ -198,6 +216,9 @@ cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
   if (a->layout < CWC_LAYOUT_AUTO || a->layout > CWC_LAYOUT_QUEUE) return fail(CWC_ERR_INVALID_ARG, "bad layout");
   if (a->block_threads != 0 && (a->block_threads < 32 || a->block_threads > 256 || a->block_threads % 32 != 0))
     return fail(CWC_ERR_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 256]");
+  if (a->lanes != 0 && !(m->flat ? a->lanes == 1 : cwc_lanes_supported(a->lanes)))
+    return fail(CWC_ERR_INVALID_ARG, m->flat ? "lanes must be 0 or 1 for flat models"
+                                             : "lanes must be 0, 1, 4 or 8 for compartment models");
   if (a->deadline_ns < 0) return fail(CWC_ERR_INVALID_ARG, "deadline_ns must be >= 0");
   if (a->resume != 0 && a->resume != 1) return fail(CWC_ERR_INVALID_ARG, "resume must be 0 or 1");
   if (a->resume && a->checkpoint == nullptr) return fail(CWC_ERR_INVALID_ARG, "resume needs the checkpoint buffer");
@@ -748,7 +769,7 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_s
   }
   const LogConstants lc = make_log_constants();
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
-  e = launch_cwc(prm, lc, queue, w.T, w.blocks, st);
+  e = launch_cwc(prm, lc, queue, w.lanes, w.T, w.blocks, st);
   if (e != cudaSuccess) return cuda_fail(e, "CWC SSA kernel launch");
   if (is_sens) {
     e = launch_reduce_partials(prm.partials, sens->grad_rates, a->P, a->R, m->M, st);
@@ -776,7 +797,7 @@ cwc_status cwc_simulate(const cwc_model* m, const cwc_sim_args* a, void* stream)
 }
 
 cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_events, void* stream,
-                        int32_t* best_layout, int32_t* best_threads, double* best_ms) {
+                        int32_t* best_layout, int32_t* best_threads, double* best_ms, int32_t* best_lanes) {
   g_last_error.clear();
   cwc_status st = check_sim_args(m, a);
   if (st != CWC_OK) return st;
@@ -806,15 +827,18 @@ cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_
   const int64_t cap = tune_events == 0 ? 2048 : tune_events;
   c.max_events = std::min<int64_t>(a->max_events, cap);
   float best = -1.0f;
-  int bl = 0, bt = 0;
+  int bl = 0, bt = 0, bn = 1;
+  for (int lanes : {1, 4, 8})
   for (int lay : {CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE}) {
+    if (m->flat && lanes != 1) continue;
     for (int T = 32; T <= 256; T += 32) {
       c.layout = lay;
       c.block_threads = T;
+      c.lanes = lanes;
       if (m->flat) {
         FlatParams prm = make_flat_params(m, &c);
         if (flat_smem_bytes(prm, T, false) > 227 * 1024) continue;
-      } else if ((size_t)cwc_table_bytes_host(m->M, m->c_n_deps) + (size_t)T * (32 + TREE_NODES + m->M) * 8 >
+      } else if ((size_t)cwc_table_bytes_host(m->M, m->c_n_deps) + (size_t)(T / lanes) * cwc_thread_bytes_host(m->M) >
                  227 * 1024) {
         continue;
       }
@@ -844,6 +868,7 @@ cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_
         best = ms_best;
         bl = lay;
         bt = T;
+        bn = lanes;
       }
     }
   }
@@ -852,10 +877,11 @@ cwc_status cwc_autotune(const cwc_model* m, const cwc_sim_args* a, int64_t tune_
   if (best < 0.0f) return fail(CWC_ERR_INTERNAL, "no autotune candidate could run (workspace too small?)");
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[std::make_tuple((const void*)m, a->P, a->R, a->G, a->Pi)] = std::make_pair(bl, bt);
+    g_tune_cache[std::make_tuple((const void*)m, a->P, a->R, a->G, a->Pi)] = std::make_tuple(bl, bt, bn);
   }
   if (best_layout) *best_layout = bl;
   if (best_threads) *best_threads = bt;
+  if (best_lanes) *best_lanes = bn;
   if (best_ms) *best_ms = best;
   g_last_error.clear();
   return CWC_OK;

@@ -5,13 +5,24 @@
 // rewrite, including transport between a compartment and its parent, binding
 // to the wrap, creation and dissolution of compartments.
 //
-// One thread per trajectory, so the FP64 part (logarithm, tau, tree) keeps
-// every lane busy.  Shared memory per thread, [index][thread]-strided: the 32
-// FP64 leaves and 31 internal nodes of the rule tree and the int64 totals H_j
+// A group of kL lanes (1, 4 or 8 of a warp) runs one trajectory.  Every lane
+// of the group keeps the trajectory's scalar state (time, event index, tree
+// walk) and computes it identically, so the group branches as one; the work
+// that grows with the term is split over the lanes: the context scan (rounds
+// of kL consecutive slots, a group prefix sum of their counts), the update of
+// the dependent rules' totals (one rule per lane), the leaf rebuild, the grid
+// records (observables over lanes) and the set-up of a term.  The rewrite
+// itself is done by lane 0 of the group.  The FP64 instructions (logarithm,
+// tau, tree) are then shared by 32 / kL terms per warp instead of 32, but a
+// batch of 16,384 terms keeps 4x more warps resident with 4 lanes per term,
+// which hides more of the slab loads' latency.
+//
+// Shared memory per trajectory, [index][trajectory]-strided: the 32 FP64
+// leaves and 31 internal nodes of the rule tree and the int64 totals H_j
 // (combinatorial counts summed over the rule's contexts; a_j = k_j * H_j).
 // The term itself (C <= 64 slots x S species, content and wrap) lives in a
-// per-thread slab of the caller's workspace, reused across the trajectories a
-// thread runs:
+// per-group slab of the caller's workspace, reused across the trajectories a
+// group runs:
 //   chmask[C]  u64  children of each slot        labmask[L] u64  alive slots per label
 //   alive      u64  alive slots                  tot[O]     i64  observable totals
 //   meta[C]    i32  label | (parent + 1) << 8   wrap[C][S], content[C][S]  i32
@@ -32,6 +43,56 @@
 
 namespace cwcgpu {
 
+// The kL lanes of a warp that run one trajectory.
+template <int kL>
+struct LaneGroup {
+  unsigned mask;   // the group's lanes within the warp
+  int gl;          // this lane's index in the group
+  int base;        // the group's first lane in the warp
+  __device__ LaneGroup() {
+    const int lane = threadIdx.x & 31;
+    gl = lane & (kL - 1);
+    base = lane & ~(kL - 1);
+    mask = kL == 32 ? 0xffffffffu : (((1u << kL) - 1u) << base);
+  }
+  __device__ __forceinline__ void sync() const {
+    if (kL > 1) __syncwarp(mask);
+  }
+  __device__ __forceinline__ bool any(bool v) const {
+    if (kL == 1) return v;
+    return (__ballot_sync(mask, v) & mask) != 0u;
+  }
+  // bit k set when lane k of the group has v
+  __device__ __forceinline__ unsigned ballot(bool v) const {
+    if (kL == 1) return v ? 1u : 0u;
+    return (__ballot_sync(mask, v) & mask) >> base;
+  }
+  template <class V>
+  __device__ __forceinline__ V bcast(V v, int src) const {
+    if (kL == 1) return v;
+    return __shfl_sync(mask, v, src, kL);
+  }
+  __device__ __forceinline__ unsigned long long incl_scan(unsigned long long x) const {
+#pragma unroll
+    for (int off = 1; off < kL; off <<= 1) {
+      const unsigned long long y = __shfl_up_sync(mask, x, off, kL);
+      if (gl >= off) x += y;
+    }
+    return x;
+  }
+  __device__ __forceinline__ unsigned long long or_all(unsigned long long x) const {
+#pragma unroll
+    for (int off = kL / 2; off > 0; off >>= 1) x |= __shfl_xor_sync(mask, x, off, kL);
+    return x;
+  }
+  // the same pairwise tree on every lane, so every lane holds the same sum
+  __device__ __forceinline__ double sum(double x) const {
+#pragma unroll
+    for (int off = kL / 2; off > 0; off >>= 1) x = __dadd_rn(x, __shfl_xor_sync(mask, x, off, kL));
+    return x;
+  }
+};
+
 __device__ __forceinline__ long long cwc_grab_next(WorkspaceHeader* ws) {
   const unsigned mask = __activemask();
   const int lane = threadIdx.x & 31;
@@ -47,6 +108,7 @@ __host__ __device__ inline int cwc_table_bytes(int M, int n_deps) {
   return ((words * 4 + 15) / 16) * 16 + 54 * 8;
 }
 
+// shared-memory bytes of one trajectory
 __host__ __device__ inline int cwc_thread_bytes(int M) { return (32 + TREE_NODES + M) * 8; }
 
 __host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, bool sens) {
@@ -55,11 +117,15 @@ __host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, 
   return (w + 31) / 32 * 32;
 }
 
-template <bool kQueue, bool kSens>
+template <int kL, bool kQueue, bool kSens>
 __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ CwcParams prm,
                                                       const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const LaneGroup<kL> grp;
+  const int gl = grp.gl;
   const int T = blockDim.x;
+  const int NT = T / kL;                 // trajectories per block
+  const int ts = threadIdx.x / kL;       // this group's trajectory column
   const int tid = threadIdx.x;
   const int S = prm.S, L = prm.L, C = prm.C, M = prm.M, B = prm.B, G = prm.G, O = prm.O;
 
@@ -68,13 +134,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   const int tbl_words = M * CWC_RULE_WORDS + prm.n_deps;
   double* s_eln2 = reinterpret_cast<double*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
   double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
-  double* leaf = dbase + tid;                                     // [32][T]
-  double* node = dbase + 32 * T + tid;                            // [31][T]
-  unsigned long long* Hs = reinterpret_cast<unsigned long long*>(dbase + (32 + TREE_NODES) * T) + tid;  // [M][T]
+  double* leaf = dbase + ts;                                      // [32][NT]
+  double* node = dbase + 32 * NT + ts;                            // [31][NT]
+  unsigned long long* Hs = reinterpret_cast<unsigned long long*>(dbase + (32 + TREE_NODES) * NT) + ts;  // [M][NT]
 
-#define LEAF(l) leaf[(l) * T]
-#define NODE(i) node[(i) * T]
-#define HV(i) Hs[(i) * T]
+#define LEAF(l) leaf[(l) * NT]
+#define NODE(i) node[(i) * NT]
+#define HV(i) Hs[(i) * NT]
 
   for (int i = tid; i < tbl_words; i += T) s_rules[i] = prm.rules[i];
   for (int i = tid; i < 54; i += T) s_eln2[i] = lc.e_ln2[i];
@@ -103,9 +169,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   const unsigned long long deadline = s_deadline;
   const long long T_bits = dbits(prm.grid[G - 1]);
 
-  // this thread's slab of the term
-  const long long gthread = (long long)blockIdx.x * T + tid;
-  int32_t* slab = prm.slabs + gthread * prm.slab_words;
+  // this group's slab of the term
+  const long long gslot = (long long)blockIdx.x * NT + ts;
+  int32_t* slab = prm.slabs + gslot * prm.slab_words;
   unsigned long long* chmask = reinterpret_cast<unsigned long long*>(slab);       // [C]
   unsigned long long* labmask = chmask + C;                                       // [L]
   unsigned long long* alive_p = labmask + L;                                      // [1]
@@ -134,28 +200,27 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   bool ovf = false;
   int status = TS_OK;
   const long long Q = prm.Q;
-  const long long qstride = (long long)gridDim.x * T;
   bool first = true;
 
-  // product of binomials of the reactants of `row` over the multiset x
-  auto pattern = [&](const int32_t* rec, int row, const int32_t* x, unsigned long long acc) -> unsigned long long {
+  // combinatorial count of rule i at context slot c (c is the context for
+  // LOCAL / CREATE, the child for PARENT_CHILD / DISSOLVE).  The reactants
+  // are stored by pattern row, then species, so one pass multiplies in the
+  // oracle's order: row 0 (the context's or the parent's content), row 1
+  // (the child's wrap), row 2 (the child's content).
+  auto count_at = [&](const int32_t* rec, int c) -> unsigned long long {
+    const int kind = rec[CR_KIND];
+    const int32_t* x0 = content + (size_t)((kind == 0 || kind == 2) ? c : PARENT(c)) * S;
+    const int32_t* x1 = wrap + (size_t)c * S;
+    const int32_t* x2 = content + (size_t)c * S;
     const int nr = rec[CR_NREAC];
+    unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
-      if (((v >> 24) & 3) != row) continue;
+      const int row = (v >> 24) & 3;
+      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
       acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &ovf);
     }
     return acc;
-  };
-  // combinatorial count of rule i at context slot c (c is the context for
-  // LOCAL / CREATE, the child for PARENT_CHILD / DISSOLVE)
-  auto count_at = [&](const int32_t* rec, int c) -> unsigned long long {
-    const int kind = rec[CR_KIND];
-    if (kind == 0 || kind == 2) return pattern(rec, 0, content + (size_t)c * S, 1ull);
-    const int qq = PARENT(c);
-    unsigned long long acc = pattern(rec, 0, content + (size_t)qq * S, 1ull);
-    acc = pattern(rec, 1, wrap + (size_t)c * S, acc);
-    return pattern(rec, 2, content + (size_t)c * S, acc);
   };
   // candidate contexts of rule i, in ascending slot order
   auto ctx_mask = [&](const int32_t* rec) -> unsigned long long {
@@ -199,9 +264,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const double b = nd < 16 ? LEAF(2 * nd + 1) : NODE(2 * nd - 31);
     return __dadd_rn(a, b);
   };
+  // leaves over the lanes, then the internal nodes by every lane in order
+  // (each lane writes the values every other lane writes)
   auto rebuild_tree = [&]() {
-    for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
+    for (int l = gl; l < 32; l += kL) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
+    grp.sync();
     for (int nd = 0; nd < TREE_NODES; ++nd) NODE(nd) = node_val(nd);
+    grp.sync();
   };
 
   // observable index of the content / wrap total of (label, species) and of the alive count
@@ -213,7 +282,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     int32_t* dst = prm.states != nullptr ? prm.states + ((size_t)q * G + g) * O : nullptr;
     unsigned long long* sdst = prm.sums != nullptr ? prm.sums + ((size_t)p * G + g) * O : nullptr;
     unsigned long long* qdst = prm.sumsq != nullptr ? prm.sumsq + ((size_t)p * G + g) * O * 2 : nullptr;
-    for (int o = 0; o < O; ++o) {
+    for (int o = gl; o < O; o += kL) {
       const long long v = tot[o];
       const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
       if (dst) dst[o] = sv;
@@ -224,13 +293,14 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const double* gm = prm.grad_means + ((size_t)p * G + g) * O;
       const double* mm = prm.means + ((size_t)p * G + g) * O;
       double cg = 0.0;
-      for (int o = 0; o < O; ++o) {
+      for (int o = gl; o < O; o += kL) {
         const long long v = tot[o];
         const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
         cg = __dadd_rn(cg, __dmul_rn(gm[o], __dadd_rn((double)sv, -mm[o])));
       }
+      cg = grp.sum(cg);
       const double gt = prm.grid[g];
-      for (int i = 0; i < M; ++i) {
+      for (int i = gl; i < M; i += kL) {
         const double Ig = __dadd_rn(Iac[i], __dmul_rn(u63_to_double_rn(HV(i)), __dadd_rn(gt, -tl[i])));
         const double Si = __dadd_rn(__ddiv_rn((double)Nf[i], kp[i]), -Ig);
         part[i] = __dadd_rn(part[i], __dmul_rn(cg, Si));
@@ -245,14 +315,16 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   auto finalize = [&]() {
     if (prm.ckpt != nullptr) {
       int32_t* rec = prm.ckpt + (size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W);
-      *reinterpret_cast<double*>(rec) = t;
-      *reinterpret_cast<unsigned long long*>(rec + 2) = h;
-      rec[4] = (int32_t)n;
-      rec[5] = gi;
-      rec[6] = status;
-      rec[7] = 0;
+      if (gl == 0) {
+        *reinterpret_cast<double*>(rec) = t;
+        *reinterpret_cast<unsigned long long*>(rec + 2) = h;
+        rec[4] = (int32_t)n;
+        rec[5] = gi;
+        rec[6] = status;
+        rec[7] = 0;
+      }
       const unsigned long long alive = *alive_p;
-      for (int c = 0; c < C; ++c) {
+      for (int c = gl; c < C; c += kL) {
         int32_t* row = rec + CKPT_HEADER_WORDS + (size_t)c * W;
         const bool a = (alive >> c) & 1ull;
         row[0] = a ? 1 : 0;
@@ -264,12 +336,15 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         }
       }
     }
-    if (prm.traj_status) prm.traj_status[q] = status;
-    if (prm.traj_events) prm.traj_events[q] = (long long)n;
-    if (prm.traj_hash) prm.traj_hash[q] = h;
-    if (prm.traj_final_t) prm.traj_final_t[q] = t;
+    if (gl == 0) {
+      if (prm.traj_status) prm.traj_status[q] = status;
+      if (prm.traj_events) prm.traj_events[q] = (long long)n;
+      if (prm.traj_hash) prm.traj_hash[q] = h;
+      if (prm.traj_final_t) prm.traj_final_t[q] = t;
+    }
     if (kSens)
-      for (int i = 0; i < M; ++i) prm.partials[(size_t)q * M + i] = part[i];
+      for (int i = gl; i < M; i += kL) prm.partials[(size_t)q * M + i] = part[i];
+    grp.sync();   // the slab is reused by the next trajectory
   };
   // fold H_i's contribution since tl_i into the integral before H_i changes
   auto integrate = [&](int i, double tnow) {
@@ -292,12 +367,12 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     ovf = false;
     status = TS_OK;
     bool bad = bad_grid;
-    for (int j = 0; j < M; ++j) {
+    for (int j = gl; j < M; j += kL) {
       const long long kb = dbits(kp[j]);
       if (!(kb > 0 && kb < 0x7FF0000000000000ll)) bad = true;
     }
     if (kSens) {
-      for (int i = 0; i < M; ++i) {
+      for (int i = gl; i < M; i += kL) {
         Iac[i] = 0.0;
         tl[i] = 0.0;
         part[i] = 0.0;
@@ -317,8 +392,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       img = rec + CKPT_HEADER_WORDS;
     }
     unsigned long long alive = 0ull;
-    for (int l = 0; l < L; ++l) labmask[l] = 0ull;
-    for (int c = 0; c < C; ++c) {
+    for (int c = gl; c < C; c += kL) {
       chmask[c] = 0ull;
       const int32_t* row = img + (size_t)c * W;
       const int a = row[0];
@@ -344,10 +418,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         }
       }
     }
+    alive = grp.or_all(alive);
     if (!(alive & 1ull)) bad = true;
+    grp.sync();
+    bad = grp.any(bad);
     if (!bad) {
       // every alive slot's parent chain reaches the root through alive slots
-      for (int c = 1; c < C && !bad; ++c) {
+      for (int c = 1 + gl; c < C; c += kL) {
         if (!((alive >> c) & 1ull)) continue;
         int qq = c, steps = 0;
         while (qq != 0) {
@@ -358,32 +435,44 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
           }
         }
       }
+      bad = grp.any(bad);
     }
     if (bad) {
       status = TS_BAD_INPUT;
       if (prm.states != nullptr) {
         int32_t* dst = prm.states + (size_t)q * G * O;
-        for (long long e = 0; e < (long long)G * O; ++e) dst[e] = 0;
+        for (long long e = gl; e < (long long)G * O; e += kL) dst[e] = 0;
       }
-      *alive_p = 0ull;
+      if (gl == 0) *alive_p = 0ull;
+      grp.sync();
       return 1;
     }
-    *alive_p = alive;
-    for (int c = 0; c < C; ++c) {
-      if (!((alive >> c) & 1ull)) continue;
-      labmask[LABEL(c)] |= 1ull << c;
-      if (c > 0) chmask[PARENT(c)] |= 1ull << c;
+    if (gl == 0) {
+      *alive_p = alive;
+      for (int l = 0; l < L; ++l) labmask[l] = 0ull;
+      for (int c = 0; c < C; ++c) {
+        if (!((alive >> c) & 1ull)) continue;
+        labmask[LABEL(c)] |= 1ull << c;
+        if (c > 0) chmask[PARENT(c)] |= 1ull << c;
+      }
     }
-    for (int o = 0; o < O; ++o) tot[o] = 0;
-    for (int c = 0; c < C; ++c) {
-      if (!((alive >> c) & 1ull)) continue;
-      const int l = LABEL(c);
-      for (int x = 0; x < S; ++x) tot[OC(l, x)] += content[(size_t)c * S + x];
-      if (l > 0)
-        for (int x = 0; x < S; ++x) tot[OW(l, x)] += wrap[(size_t)c * S + x];
-      tot[OA(l)] += 1;
+    for (int o = gl; o < O; o += kL) tot[o] = 0;
+    grp.sync();
+    for (int x = gl; x < S; x += kL) {
+      for (int c = 0; c < C; ++c) {
+        if (!((alive >> c) & 1ull)) continue;
+        const int l = LABEL(c);
+        tot[OC(l, x)] += content[(size_t)c * S + x];
+        if (l > 0) tot[OW(l, x)] += wrap[(size_t)c * S + x];
+      }
     }
-    for (int i = 0; i < M; ++i) HV(i) = total_h(i);
+    if (gl == 0) {
+      for (int c = 0; c < C; ++c)
+        if ((alive >> c) & 1ull) tot[OA(LABEL(c))] += 1;
+    }
+    for (int i = gl; i < M; i += kL) HV(i) = total_h(i);
+    ovf = grp.any(ovf);
+    grp.sync();
     rebuild_tree();
     return 0;
   };
@@ -447,7 +536,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     return TS_OK;
   };
 
-  // the rewrite of rule j at context c, after apply_check accepted it
+  // the rewrite of rule j at context c, after apply_check accepted it (one lane)
   auto apply = [&](const int32_t* rec, int c) {
     const int kind = rec[CR_KIND];
     const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
@@ -575,39 +664,87 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
   };
 
-  auto step = [&]() -> bool {
+  // context of rule `rec` for the integer draw xc in [0, H_j): the first
+  // context, in ascending slot order, whose running count exceeds xc
+  auto choose_context = [&](const int32_t* rec, unsigned long long xc) -> int {
+    const unsigned long long m = ctx_mask(rec);
+    int ctx = -1, lastc = -1;
+    if (kL == 1) {
+      unsigned long long mm = m, cum = 0ull;
+      while (mm) {
+        const int c = __ffsll((long long)mm) - 1;
+        mm &= mm - 1ull;
+        if (!ctx_ok(rec, c)) continue;
+        const unsigned long long hc = count_at(rec, c);
+        if (hc == 0ull) continue;
+        lastc = c;
+        cum += hc;
+        if (xc < cum) {
+          ctx = c;
+          break;
+        }
+      }
+    } else {
+      // rounds of kL consecutive slots, lane k taking slot r0 + k: a group
+      // prefix sum over the round gives every lane its running count
+      unsigned long long base = 0ull;
+      for (int r0 = 0; r0 < C; r0 += kL) {
+        const unsigned long long rm = (m >> r0) & ((1ull << kL) - 1ull);
+        if (rm == 0ull) continue;
+        const int c = r0 + gl;
+        unsigned long long hc = 0ull;
+        if (((rm >> gl) & 1ull) && ctx_ok(rec, c)) hc = count_at(rec, c);
+        const unsigned long long incl = grp.incl_scan(hc);
+        const unsigned nz = grp.ballot(hc != 0ull);
+        const unsigned hit = grp.ballot(hc != 0ull && xc < base + incl);
+        if (nz) lastc = r0 + (31 - __clz((int)nz));
+        if (hit) {
+          ctx = r0 + __ffs((int)hit) - 1;
+          break;
+        }
+        base += grp.bcast(incl, kL - 1);
+      }
+    }
+    if (ctx < 0) ctx = lastc;
+    if (ctx < 0) ctx = 0;  // unreachable: H_j > 0 has a context with h > 0
+    return ctx;
+  };
+
+  // one event or the end of the trajectory: 0 = running, 1 = ended with grid
+  // points left to fill, 2 = ended with the grid complete (or left to a resume)
+  auto step = [&]() -> int {
     if (ovf) {
       status = TS_PROP_OVERFLOW;
       if (kSens)
-        for (int i = 0; i < M; ++i) HV(i) = 0ull;
-      fill();
-      return true;
+        for (int i = gl; i < M; i += kL) HV(i) = 0ull;
+      grp.sync();
+      return 1;
     }
     if ((long long)n == prm.max_events) {
       status = TS_EVENT_LIMIT;
-      fill();
-      return true;
+      return 1;
     }
     const double a0 = NODE(TREE_ROOT);
     const long long a0b = dbits(a0);
     if (a0b == 0) {
       status = TS_ABSORBED;
-      fill();
-      return true;
+      return 1;
     }
     if (a0b >= 0x7FF0000000000000ll) {
       status = TS_PROP_OVERFLOW;
       if (kSens)
-        for (int i = 0; i < M; ++i) HV(i) = 0ull;
-      fill();
-      return true;
+        for (int i = gl; i < M; i += kL) HV(i) = 0ull;
+      grp.sync();
+      return 1;
     }
     // the deadline is read every 1024 events, never before a trajectory has
     // applied 1024 events in this launch, so every launch makes progress
-    if ((n & 1023u) == 0u && n != n_launch && deadline != ~0ull && globaltimer_ns() > deadline) {
-      status = TS_TIMEOUT;
-      if (prm.ckpt == nullptr) fill();   // with a checkpoint the rest is recorded on resume
-      return true;
+    if ((n & 1023u) == 0u && n != n_launch && deadline != ~0ull) {
+      const bool late = grp.bcast(gl == 0 ? globaltimer_ns() > deadline : false, 0);
+      if (late) {
+        status = TS_TIMEOUT;
+        return prm.ckpt == nullptr ? 1 : 2;   // with a checkpoint the rest is recorded on resume
+      }
     }
     const uint32_t rr = (uint32_t)r + prm.r_offset;
     const uint4 w = philox4x32_10(make_uint4(n, 0u, rr, (uint32_t)p), prm.key0, prm.key1);
@@ -623,7 +760,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     if (tnb > T_bits) {
       status = TS_OK;
-      return true;
+      return 2;
     }
     // 1. rule: guarded descent of x = u_sel * a0
     double x = __dmul_rn(u_sel, a0);
@@ -669,31 +806,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     j = min(max(j, 0), M - 1);
     const int32_t* rec = s_rules + j * CWC_RULE_WORDS;
-    // 2. context: integer draw xc in [0, H_j), first context whose running count exceeds it
+    // 2. context: integer draw xc in [0, H_j)
     const uint4 w1 = philox4x32_10(make_uint4(n, 1u, rr, (uint32_t)p), prm.key0, prm.key1);
     const unsigned long long Wd = (unsigned long long)w1.x | ((unsigned long long)w1.y << 32);
     const unsigned long long xc = __umul64hi(Wd, HV(j));
-    int ctx = -1;
-    {
-      unsigned long long m = ctx_mask(rec);
-      unsigned long long cum = 0ull;
-      int lastc = -1;
-      while (m) {
-        const int c = __ffsll((long long)m) - 1;
-        m &= m - 1ull;
-        if (!ctx_ok(rec, c)) continue;
-        const unsigned long long hc = count_at(rec, c);
-        if (hc == 0ull) continue;
-        lastc = c;
-        cum += hc;
-        if (xc < cum) {
-          ctx = c;
-          break;
-        }
-      }
-      if (ctx < 0) ctx = lastc;
-      if (ctx < 0) ctx = 0;  // unreachable: H_j > 0 has a context with h > 0
-    }
+    const int ctx = choose_context(rec, xc);
     // 3. update.  Only contexts in `touched` can change their counts: the
     // rewritten compartments, their children (which read the parent content),
     // and the free slots (one of which CREATE fills).  Each dependent rule
@@ -702,8 +819,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const int ast = apply_check(rec, ctx);
     if (ast != TS_OK) {
       status = ast;
-      fill();
-      return true;
+      return 1;
     }
     const int kind_j = rec[CR_KIND];
     unsigned long long touched = chmask[ctx];
@@ -714,43 +830,48 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const int qq = PARENT(ctx);
       touched |= (1ull << qq) | chmask[qq];
     }
-    if (kSens) Nf[j] += 1;
+    if (kSens && gl == 0) Nf[j] += 1;
     const int doff = rec[CR_DEPOFF], dcnt = rec[CR_DEPCNT];
-    for (int e = 0; e < dcnt; ++e) {
+    for (int e = gl; e < dcnt; e += kL) {
       const int i = s_deps[doff + e];
       const int32_t* ri = s_rules + i * CWC_RULE_WORDS;
       if (kSens) integrate(i, tn);
       const unsigned long long cm = ctx_mask(ri);
       HV(i) = (cm & ~touched) == 0ull ? 0ull : HV(i) - partial_h(ri, cm & touched);
     }
-    apply(rec, ctx);
-    for (int e = 0; e < dcnt; ++e) {
+    grp.sync();
+    if (gl == 0) apply(rec, ctx);
+    grp.sync();
+    for (int e = gl; e < dcnt; e += kL) {
       const int i = s_deps[doff + e];
       const int32_t* ri = s_rules + i * CWC_RULE_WORDS;
       const unsigned long long s2 = HV(i) + partial_h(ri, ctx_mask(ri) & touched);
       if ((s2 >> 63) != 0ull) ovf = true;
       HV(i) = s2;
     }
+    ovf = grp.any(ovf);
+    grp.sync();
     if (B == 1) {
-      for (int e = 0; e < dcnt; ++e) {
+      for (int e = gl; e < dcnt; e += kL) {
         const int i = s_deps[doff + e];
         LEAF(i) = prop_of(i);
       }
     } else {
       unsigned lm = (unsigned)rec[CR_LEAFMASK];
-      while (lm) {
+      for (int k = 0; lm; ++k) {
         const int ll = __ffs(lm) - 1;
         lm &= lm - 1u;
-        LEAF(ll) = leaf_sum(ll);
+        if ((k & (kL - 1)) == gl) LEAF(ll) = leaf_sum(ll);
       }
     }
+    grp.sync();
     unsigned nm = (unsigned)rec[CR_NODEMASK];
     while (nm) {
       const int k = __ffs(nm) - 1;
       nm &= nm - 1u;
       NODE(k) = node_val(k);
     }
-    if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
+    if (gl == 0 && prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
       const size_t at = (size_t)q * prm.log_cap + n;
       prm.log_rule[at] = j;
       if (prm.log_slot) prm.log_slot[at] = ctx;
@@ -759,16 +880,23 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     t = tn;
     ++n;
     h = fnv1a_event(h, (uint32_t)j, (uint32_t)ctx);
-    return false;
+    grp.sync();
+    return 0;
   };
 
   bool need_new = true;
   for (;;) {
     if (need_new) {
       if (kQueue) {
-        q = cwc_grab_next(prm.ws);
+        if (kL == 1) {
+          q = cwc_grab_next(prm.ws);
+        } else {
+          long long v = 0;
+          if (gl == 0) v = (long long)atomicAdd(&prm.ws->queue_next, 1ull);
+          q = grp.bcast(v, 0);
+        }
       } else {
-        q = first ? gthread : q + qstride;
+        q = first ? gslot : q + (long long)gridDim.x * NT;
         first = false;
       }
       if (q >= Q) break;
@@ -781,7 +909,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       n_launch = n;
       need_new = false;
     }
-    if (step()) {
+    const int ended = step();
+    if (ended != 0) {
+      if (ended == 1) fill();
       finalize();
       need_new = true;
     }
@@ -793,10 +923,10 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
 
 // ---------------------------------------------------------------------------
 
-template <bool kQueue, bool kSens>
+template <int kL, bool kQueue, bool kSens>
 static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, size_t* smem_out) {
-  auto kern = cwc_ssa_kernel<kQueue, kSens>;
-  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * cwc_thread_bytes(prm.M);
+  auto kern = cwc_ssa_kernel<kL, kQueue, kSens>;
+  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)(T / kL) * cwc_thread_bytes(prm.M);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -806,7 +936,8 @@ static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, si
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = (long long)sms * per_sm;
-  const long long need = (prm.Q + T - 1) / T;
+  const long long per_block = T / kL;
+  const long long need = (prm.Q + per_block - 1) / per_block;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   *blocks_out = (int)blocks;
@@ -814,29 +945,46 @@ static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, si
   return cudaSuccess;
 }
 
-// Launch shape (threads per block, blocks): both layouts use a grid of at most
-// the resident capacity, so the term slabs number threads, not trajectories.
-cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int T, int* blocks) {
-  size_t smem = 0;
+template <int kL>
+static cudaError_t cwc_config_l(const CwcParams& prm, bool queue, int T, int* blocks, size_t* smem) {
   const bool sens = prm.sens != 0;
   if (queue)
-    return sens ? cwc_config_t<true, true>(prm, T, blocks, &smem) : cwc_config_t<true, false>(prm, T, blocks, &smem);
-  return sens ? cwc_config_t<false, true>(prm, T, blocks, &smem) : cwc_config_t<false, false>(prm, T, blocks, &smem);
+    return sens ? cwc_config_t<kL, true, true>(prm, T, blocks, smem) : cwc_config_t<kL, true, false>(prm, T, blocks, smem);
+  return sens ? cwc_config_t<kL, false, true>(prm, T, blocks, smem) : cwc_config_t<kL, false, false>(prm, T, blocks, smem);
 }
 
-int cwc_best_threads(const CwcParams& prm, bool queue) {
+static cudaError_t cwc_config(const CwcParams& prm, bool queue, int lanes, int T, int* blocks, size_t* smem) {
+  if (T < 32 || T > 256 || T % 32 != 0) return cudaErrorInvalidValue;
+  switch (lanes) {
+    case 1: return cwc_config_l<1>(prm, queue, T, blocks, smem);
+    case 4: return cwc_config_l<4>(prm, queue, T, blocks, smem);
+    case 8: return cwc_config_l<8>(prm, queue, T, blocks, smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool cwc_lanes_supported(int lanes) { return lanes == 1 || lanes == 4 || lanes == 8; }
+
+// Launch shape (threads per block, blocks): both layouts use a grid of at most
+// the resident capacity, so the term slabs number resident groups, not
+// trajectories.
+cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int lanes, int T, int* blocks) {
+  size_t smem = 0;
+  return cwc_config(prm, queue, lanes, T, blocks, &smem);
+}
+
+// Threads per block giving the most resident warps.
+int cwc_best_threads(const CwcParams& prm, bool queue, int lanes) {
   int best_T = 32, best_warps = -1;
   for (int T = 32; T <= 256; T += 32) {
-    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * cwc_thread_bytes(prm.M);
+    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)(T / lanes) * cwc_thread_bytes(prm.M);
     if (smem > 227 * 1024) break;
-    int per_sm = 0;
-    cudaError_t e = queue ? cudaFuncSetAttribute(cwc_ssa_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                          : cudaFuncSetAttribute(cwc_ssa_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) break;
-    e = queue ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<true, false>, T, smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cwc_ssa_kernel<false, false>, T, smem);
-    if (e != cudaSuccess) break;
-    const int warps = per_sm * T / 32;
+    int blocks = 0;
+    size_t sm = 0;
+    CwcParams big = prm;
+    big.Q = 1ll << 40;   // resident capacity, not the batch
+    if (cwc_config(big, queue, lanes, T, &blocks, &sm) != cudaSuccess) break;
+    const int warps = blocks * T / 32;
     if (warps >= best_warps) {
       best_warps = warps;
       best_T = T;
@@ -846,29 +994,38 @@ int cwc_best_threads(const CwcParams& prm, bool queue) {
 }
 
 int cwc_table_bytes_host(int M, int n_deps) { return cwc_table_bytes(M, n_deps); }
+int cwc_thread_bytes_host(int M) { return cwc_thread_bytes(M); }
 long long cwc_slab_words_host(int S, int L, int C, int M, bool sens) { return cwc_slab_words(S, L, C, M, sens); }
 
-cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks,
+template <int kL>
+static void cwc_launch_l(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, size_t smem,
+                         cudaStream_t stream) {
+  const bool sens = prm.sens != 0;
+  if (queue) {
+    if (sens)
+      cwc_ssa_kernel<kL, true, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+    else
+      cwc_ssa_kernel<kL, true, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  } else {
+    if (sens)
+      cwc_ssa_kernel<kL, false, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+    else
+      cwc_ssa_kernel<kL, false, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  }
+}
+
+cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int lanes, int T, int blocks,
                        cudaStream_t stream) {
   size_t smem = 0;
   int b = 0;
-  const bool sens = prm.sens != 0;
-  cudaError_t e;
-  if (queue)
-    e = sens ? cwc_config_t<true, true>(prm, T, &b, &smem) : cwc_config_t<true, false>(prm, T, &b, &smem);
-  else
-    e = sens ? cwc_config_t<false, true>(prm, T, &b, &smem) : cwc_config_t<false, false>(prm, T, &b, &smem);
+  cudaError_t e = cwc_config(prm, queue, lanes, T, &b, &smem);
   if (e != cudaSuccess) return e;
-  if (queue) {
-    if (sens)
-      cwc_ssa_kernel<true, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
-    else
-      cwc_ssa_kernel<true, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
-  } else {
-    if (sens)
-      cwc_ssa_kernel<false, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
-    else
-      cwc_ssa_kernel<false, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+  if (blocks > b) return cudaErrorInvalidConfiguration;   // the slabs were sized for at most b blocks
+  switch (lanes) {
+    case 1: cwc_launch_l<1>(prm, lc, queue, T, blocks, smem, stream); break;
+    case 4: cwc_launch_l<4>(prm, lc, queue, T, blocks, smem, stream); break;
+    case 8: cwc_launch_l<8>(prm, lc, queue, T, blocks, smem, stream); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

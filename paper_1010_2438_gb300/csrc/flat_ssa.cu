@@ -289,40 +289,36 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     return 0;
   };
 
-  // one event (or the end of the trajectory); returns true when it ended
-  auto step = [&]() -> bool {
+  // one event or the end of the trajectory: 0 = running, 1 = ended with grid
+  // points left to fill, 2 = ended with the grid complete (or left to a resume)
+  auto step = [&]() -> int {
     if (ovf) {
       status = TS_PROP_OVERFLOW;
       if (kSens)
         for (int i = 0; i < M; ++i) Hd[i * T] = 0.0;
-      fill();
-      return true;
+      return 1;
     }
     if ((long long)n == prm.max_events) {
       status = TS_EVENT_LIMIT;
-      fill();
-      return true;
+      return 1;
     }
     const double a0 = NODE(TREE_ROOT);
     const long long a0b = dbits(a0);
     if (a0b == 0) {
       status = TS_ABSORBED;
-      fill();
-      return true;
+      return 1;
     }
     if (a0b >= 0x7FF0000000000000ll) {
       status = TS_PROP_OVERFLOW;
       if (kSens)
         for (int i = 0; i < M; ++i) Hd[i * T] = 0.0;
-      fill();
-      return true;
+      return 1;
     }
     // the deadline is read every 1024 events, never before a trajectory has
     // applied 1024 events in this launch, so every launch makes progress
     if ((n & 1023u) == 0u && n != n_launch && deadline != ~0ull && globaltimer_ns() > deadline) {
       status = TS_TIMEOUT;
-      if (prm.ckpt == nullptr) fill();   // with a checkpoint the rest is recorded on resume
-      return true;
+      return prm.ckpt == nullptr ? 1 : 2;   // with a checkpoint the rest is recorded on resume
     }
     const uint4 w = philox4x32_10(make_uint4(n, 0u, (uint32_t)r + prm.r_offset, (uint32_t)p), prm.key0, prm.key1);
     const double u_tau = uniform52(w.x, w.y);
@@ -337,7 +333,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     }
     if (tnb > T_bits) {
       status = TS_OK;
-      return true;
+      return 2;
     }
     // rule selection: guarded descent of x = u_sel * a0
     double x = __dmul_rn(u_sel, a0);
@@ -393,8 +389,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       const int dv = v >> 16;
       if (dv > 0 && CNT(v & 0xffff) > 0x7FFFFFFF - dv) {
         status = TS_INT_OVERFLOW;
-        fill();
-        return true;
+        return 1;
       }
     }
     for (int d = 0; d < nd_; ++d) {
@@ -444,7 +439,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     t = tn;
     ++n;
     h = fnv1a_event(h, (uint32_t)j, 0u);
-    return false;
+    return 0;
   };
 
   bool need_new = true;
@@ -467,7 +462,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       n_launch = n;
       need_new = false;
     }
-    if (step()) {
+    const int ended = step();
+    if (ended != 0) {
+      if (ended == 1) fill();
       finalize();
       need_new = true;
     }

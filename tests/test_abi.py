@@ -102,3 +102,34 @@ def test_simulate_argument_checks_on_host(lib):
     assert lib.cwc_simulate_workspace_size(None, ctypes.byref(args), ctypes.byref(n)) == capi.CWC_ERR_INVALID_ARG
     assert lib.cwc_model_num_observables(None) == -1
     lib.cwc_model_destroy(None)  # NULL is ignored
+
+
+def _header_struct_fields(name):
+    """(field, is_pointer, base type) of a typedef'd struct in the header."""
+    text = open(os.path.join(ROOT, "include", "cwcgpu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, rest = re.match(r"(?:const\s+)?([A-Za-z_0-9]+)\s*(.*)", decl).groups()
+        for nm in rest.split(","):
+            nm = nm.strip()
+            fields.append((nm.lstrip("*").strip(), nm.startswith("*"), typ))
+    return fields
+
+
+@pytest.mark.parametrize("name", ["cwc_sim_args", "cwc_sens_args", "cwc_model_desc"])
+def test_ctypes_structs_follow_the_header(name):
+    """Field names, order and widths of the Python mirror equal the C
+    declarations, so the binding passes what the library reads."""
+    sizes = {"int32_t": 4, "uint32_t": 4, "int64_t": 8, "uint64_t": 8, "size_t": 8, "double": 8}
+    hdr = _header_struct_fields(name)
+    py = getattr(capi, name)._fields_
+    assert [f[0] for f in hdr] == [f[0] for f in py]
+    for (nm, is_ptr, typ), (_, ctype) in zip(hdr, py):
+        want = 8 if is_ptr else sizes[typ]
+        assert ctypes.sizeof(ctype) == want, nm

@@ -38,18 +38,21 @@ def check(batch, threads=8, **kw):
     return g, o
 
 
-@pytest.mark.parametrize("layout", [capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE])
-def test_cwc3x24_bit_exact_with_event_log(layout):
+@pytest.mark.parametrize("layout,lanes", [(capi.CWC_LAYOUT_STATIC, 1), (capi.CWC_LAYOUT_QUEUE, 1),
+                                          (capi.CWC_LAYOUT_STATIC, 4), (capi.CWC_LAYOUT_QUEUE, 8)])
+def test_cwc3x24_bit_exact_with_event_log(layout, lanes):
+    """One lane or a group of 4 / 8 lanes per term give the oracle's events."""
     b = W.cwc3x24(R=48)
-    g, o = check(b, log_cap=512, layout=layout)
+    g, o = check(b, log_cap=512, layout=layout, lanes=lanes)
     assert np.all(g["status"] == oracle.ST_OK)
 
 
-def test_cwc3x24_structural_events_occur_and_match():
+@pytest.mark.parametrize("lanes", [1, 4, 8])
+def test_cwc3x24_structural_events_occur_and_match(lanes):
     """Longer horizon so that creations and dissolutions certainly happen."""
     b0 = W.cwc3x24(R=24, G=50)
     b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 3.0, b0.R, b0.seed)
-    g, o = check(b, log_cap=40000)
+    g, o = check(b, log_cap=40000, lanes=lanes)
     lr = o["log_rule"]
     kinds = b.model.kind[lr[lr >= 0]]
     assert np.sum(kinds == W.CREATE) > 0 and np.sum(kinds == W.DISSOLVE) > 0
@@ -66,15 +69,18 @@ def _transport(n_children=2):
     return m, img
 
 
-def test_law_models_bit_exact():
+@pytest.mark.parametrize("lanes", [1, 8])
+def test_law_models_bit_exact(lanes):
     m, img = _transport()
-    check(W.Batch(m, np.array([[0.4, 1.1]]), img[None], np.array([0.0, 0.2, 0.6, 1.5, 6.0]), 300, 8), log_cap=64)
+    check(W.Batch(m, np.array([[0.4, 1.1]]), img[None], np.array([0.0, 0.2, 0.6, 1.5, 6.0]), 300, 8), log_cap=64,
+          lanes=lanes)
     # create / dissolve with a conserved token
     rules = [W.RuleSpec(W.CREATE, 0, 1, lhs_ctx={0: 1}, rhs_wrap={0: 1}), W.RuleSpec(W.DISSOLVE, 0, 1)]
     m = W.cwc_model(1, 2, 13, rules)
     img = W.empty_slot_image(m)
     img[0, 4] = 12
-    check(W.Batch(m, np.array([[0.9, 0.5]]), img[None], np.array([0.0, 0.3, 1.0, 3.0, 10.0]), 300, 9), log_cap=64)
+    check(W.Batch(m, np.array([[0.9, 0.5]]), img[None], np.array([0.0, 0.3, 1.0, 3.0, 10.0]), 300, 9), log_cap=64,
+          lanes=lanes)
     # dissolution reparents a label-2 child to the top, which a transport rule then drains
     rules = [W.RuleSpec(W.DISSOLVE, 0, 1), W.RuleSpec(W.PARENT_CHILD, 0, 2, lhs_child={0: 1}, rhs_ctx={0: 1})]
     m = W.cwc_model(1, 3, 3, rules)
@@ -82,16 +88,18 @@ def test_law_models_bit_exact():
     img[1, :3] = [1, 1, 0]
     img[2, :3] = [1, 2, 1]
     img[2, 4] = 5
-    g, _ = check(W.Batch(m, np.array([[1.0, 1.0]]), img[None], np.array([0.0, 200.0]), 64, 10), log_cap=8)
+    g, _ = check(W.Batch(m, np.array([[1.0, 1.0]]), img[None], np.array([0.0, 200.0]), 64, 10), log_cap=8,
+                 lanes=lanes)
     assert np.all(g["status"] == oracle.ST_ABSORBED)
 
 
-def test_capacity_and_bad_slot_images():
+@pytest.mark.parametrize("lanes", [1, 8])
+def test_capacity_and_bad_slot_images(lanes):
     rules = [W.RuleSpec(W.CREATE, 0, 1, lhs_ctx={0: 1})]
     m = W.cwc_model(1, 2, 3, rules)
     img = W.empty_slot_image(m)
     img[0, 4] = 10
-    g, _ = check(W.Batch(m, np.array([[1.0]]), img[None], np.array([0.0, 1e6]), 4, 11))
+    g, _ = check(W.Batch(m, np.array([[1.0]]), img[None], np.array([0.0, 1e6]), 4, 11), lanes=lanes)
     assert np.all(g["status"] == oracle.ST_CAPACITY)
     m, good = _transport(2)
     bads = []
@@ -104,7 +112,7 @@ def test_capacity_and_bad_slot_images():
     x = good.copy(); x[1, 0] = 2; bads.append(x)            # alive flag not 0/1
     x = good.copy(); x[1, 2] = 7; bads.append(x)            # parent out of range
     for img in bads:
-        g, _ = check(W.Batch(m, np.array([[0.4, 1.1]]), img[None], np.array([0.0, 1.0]), 3, 1))
+        g, _ = check(W.Batch(m, np.array([[0.4, 1.1]]), img[None], np.array([0.0, 1.0]), 3, 1), lanes=lanes)
         assert np.all(g["status"] == oracle.ST_BAD_INPUT)
 
 
@@ -151,7 +159,8 @@ def test_cwc_replica_variance_and_interval_bit_exact():
     assert np.array_equal(g["ci90"].view(np.int64), ci.view(np.int64))
 
 
-def test_cwc_sensitivity_partials_match_oracle():
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_cwc_sensitivity_partials_match_oracle(lanes):
     """Score replay on a compartment model (structural events included):
     per-trajectory partials within 1e-9 * (|x| + mean |x|) of the oracle (the
     integral of H_j is accumulated lazily on the GPU and at every event in the
@@ -163,7 +172,7 @@ def test_cwc_sensitivity_partials_match_oracle():
     means = torch.from_numpy(oracle.mean_observables(b, threads=8)).cuda()
     rng = np.random.default_rng(11)
     gm = torch.from_numpy(rng.standard_normal((1, b.G, cm.n_observables)) * 1e-3).cuda()
-    res = api.sensitivity(cm, rates, init, grid, b.R, b.seed, means, gm, partials=True)
+    res = api.sensitivity(cm, rates, init, grid, b.R, b.seed, means, gm, partials=True, lanes=lanes)
     torch.cuda.synchronize()
     gp = res["partials"].cpu().numpy().reshape(b.R, -1)
     ograd, op = oracle.sensitivity(b, means.cpu().numpy(), gm.cpu().numpy(), threads=8)

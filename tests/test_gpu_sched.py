@@ -34,8 +34,8 @@ def test_autotune_choice_and_all_candidates_agree():
     cm = api.CompiledModel(b.model)
     rates, init, grid = api.device_inputs(b)
     ref = api.simulate(cm, rates, init, grid, b.R, b.seed, layout=capi.CWC_LAYOUT_STATIC, block_threads=64)
-    lay, thr, ms = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=500)
-    assert lay in (capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE) and 32 <= thr <= 256 and ms > 0
+    lay, thr, lanes, ms = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=500)
+    assert lay in (capi.CWC_LAYOUT_STATIC, capi.CWC_LAYOUT_QUEUE) and 32 <= thr <= 256 and ms > 0 and lanes == 1
     auto = api.simulate(cm, rates, init, grid, b.R, b.seed)          # uses the cached choice
     torch.cuda.synchronize()
     _same(auto, ref)
@@ -67,7 +67,8 @@ def test_cwc_model_autotune_and_graph():
     cm = api.CompiledModel(b.model)
     rates, init, grid = api.device_inputs(b)
     ref = api.simulate(cm, rates, init, grid, b.R, b.seed, layout=capi.CWC_LAYOUT_STATIC, block_threads=32)
-    api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=200)
+    lay, thr, lanes, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=200)
+    assert lanes in (1, 4, 8)
     got = api.simulate(cm, rates, init, grid, b.R, b.seed)
     g = api.GraphedSimulation(cm, rates, init, grid, b.R, b.seed)
     out = g.replay()
