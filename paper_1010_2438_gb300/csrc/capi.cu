@@ -81,7 +81,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout: [header 256 B][sums P*G*O int64 if needed][partials Q*M double if needed]
 struct WsLayout {
-  size_t header = 0, sums = 0, sumsq = 0, partials = 0, slabs = 0, order = 0, total = 0;
+  size_t header = 0, sums = 0, sumsq = 0, partials = 0, slabs = 0, order = 0, sens_acc = 0, total = 0;
   bool need_sumsq = false;
   bool need_order = false;        // flat queue layout over several sweep points
   bool need_header = false, need_sums = false, need_partials = false;
@@ -180,6 +180,10 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
   if (w.need_partials) {
     w.partials = off;
     off = align256(off + (size_t)a->P * a->R * m->M * sizeof(double));
+  }
+  if (m->flat && sens) {   // the flat replay's per-trajectory integrals, times and firing counts
+    w.sens_acc = off;
+    off = align256(off + (size_t)a->P * a->R * 3 * m->M * sizeof(double));
   }
   w.need_order = m->flat && chosen_layout(a) == CWC_LAYOUT_QUEUE && a->P > 1 && a->P <= 65536;
   if (w.need_order) {
@@ -632,6 +636,7 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     prm.means = sens->means;
     prm.grad_means = sens->grad_means;
     prm.partials = sens->partials != nullptr ? sens->partials : reinterpret_cast<double*>(ws + w.partials);
+    prm.sens_acc = reinterpret_cast<double*>(ws + w.sens_acc);
   }
   const LogConstants lc = make_log_constants();
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;

@@ -102,6 +102,7 @@ struct FlatParams {
   const double* means;             // [P][G][S]
   const double* grad_means;        // [P][G][S]
   double* partials;                // [Q][M]
+  double* sens_acc;                // score replay: [Q][3][M] int_0^tl H_i dt, tl_i, firings N_i
   // scheduling
   WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)
   int32_t* ckpt;                   // [Q][S + CKPT_HEADER_WORDS] trajectory checkpoints (or null)

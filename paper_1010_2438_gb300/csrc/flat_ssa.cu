@@ -12,7 +12,10 @@
 //                        when needed instead of being stored
 //   node[31][T]  double  internal tree nodes, root = node[30] = a0
 //   cnt[S][T]    int32   species counts
-// plus, for the score replay, Hd/I/tl/partial [M][T] doubles and N [M][T].
+// plus, for the score replay, H_i as doubles [M][T].  The replay's integrals,
+// their times, the firing counts and the partials, touched a few at a time
+// per event, live in global memory per trajectory, so that the replay keeps
+// almost the forward pass's residency.
 // Keeping only the tree and the counts (504 + 4S bytes per trajectory) is
 // what lets 8-10 warps share an SM: GB300's FP64 pipe (~1.6 lane-ops per
 // clock per SM) has long latency, and hiding it needs resident warps.
@@ -53,8 +56,8 @@ __host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
 }
 
 __host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
-  int doubles = 32 + TREE_NODES + (sens ? 4 * M : 0);
-  int ints = S + (sens ? M : 0);
+  int doubles = 32 + TREE_NODES + (sens ? M : 0);
+  int ints = S;
   return doubles * 8 + ints * 4;
 }
 
@@ -74,16 +77,17 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   // Per-thread arrays [index][T]: each pointer below already points at this
   // thread's column, so element i of the array is ptr[i * T].
   double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
-  const int n_dbl_rows = 32 + TREE_NODES + (kSens ? 4 * M : 0);
+  const int n_dbl_rows = 32 + TREE_NODES + (kSens ? M : 0);
   double* leaf = dbase + tid;                                   // [32][T]
   double* node = dbase + 32 * T + tid;                          // [31][T]
-  double* Hd = dbase + (32 + TREE_NODES) * T + tid;             // score replay only: [M][T] each
-  double* Iac = Hd + M * T;
-  double* tl = Iac + M * T;
-  double* part = tl + M * T;
+  double* Hd = dbase + (32 + TREE_NODES) * T + tid;             // score replay only: [M][T]
+  // score replay, per trajectory in global memory (set by start()):
+  double* Iac = nullptr;    // [M] int_0^tl_i H_i dt
+  double* tl = nullptr;     // [M]
+  double* Nf = nullptr;     // [M] firings (whole numbers)
+  double* part = nullptr;   // [M] the trajectory's partials
   int32_t* ibase = reinterpret_cast<int32_t*>(dbase + (size_t)n_dbl_rows * T);
   int32_t* cnt = ibase + tid;                                   // [S][T]
-  int32_t* Nf = ibase + S * T + tid;                            // score replay only: [M][T]
 
 #define LEAF(l) leaf[(l) * T]
 #define NODE(i) node[(i) * T]
@@ -162,9 +166,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
         c = __dadd_rn(c, __dmul_rn(gm[o], __dadd_rn((double)CNT(o), -mm[o])));
       const double gt = prm.grid[g];
       for (int i = 0; i < M; ++i) {
-        const double Ig = __dadd_rn(Iac[i * T], __dmul_rn(Hd[i * T], __dadd_rn(gt, -tl[i * T])));
-        const double Si = __dadd_rn(__ddiv_rn((double)Nf[i * T], kp[i]), -Ig);
-        part[i * T] = __dadd_rn(part[i * T], __dmul_rn(c, Si));
+        const double Ig = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(gt, -tl[i])));
+        const double Si = __dadd_rn(__ddiv_rn(Nf[i], kp[i]), -Ig);
+        part[i] = __dadd_rn(part[i], __dmul_rn(c, Si));
       }
     }
   };
@@ -221,9 +225,6 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     if (prm.traj_events) prm.traj_events[q] = (long long)n;
     if (prm.traj_hash) prm.traj_hash[q] = h;
     if (prm.traj_final_t) prm.traj_final_t[q] = t;
-    if (kSens) {
-      for (int i = 0; i < M; ++i) prm.partials[(size_t)q * M + i] = part[i * T];
-    }
   };
 
   // set up trajectory q: 0 = running, 1 = ended at once (bad input),
@@ -262,7 +263,11 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       CNT(s) = v;
     }
     if (kSens) {
-      for (int i = 0; i < M; ++i) part[i * T] = 0.0;
+      Iac = prm.sens_acc + (size_t)q * 3 * M;
+      tl = Iac + M;
+      Nf = tl + M;
+      part = prm.partials + (size_t)q * M;
+      for (int i = 0; i < M; ++i) part[i] = 0.0;
     }
     if (bad) {
       status = TS_BAD_INPUT;
@@ -275,9 +280,9 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     if (kSens) {
       for (int i = 0; i < M; ++i) {
         Hd[i * T] = u63_to_double_rn(count_h(i));
-        Iac[i * T] = 0.0;
-        tl[i * T] = 0.0;
-        Nf[i * T] = 0;
+        Iac[i] = 0.0;
+        tl[i] = 0.0;
+        Nf[i] = 0.0;
       }
     }
     for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
@@ -397,13 +402,13 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       CNT(v & 0xffff) += v >> 16;
     }
     if (kSens) {
-      Nf[j * T] += 1;
+      Nf[j] = __dadd_rn(Nf[j], 1.0);
       const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
       for (int e = 0; e < dcnt; ++e) {
         const int i = s_deps[doff + e];
         const double hd = u63_to_double_rn(count_h(i));
-        Iac[i * T] = __dadd_rn(Iac[i * T], __dmul_rn(Hd[i * T], __dadd_rn(tn, -tl[i * T])));
-        tl[i * T] = tn;
+        Iac[i] = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(tn, -tl[i])));
+        tl[i] = tn;
         Hd[i * T] = hd;
       }
     }
