@@ -362,14 +362,22 @@ def main():
     kernel_s = t_total / args.steps
     achieved = f_evt * events / kernel_s
     traffic = None
+    issue = None
     tpath = os.path.join(ROOT, "profiles", "flat_ssa_kernel_flat32x64_traffic.txt")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
         if tj.get("kernel_source_hash") == kernel_source_hash() and tj.get("workload") == WORKLOAD:
             traffic = tj.get("dram_bytes_per_launch")
+            # issue-rate roofline of the same kernel (warp instructions issued per
+            # scheduler cycle, of the 1 per cycle peak) and the FP64 pipe's busy
+            # fraction, from the ncu capture of the profiling case
+            issue = {"frac": tj.get("issue_active_frac"), "fp64_pipe_frac": tj.get("fp64_pipe_frac"),
+                     "warps_per_sm": tj.get("warps_per_sm"),
+                     "source": "ncu smsp__issue_active / sm__pipe_fp64_cycles_active, profiling case "
+                               "(profiles/flat_ssa_kernel_flat32x64.md)"}
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9, "unit": "GFLOP/s (FP64)",
-                "frac": achieved / FP64_PEAK_OPS, "traffic": traffic,
+                "frac": achieved / FP64_PEAK_OPS, "traffic": traffic, "issue": issue,
                 "note": "FP64-pipe bound; %.1f algorithmic FP64 ops/event x %d events / %.4f s; peak derived from "
                         "152 SMs x 2 FP64 lanes/clk x 2.07 GHz" % (f_evt, events, kernel_s)}
 
