@@ -334,6 +334,17 @@ cwc_status cwc_sensitivity(const cwc_model* model, const cwc_sim_args* sim, cons
 cwc_status cwc_autotune(const cwc_model* model, const cwc_sim_args* args, int64_t tune_events, void* stream,
                         int32_t* best_layout, int32_t* best_block_threads, double* best_ms, int32_t* best_lanes);
 
+/*
+ * The fixed logarithm of the time step (the atanh series described above,
+ * every operation rounded to nearest, no fused multiply-add) evaluated on the
+ * device for n values: out[i] = log_spec(u[i]).  For checking the kernels'
+ * logarithm against a CPU implementation bit for bit.  u and out are device
+ * arrays of n doubles (caller-owned); inputs outside [2^-53, 1), the range of
+ * the 52-bit uniforms, give NaN.  Asynchronous on `stream`.
+ * Errors: CWC_ERR_INVALID_ARG (n < 0, NULL arrays), CWC_ERR_CUDA.
+ */
+cwc_status cwc_log_spec(const double* u, double* out, int64_t n, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* cwc_last_error(void);
 

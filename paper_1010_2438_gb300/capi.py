@@ -25,7 +25,7 @@ CWC_LAYOUT_AUTO, CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE = range(3)
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = ("cwc_model_create", "cwc_model_destroy", "cwc_model_num_observables", "cwc_simulate_workspace_size",
             "cwc_simulate", "cwc_simulate_noalloc", "cwc_sensitivity_workspace_size", "cwc_sensitivity",
-            "cwc_autotune", "cwc_checkpoint_words", "cwc_last_error", "cwc_version")
+            "cwc_autotune", "cwc_checkpoint_words", "cwc_log_spec", "cwc_last_error", "cwc_version")
 CWC_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 _vp = ctypes.c_void_p
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
         L.cwc_autotune.restype = ctypes.c_int
         L.cwc_checkpoint_words.argtypes = [_vp]
         L.cwc_checkpoint_words.restype = _i32
+        L.cwc_log_spec.argtypes = [_vp, _vp, _i64, _vp]
+        L.cwc_log_spec.restype = ctypes.c_int
         L.cwc_last_error.argtypes = []
         L.cwc_last_error.restype = ctypes.c_char_p
         L.cwc_version.argtypes = []
@@ -160,6 +162,11 @@ def cwc_autotune(handle: int, args: cwc_sim_args, tune_events: int = 0, stream: 
     _check(lib().cwc_autotune(handle, ctypes.byref(args), tune_events, stream, ctypes.byref(lay), ctypes.byref(thr),
                               ctypes.byref(ms), ctypes.byref(lanes)))
     return lay.value, thr.value, lanes.value, ms.value
+
+
+def cwc_log_spec(u_ptr: int, out_ptr: int, n: int, stream: int = 0) -> None:
+    """The device logarithm of the time step over n doubles (device pointers)."""
+    _check(lib().cwc_log_spec(u_ptr, out_ptr, n, stream))
 
 
 def cwc_sensitivity_workspace_size(handle: int, args: cwc_sim_args, sens: cwc_sens_args) -> int:

@@ -31,6 +31,7 @@ cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue,
                        cudaStream_t stream);
 cudaError_t cwc_launch_shape(const CwcParams& prm, bool queue, int lanes, int T, int* blocks);
 int cwc_best_threads(const CwcParams& prm, bool queue, int lanes);
+cudaError_t launch_log_spec(const double* u, double* out, long long n, const LogConstants& lc, cudaStream_t st);
 bool cwc_lanes_supported(int lanes);
 int cwc_thread_bytes_host(int M);
 int cwc_table_bytes_host(int M, int n_deps);
@@ -275,6 +276,16 @@ int pick_threads(const cwc_model* m, const cwc_sim_args* a, const FlatParams& pr
 extern "C" {
 
 const char* cwc_last_error(void) { return g_last_error.c_str(); }
+
+cwc_status cwc_log_spec(const double* u, double* out, int64_t n, void* stream) {
+  g_last_error.clear();
+  if (n < 0) return fail(CWC_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > 0 && (u == nullptr || out == nullptr)) return fail(CWC_ERR_INVALID_ARG, "u and out must not be NULL");
+  const LogConstants lc = make_log_constants();
+  cudaError_t e = launch_log_spec(u, out, (long long)n, lc, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "log kernel launch");
+  return CWC_OK;
+}
 
 const char* cwc_version(void) { return "cwcgpu 0.1 (sm_103a)"; }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "cwc_internal.h"
+#include "ssa_device.cuh"
 
 namespace cwcgpu {
 
@@ -84,6 +85,30 @@ cudaError_t launch_means(const unsigned long long* sums, double* means, long lon
   long long blocks = (n + 255) / 256;
   if (blocks > 65535) blocks = 65535;
   means_kernel<<<(unsigned)blocks, 256, 0, st>>>(sums, means, n, (double)R);
+  return cudaGetLastError();
+}
+
+// The simulation's fixed logarithm over an array (for checking it against
+// the oracle bit for bit).  Inputs outside [2^-53, 1), the range of the
+// uniforms, give NaN.
+__global__ void log_spec_kernel(const double* __restrict__ u, double* __restrict__ out, long long n,
+                                const __grid_constant__ LogConstants lc) {
+  __shared__ double s_eln2[54];
+  for (int i = threadIdx.x; i < 54; i += blockDim.x) s_eln2[i] = lc.e_ln2[i];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = u[i];
+    const long long b = dbits(v);
+    const bool ok = b >= 0x3CA0000000000000ll && b < 0x3FF0000000000000ll;   // 2^-53 <= v < 1
+    out[i] = ok ? log_fixed(v, lc.c, s_eln2) : __longlong_as_double(0x7FF8000000000000ll);
+  }
+}
+
+cudaError_t launch_log_spec(const double* u, double* out, long long n, const LogConstants& lc, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  log_spec_kernel<<<(unsigned)blocks, 256, 0, st>>>(u, out, n, lc);
   return cudaGetLastError();
 }
 

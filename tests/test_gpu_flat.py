@@ -360,3 +360,23 @@ def test_checkpoint_argument_rules():
     a.resume = 1
     with pytest.raises(capi.CwcError, match="checkpoint"):
         capi.cwc_simulate(cm.handle, a, 0)
+
+
+def test_extreme_rate_spreads_bit_exact():
+    """Rates from the smallest subnormal to 1e20 in one network: propensity
+    sums with subnormal and huge terms, near-empty subtrees in the descent
+    and an event cap (EVENT_LIMIT) all match the oracle bit for bit."""
+    b0 = W.flat8x12(R=16)
+    rng = np.random.default_rng(77)
+    choices = np.array([5e-324, 1e-310, 1e-300, 1e-20, 1.0, 3.7, 1e20])
+    rates = choices[rng.integers(0, len(choices), (3, b0.model.n_rules))]
+    for p in range(3):
+        if not np.any(rates[p] >= 1.0):
+            rates[p, 0] = 1.0
+    b = W.Batch(b0.model, rates, b0.init, b0.grid, b0.R, b0.seed, max_events=3000)
+    g = gpu_run(b, log_cap=64)
+    o = oracle.simulate(b, threads=8, log_cap=64)
+    assert_same(g, o)
+    valid = np.arange(64)[None, :] < np.minimum(o["events"], 64)[:, None]
+    assert np.array_equal(g["log_rule"][valid], o["log_rule"][valid])
+    assert np.any(o["status"] == oracle.ST_EVENT_LIMIT)
