@@ -204,7 +204,9 @@ enum {
  * (52-bit uniforms (k + 1/2) 2^-52); a0 is the 32-lane blocked FP64 tree
  * sum of a_j = k_j * H_j (H_j the int64 number of reactant combinations
  * summed over the rule's contexts); tau = -log(u_tau) / a0 with a fixed
- * atanh-series logarithm; grid points before t + tau record the current
+ * logarithm evaluated in integer fixed point (the Mercator series near 1,
+ * else a 64-entry table of ln(1 + j/64) and the Mercator series of the
+ * remainder, rounded once to nearest); grid points before t + tau record the current
  * term; an event past T is discarded; rule j is chosen by guarded tree
  * descent of u_sel * a0; its context by the integer draw
  * floor(W * H_j / 2^64), W from counter (n, 1, r, p); then the rewrite.
@@ -335,8 +337,8 @@ cwc_status cwc_autotune(const cwc_model* model, const cwc_sim_args* args, int64_
                         int32_t* best_layout, int32_t* best_block_threads, double* best_ms, int32_t* best_lanes);
 
 /*
- * The fixed logarithm of the time step (the atanh series described above,
- * every operation rounded to nearest, no fused multiply-add) evaluated on the
+ * The fixed logarithm of the time step (the integer fixed-point evaluation
+ * described above, one rounding to nearest at the end) evaluated on the
  * device for n values: out[i] = log_spec(u[i]).  For checking the kernels'
  * logarithm against a CPU implementation bit for bit.  u and out are device
  * arrays of n doubles (caller-owned); inputs outside [2^-53, 1), the range of

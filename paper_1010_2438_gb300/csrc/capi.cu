@@ -69,12 +69,31 @@ cwc_status cuda_fail(cudaError_t e, const char* what) {
   return fail(CWC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Constants of the time step's logarithm: floor(2^63 / n); ln 2 in Q120 as
+// the truncated sum of floor(2^(120-k) / k), k = 1..120 (ln 2 = sum over k
+// of 1 / (k 2^k)); per prefix j, ceil(2^69 / (64 + j)) and ln(1 + j/64) in
+// Q64 from 2 atanh(s), s = j / (128 + j): s floored in Q64, the series
+// 1 + s^2/3 + ... + s^38/39 by Horner in Q63, then 2 s P floored to Q64.
 LogConstants make_log_constants() {
+  typedef unsigned __int128 u128;
   LogConstants lc;
   std::memset(&lc, 0, sizeof(lc));
-  for (int k = 3; k <= 21; k += 2) lc.c[k] = 1.0 / (double)k;
-  const double LN2 = 0.6931471805599453;  // the double nearest ln 2
-  for (int e = -53; e <= 0; ++e) lc.e_ln2[e + 53] = (double)e * LN2;
+  const u128 one = 1;
+  for (int n = 1; n < 40; ++n) lc.cq[n] = (unsigned long long)((one << 63) / (u128)n);
+  u128 ln2 = 0;
+  for (int k = 1; k <= 120; ++k) ln2 += (one << (120 - k)) / (u128)k;
+  lc.ln2_lo = (unsigned long long)ln2;
+  lc.ln2_hi = (unsigned long long)(ln2 >> 64);
+  auto hi64 = [](unsigned long long a, unsigned long long b) { return (unsigned long long)(((u128)a * b) >> 64); };
+  for (int j = 0; j < 64; ++j) {
+    lc.rj[j] = (unsigned long long)(((one << 69) + (u128)(63 + j)) / (u128)(64 + j));
+    const unsigned long long s = (unsigned long long)(((u128)j << 64) / (u128)(128 + j));
+    const unsigned long long z = hi64(s, s);
+    unsigned long long p = lc.cq[39];
+    for (int k = 37; k >= 3; k -= 2) p = lc.cq[k] + hi64(p, z);
+    p = (1ull << 63) + hi64(p, z);
+    lc.tj[j] = (unsigned long long)(((u128)s * p) >> 62);
+  }
   return lc;
 }
 

@@ -105,7 +105,7 @@ __device__ __forceinline__ long long cwc_grab_next(WorkspaceHeader* ws) {
 
 __host__ __device__ inline int cwc_table_bytes(int M, int n_deps) {
   int words = M * CWC_RULE_WORDS + n_deps;
-  return ((words * 4 + 15) / 16) * 16 + 54 * 8;
+  return ((words * 4 + 15) / 16) * 16 + 128 * 8;   // then the logarithm's 64 + 64 table words
 }
 
 // shared-memory bytes of one trajectory
@@ -132,7 +132,6 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   int32_t* s_rules = reinterpret_cast<int32_t*>(smem);
   int32_t* s_deps = s_rules + M * CWC_RULE_WORDS;
   const int tbl_words = M * CWC_RULE_WORDS + prm.n_deps;
-  double* s_eln2 = reinterpret_cast<double*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
   double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
   double* leaf = dbase + ts;                                      // [32][NT]
   double* node = dbase + 32 * NT + ts;                            // [31][NT]
@@ -142,8 +141,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
 #define NODE(i) node[(i) * NT]
 #define HV(i) Hs[(i) * NT]
 
+  unsigned long long* s_rj = reinterpret_cast<unsigned long long*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
+  unsigned long long* s_tj = s_rj + 64;
   for (int i = tid; i < tbl_words; i += T) s_rules[i] = prm.rules[i];
-  for (int i = tid; i < 54; i += T) s_eln2[i] = lc.e_ln2[i];
+  for (int i = tid; i < 64; i += T) {
+    s_rj[i] = lc.rj[i];
+    s_tj[i] = lc.tj[i];
+  }
   bool bad_grid = false;
   for (int g = tid; g < G; g += T) {
     const double v = prm.grid[g];
@@ -750,7 +754,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const uint4 w = philox4x32_10(make_uint4(n, 0u, rr, (uint32_t)p), prm.key0, prm.key1);
     const double u_tau = uniform52(w.x, w.y);
     const double u_sel = uniform52(w.z, w.w);
-    const double tau = __ddiv_rn(-log_fixed(u_tau, lc.c, s_eln2), a0);
+    const double tau = __ddiv_rn(-log_spec_q(u_tau, lc, s_rj, s_tj), a0);
     const double tn = __dadd_rn(t, tau);
     const long long tnb = dbits(tn);
     while (gi < G && gbits < tnb) {

@@ -21,7 +21,7 @@
 // clock per SM) has long latency, and hiding it needs resident warps.
 //
 // Per event the thread: draws Philox(n, 0, r, p); computes tau with the
-// fixed FP64 logarithm and one IEEE division; records grid points passed;
+// fixed integer logarithm and one IEEE division; records grid points passed;
 // descends the tree (integer compares of non-negative doubles, one FP64
 // subtraction per level); applies the stoichiometry change; rebuilds only the
 // leaves holding a rule whose propensity reads a changed species (Gibson-
@@ -47,12 +47,12 @@ __device__ __forceinline__ long long grab_next(WorkspaceHeader* ws) {
   return (long long)(base + (unsigned long long)__popc(mask & ((1u << lane) - 1u)));
 }
 
-// Shared-memory table region: rules, dependents, e*ln2 table (doubles last,
-// 16-byte aligned).  Must match on host and device.
+// Shared-memory table region: rules, dependents, reactant descriptors, then
+// (16-byte aligned) the logarithm's 64 + 64 table words.  Must match on host
+// and device.
 __host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
   int words = M * RULE_WORDS + n_deps + M;
-  int bytes = ((words * 4 + 15) / 16) * 16;
-  return bytes + 54 * 8;
+  return ((words * 4 + 15) / 16) * 16 + 128 * 8;
 }
 
 __host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   int32_t* s_deps = s_rules + M * RULE_WORDS;
   const uint32_t* s_desc = reinterpret_cast<const uint32_t*>(s_deps + prm.n_deps);
   const int tbl_words = M * RULE_WORDS + prm.n_deps + M;
-  double* s_eln2 = reinterpret_cast<double*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
   // Per-thread arrays [index][T]: each pointer below already points at this
   // thread's column, so element i of the array is ptr[i * T].
   double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
@@ -93,8 +92,13 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
 #define NODE(i) node[(i) * T]
 #define CNT(s) cnt[(s) * T]
 
+  unsigned long long* s_rj = reinterpret_cast<unsigned long long*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
+  unsigned long long* s_tj = s_rj + 64;
   for (int i = tid; i < tbl_words; i += T) s_rules[i] = prm.rules[i];   // rules then deps, contiguous
-  for (int i = tid; i < 54; i += T) s_eln2[i] = lc.e_ln2[i];
+  for (int i = tid; i < 64; i += T) {
+    s_rj[i] = lc.rj[i];
+    s_tj[i] = lc.tj[i];
+  }
   // grid check, once per block: finite, grid[0] >= 0, strictly increasing
   bool bad_grid = false;
   for (int g = tid; g < G; g += T) {
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
     const uint4 w = philox4x32_10(make_uint4(n, 0u, (uint32_t)r + prm.r_offset, (uint32_t)p), prm.key0, prm.key1);
     const double u_tau = uniform52(w.x, w.y);
     const double u_sel = uniform52(w.z, w.w);
-    const double tau = __ddiv_rn(-log_fixed(u_tau, lc.c, s_eln2), a0);
+    const double tau = __ddiv_rn(-log_spec_q(u_tau, lc, s_rj, s_tj), a0);
     const double tn = __dadd_rn(t, tau);
     const long long tnb = dbits(tn);
     while (gi < G && gbits < tnb) {

@@ -93,14 +93,17 @@ cudaError_t launch_means(const unsigned long long* sums, double* means, long lon
 // uniforms, give NaN.
 __global__ void log_spec_kernel(const double* __restrict__ u, double* __restrict__ out, long long n,
                                 const __grid_constant__ LogConstants lc) {
-  __shared__ double s_eln2[54];
-  for (int i = threadIdx.x; i < 54; i += blockDim.x) s_eln2[i] = lc.e_ln2[i];
+  __shared__ unsigned long long s_rj[64], s_tj[64];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    s_rj[i] = lc.rj[i];
+    s_tj[i] = lc.tj[i];
+  }
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = u[i];
     const long long b = dbits(v);
     const bool ok = b >= 0x3CA0000000000000ll && b < 0x3FF0000000000000ll;   // 2^-53 <= v < 1
-    out[i] = ok ? log_fixed(v, lc.c, s_eln2) : __longlong_as_double(0x7FF8000000000000ll);
+    out[i] = ok ? log_spec_q(v, lc, s_rj, s_tj) : __longlong_as_double(0x7FF8000000000000ll);
   }
 }
 

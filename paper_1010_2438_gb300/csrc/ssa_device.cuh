@@ -1,6 +1,6 @@
 // Device primitives of the direct-method step (Sec. 2.2): counter-based
-// random words, the exact 52-bit uniform, the fixed FP64 logarithm for
-// tau = -ln(u)/a0, and the FNV-1a event hash.
+// random words, the exact 52-bit uniform, the fixed logarithm for
+// tau = -ln(u)/a0 (integer arithmetic), and the FNV-1a event hash.
 //
 // On GB300 the FP64 pipe retires about 1.6 lane-operations per clock per SM
 // (~1/70 of FP32), so everything here that can be done exactly with integer
@@ -49,40 +49,80 @@ __device__ __forceinline__ double uniform52(uint32_t wa, uint32_t wb) {
 // integer order equals the numeric order.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
-// Coefficients of the logarithm: c[k] = 1/k for odd k = 3..21 (IEEE-divided
-// on the host), and e*ln2 rounded to nearest for e = -53..0.
+// Constants of the logarithm, filled on the host: cq[n] = floor(2^63 / n);
+// ln 2 in Q120 as the truncated series sum_{k=1..120} floor(2^(120-k) / k)
+// (ln 2 = sum 1/(k 2^k)), in two words; per 6-bit significand prefix j,
+// rj[j] = ceil(2^69 / (64 + j)) (1/c_j in Q63, c_j = 1 + j/64) and tj[j] =
+// ln c_j in Q64 (atanh series).  Kernels keep rj / tj in shared memory (they
+// are indexed per lane).
 struct LogConstants {
-  double c[22];
-  double e_ln2[54];   // index e + 53
+  unsigned long long cq[40];
+  unsigned long long ln2_lo, ln2_hi;
+  unsigned long long rj[64];
+  unsigned long long tj[64];
 };
 
-// ln(u) for u in (0,1):  u = f 2^E with f in [1,2); if f >= sqrt2 (the double
-// nearest) then m = f/2, e = E + 1, else m = f, e = E; s = (m-1)/(m+1),
-// z = s^2, p = c21 z + c19 ... + c3 by Horner, r = 2 (s + s (z p)),
-// ln(u) = e ln2 + r.  ln m = 2 atanh(s) (Abramowitz & Stegun 4.1.27); the
-// truncation after s^21/21 is below 1e-18 relative for |s| <= 0.1716.
-// c: the coefficients (uniform index); eln2: the e*ln2 table (per-lane index,
-// kept in shared memory).
-__device__ __forceinline__ double log_fixed(double u, const double* c, const double* eln2) {
-  const long long SQRT2_BITS = 0x3FF6A09E667F3BCDll;                 // 1.4142135623730951
-  const long long ub = dbits(u);
-  int e = (int)((ub >> 52) & 0x7ff) - 1023;
-  long long fb = (ub & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll;  // f in [1,2)
-  if (fb >= SQRT2_BITS) {
-    fb -= (1ll << 52);                                               // f * 0.5, exact
-    e += 1;
+// (x * 2^scale) rounded to the nearest double, ties to even, assembled from
+// the integer's bits; x > 0 and the result normal.
+__device__ __forceinline__ double round_q128(unsigned __int128 x, int scale) {
+  const unsigned long long hi = (unsigned long long)(x >> 64), lo = (unsigned long long)x;
+  const int lead = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long mant;
+  int e = lead;
+  if (lead <= 52) {
+    mant = lo << (52 - lead);
+  } else {
+    const int sh = lead - 52;
+    mant = (unsigned long long)(x >> sh);
+    const unsigned __int128 rem = x & ((((unsigned __int128)1) << sh) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) mant += 1ull;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      e += 1;
+    }
   }
-  const double m = __longlong_as_double(fb);
-  const double s = __ddiv_rn(__dadd_rn(m, -1.0), __dadd_rn(m, 1.0));
-  const double z = __dmul_rn(s, s);
-  double p = c[21];
+  const unsigned long long bexp = (unsigned long long)(e + scale + 1023);
+  return __longlong_as_double((long long)((bexp << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
+}
+
+// ln(u) for u in [2^-53, 1), in exact integer arithmetic with one rounding
+// at the end.  u = F 2^(E-52), F the 53-bit significand, f = F 2^-52.
+//  * Near one (E = -1, D = 2^53 - F < 2^46, d = 1 - u < 2^-7): -ln u =
+//    d (1 + d/2 + ... + d^8/9) (Mercator series, Abramowitz & Stegun
+//    4.1.24), Horner with q in Q63 and d in Q64; -ln u = D q 2^-116.
+//  * Otherwise, j = the top 6 fraction bits of f: -ln u = -E ln2 - ln c_j -
+//    ln(1 + y), y = f rj[j] - 1 in [0, 2^-6) in Q64, ln(1 + y) = y (1 - y/2
+//    + ... + y^10/11) by Horner in Q63, the sum in Q120.
+// Every product is floored to the stated width.  No division, no FP64
+// instruction.  Error < 0.55 ulp.
+__device__ __forceinline__ double log_spec_q(double u, const LogConstants& lc, const unsigned long long* s_rj,
+                                             const unsigned long long* s_tj) {
+  typedef unsigned __int128 u128;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+  const int E = (int)((b >> 52) & 0x7ff) - 1023;
+  const unsigned long long F = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long D = (1ull << 53) - F;
+  double y;
+  if (E == -1 && D < (1ull << 46)) {
+    const unsigned long long dq = D << 11;
+    unsigned long long q = lc.cq[9];
 #pragma unroll
-  for (int k = 19; k >= 3; k -= 2) p = __dadd_rn(__dmul_rn(p, z), c[k]);
-  const double inner = __dadd_rn(s, __dmul_rn(s, __dmul_rn(z, p)));
-  // 2 * inner, exact: inner is 0 or a normal number far from the top of the range
-  const long long ib = dbits(inner);
-  const double r = (ib & 0x7FFFFFFFFFFFFFFFll) == 0 ? inner : __longlong_as_double(ib + (1ll << 52));
-  return __dadd_rn(eln2[e + 53], r);
+    for (int n = 8; n >= 1; --n) q = lc.cq[n] + __umul64hi(q, dq);
+    y = round_q128((u128)D * q, -116);
+  } else {
+    const int j = (int)((F >> 46) & 63);
+    const u128 fr = (u128)(F << 11) * s_rj[j];                       // f rj in Q126
+    const unsigned long long yq = (unsigned long long)(fr >> 62);    // f rj - 1 in Q64 (the 2^64 drops)
+    unsigned long long p = lc.cq[11];
+#pragma unroll
+    for (int k = 10; k >= 2; --k) p = lc.cq[k] - __umul64hi(p, yq);
+    p = (1ull << 63) - __umul64hi(p, yq);
+    const u128 l1 = ((u128)yq * p) >> 7;
+    const u128 ln2 = (((u128)lc.ln2_hi) << 64) | lc.ln2_lo;
+    y = round_q128((u128)(unsigned long long)(-E) * ln2 - (((u128)s_tj[j]) << 56) - l1, -120);
+  }
+  return __longlong_as_double(__double_as_longlong(y) | (long long)0x8000000000000000ull);
 }
 
 // FNV-1a 64-bit over the little-endian bytes of (uint32 rule, uint32 slot).
