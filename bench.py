@@ -156,15 +156,25 @@ def cpu_baseline(batch, threads: int, n_traj: int):
 # Other workloads of the path (one timed step each, after one warm-up)
 # ---------------------------------------------------------------------------
 
-def _timed(fn):
+CLOCK_LOG = {}
+
+
+def _timed(fn, name=None):
+    """One warm-up call, then one call timed with CUDA events; the SM clock is
+    sampled during the timed call and kept in CLOCK_LOG[name]."""
     import torch
     fn()
     torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if name else None
+    if sampler:
+        sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     out = fn()
     e1.record()
     torch.cuda.synchronize()
+    if sampler:
+        CLOCK_LOG[name] = sampler.stop()
     return out, e0.elapsed_time(e1) / 1e3
 
 
@@ -185,7 +195,7 @@ def measure_extras(dev):
         keep["o"] = api.simulate(cm, rates, init, grid, b.R, b.seed, states=True, out=keep.get("o"))
         return keep["o"]
 
-    out, sec = _timed(run_cwc)
+    out, sec = _timed(run_cwc, "cwc3x24")
     ev = int(out["events"].sum().item())
     extras["cwc3x24"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay, "block_threads": thr,
                          "lanes_per_trajectory": lanes,
@@ -198,7 +208,7 @@ def measure_extras(dev):
     rates, init, grid = api.device_inputs(b, dev)
     lay, thr, _, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=2000)
     g = api.GraphedSimulation(cm, rates, init, grid, b.R, b.seed, states=True)
-    out, sec = _timed(g.replay)
+    out, sec = _timed(g.replay, "sweep256x256")
     evp = out["events"].double().mean(dim=1)
     ev = int(out["events"].sum().item())
     extras["sweep256x256"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay,
@@ -218,7 +228,7 @@ def measure_extras(dev):
             keep["o"] = api.simulate(cm, rates, init, grid, b.R, b.seed, states=True, out=keep.get("o"))
             return keep["o"]
 
-        out, sec = _timed(run_lv)
+        out, sec = _timed(run_lv, "lotka_volterra_%d" % nsp)
         ev = int(out["events"].sum().item())
         lv[str(nsp)] = {"events_per_s": ev / sec, "events": ev, "seconds": sec}
         del keep, out
@@ -228,13 +238,17 @@ def measure_extras(dev):
     b = W.flat16x24()
     cm = api.CompiledModel(b.model)
     rates, init, grid = api.device_inputs(b, dev)
-    fwd, t_fwd = _timed(lambda: api.simulate(cm, rates, init, grid, b.R, b.seed, states=False, means=True, traj=True))
+    fwd, t_fwd = _timed(lambda: api.simulate(cm, rates, init, grid, b.R, b.seed, states=False, means=True, traj=True),
+                        "flat16x24_forward")
     ev = int(fwd["events"].sum().item())
     gm = torch.ones_like(fwd["means"])
-    _, t_bwd = _timed(lambda: api.sensitivity(cm, rates, init, grid, b.R, b.seed, fwd["means"], gm))
+    _, t_bwd = _timed(lambda: api.sensitivity(cm, rates, init, grid, b.R, b.seed, fwd["means"], gm),
+                      "flat16x24_backward")
     extras["flat16x24_sensitivity"] = {"forward_events_per_s": ev / t_fwd, "forward_s": t_fwd, "backward_s": t_bwd,
                                        "grad_over_fwd": t_bwd / t_fwd, "events": ev,
                                        "workload": "d E[X(g)]/d k for 24 rates, 131072 replicas, 100-point grid"}
+    # SM clock (median MHz) and throttle reasons seen during each timed call
+    extras["clocks"] = {k: {"sm_mhz": v.get("sm_mhz"), "reasons": v.get("reasons")} for k, v in CLOCK_LOG.items()}
     return extras
 
 
