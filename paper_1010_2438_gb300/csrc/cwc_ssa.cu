@@ -117,6 +117,50 @@ __host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, 
   return (w + 31) / 32 * 32;
 }
 
+// Sum of the counts of rule `rec` over the contexts in m (the child slots of
+// a parent-child rule count only under a parent of the rule's context label);
+// bit 63 of the result flags an int64 overflow of a count or of the sum.
+// Kept out of line for lane groups, which call it from four places: one
+// copy of the code instead of four keeps the kernel's hot loop in the
+// instruction cache (instruction-fetch stalls were the first stall reason;
+// +27 % events/s with 4 lanes per term).  One lane per term keeps the inline
+// form, which measured faster there.
+__device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restrict__ content,
+                                                        const int32_t* __restrict__ wrap,
+                                                        const int32_t* __restrict__ meta, int S,
+                                                        const int32_t* rec, unsigned long long m) {
+  const int kind = rec[CR_KIND];
+  const bool parent_child = !(kind == 0 || kind == 2);
+  const int nr = rec[CR_NREAC];
+  const int ctx = rec[CR_CTX];
+  bool of = false;
+  unsigned long long tot = 0ull;
+  while (m) {
+    const int c = __ffsll((long long)m) - 1;
+    m &= m - 1ull;
+    int x0c = c;
+    if (parent_child) {
+      const int qq = (meta[c] >> 8) - 1;
+      if ((meta[qq] & 0xff) != ctx) continue;
+      x0c = qq;
+    }
+    const int32_t* x0 = content + (size_t)x0c * S;
+    const int32_t* x1 = wrap + (size_t)c * S;
+    const int32_t* x2 = content + (size_t)c * S;
+    unsigned long long acc = 1ull;
+    for (int a = 0; a < nr; ++a) {
+      const int v = rec[CR_REAC + a];
+      const int row = (v >> 24) & 3;
+      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
+      acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
+    }
+    const unsigned long long s2 = tot + acc;
+    if (s2 < tot || (s2 >> 63) != 0ull) of = true;
+    tot = s2;
+  }
+  return of ? (tot | (1ull << 63)) : tot;
+}
+
 template <int kL, bool kQueue, bool kSens>
 __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ CwcParams prm,
                                                       const __grid_constant__ LogConstants lc) {
@@ -239,17 +283,22 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // sum of the counts of a rule over the contexts in m (ascending slots),
   // overflow-checked like a from-scratch H
   auto partial_h = [&](const int32_t* rec, unsigned long long m) -> unsigned long long {
-    unsigned long long tot = 0ull;
-    while (m) {
-      const int c = __ffsll((long long)m) - 1;
-      m &= m - 1ull;
-      if (!ctx_ok(rec, c)) continue;
-      const unsigned long long hc = count_at(rec, c);
-      const unsigned long long s2 = tot + hc;
-      if (s2 < tot || (s2 >> 63) != 0ull) ovf = true;
-      tot = s2;
+    if (kL == 1) {
+      unsigned long long tot = 0ull;
+      while (m) {
+        const int c = __ffsll((long long)m) - 1;
+        m &= m - 1ull;
+        if (!ctx_ok(rec, c)) continue;
+        const unsigned long long hc = count_at(rec, c);
+        const unsigned long long s2 = tot + hc;
+        if (s2 < tot || (s2 >> 63) != 0ull) ovf = true;
+        tot = s2;
+      }
+      return tot;
     }
-    return tot;
+    const unsigned long long r = cwc_count_sum(content, wrap, meta, S, rec, m);
+    if (r >> 63) ovf = true;
+    return r;
   };
   // H_i from scratch: sum over all its contexts
   auto total_h = [&](int i) -> unsigned long long {
@@ -697,7 +746,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         if (rm == 0ull) continue;
         const int c = r0 + gl;
         unsigned long long hc = 0ull;
-        if (((rm >> gl) & 1ull) && ctx_ok(rec, c)) hc = count_at(rec, c);
+        if ((rm >> gl) & 1ull) {
+          hc = cwc_count_sum(content, wrap, meta, S, rec, 1ull << c);
+          if (hc >> 63) ovf = true;
+          hc &= ~(1ull << 63);
+        }
         const unsigned long long incl = grp.incl_scan(hc);
         const unsigned nz = grp.ballot(hc != 0ull);
         const unsigned hit = grp.ballot(hc != 0ull && xc < base + incl);
