@@ -120,11 +120,7 @@ __host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, 
 // Sum of the counts of rule `rec` over the contexts in m (the child slots of
 // a parent-child rule count only under a parent of the rule's context label);
 // bit 63 of the result flags an int64 overflow of a count or of the sum.
-// Kept out of line for lane groups, which call it from four places: one
-// copy of the code instead of four keeps the kernel's hot loop in the
-// instruction cache (instruction-fetch stalls were the first stall reason;
-// +27 % events/s with 4 lanes per term).  One lane per term keeps the inline
-// form, which measured faster there.
+// Out of line for lane groups (see below).
 __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restrict__ content,
                                                         const int32_t* __restrict__ wrap,
                                                         const int32_t* __restrict__ meta, int S,
@@ -159,6 +155,88 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
     tot = s2;
   }
   return of ? (tot | (1ull << 63)) : tot;
+}
+
+// With lane groups a warp holds 8 or 4 terms on different paths and runs
+// those paths one after another, so its instruction footprint is the sum of
+// theirs; instruction fetch was the first stall reason.  The count sums, the
+// grid-point record and the rewrite check are therefore kept out of line for
+// lane groups (one copy each, shared by every path that calls them): 2.0e8 ->
+// 3.4e8 events/s with 4 lanes per term on 16,384 terms.  One lane per term
+// keeps them inline, which measured faster there; an out-of-line Philox or
+// rewrite measured slower.
+
+// Observables of one grid point: lane gl of a group writes o = gl, gl + step, ...
+__device__ __noinline__ void cwc_record_rows(const long long* tot, int32_t* dst, unsigned long long* sdst,
+                                            unsigned long long* qdst, int O, int gl, int step) {
+  for (int o = gl; o < O; o += step) {
+    const long long v = tot[o];
+    const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
+    if (dst) dst[o] = sv;
+    if (sdst) atomicAdd(sdst + o, (unsigned long long)(long long)sv);
+    if (qdst) add_square_u128(qdst + 2 * o, sv);
+  }
+}
+
+// Whether the rewrite of rule `rec` at context c fits (TS_OK), else its
+// status; reads only (the in-line version is apply_check in the kernel).
+__device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_t* wrap, const int32_t* meta,
+                                            unsigned long long alive, int S, int C, const int32_t* rec, int c) {
+  const unsigned long long* alive_p = &alive;
+  auto PARENT = [&](int cc) -> int { return (meta[cc] >> 8) - 1; };
+  auto fits_add = [](int32_t v, int d) -> bool {
+    const long long s = (long long)v + d;
+    return s >= 0 && s <= 0x7FFFFFFFll;
+  };
+    const int kind = rec[CR_KIND];
+    const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
+    if (kind == 0 || kind == 2) {
+      if (kind == 2) {
+        const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
+        if (freeslots == 0ull) return TS_CAPACITY;
+      }
+      const int32_t* x = content + (size_t)c * S;
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      return TS_OK;
+    }
+    const int qq = PARENT(c);
+    const int32_t* xp = content + (size_t)qq * S;
+    const int32_t* w = wrap + (size_t)c * S;
+    const int32_t* xc = content + (size_t)c * S;
+    if (kind == 1) {
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      for (int d = 0; d < nd1; ++d) {
+        const int v = rec[CR_D1 + d];
+        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      for (int d = 0; d < nd2; ++d) {
+        const int v = rec[CR_D2 + d];
+        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+      }
+      return TS_OK;
+    }
+    // DISSOLVE: the parent content gains (rhs0 - lhs0) + (wrap - lhs1) + (content - lhs2)
+    for (int s = 0; s < S; ++s) {
+      long long dv = (long long)w[s] + xc[s];
+      for (int d = 0; d < nd0; ++d) {
+        const int v = rec[CR_D0 + d];
+        if ((v & 0xffff) == s) dv += v >> 16;
+      }
+      const int nr = rec[CR_NREAC];
+      for (int a = 0; a < nr; ++a) {
+        const int v = rec[CR_REAC + a];
+        if (((v >> 24) & 3) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
+      }
+      const long long nv = (long long)xp[s] + dv;
+      if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
+    }
+    return TS_OK;
 }
 
 template <int kL, bool kQueue, bool kSens>
@@ -335,12 +413,16 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     int32_t* dst = prm.states != nullptr ? prm.states + ((size_t)q * G + g) * O : nullptr;
     unsigned long long* sdst = prm.sums != nullptr ? prm.sums + ((size_t)p * G + g) * O : nullptr;
     unsigned long long* qdst = prm.sumsq != nullptr ? prm.sumsq + ((size_t)p * G + g) * O * 2 : nullptr;
-    for (int o = gl; o < O; o += kL) {
-      const long long v = tot[o];
-      const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
-      if (dst) dst[o] = sv;
-      if (sdst) atomicAdd(sdst + o, (unsigned long long)(long long)sv);
-      if (qdst) add_square_u128(qdst + 2 * o, sv);
+    if (kL > 1) {
+      cwc_record_rows(tot, dst, sdst, qdst, O, gl, kL);
+    } else {
+      for (int o = gl; o < O; o += kL) {
+        const long long v = tot[o];
+        const int32_t sv = v > 0x7FFFFFFFll ? 0x7FFFFFFF : (int32_t)v;
+        if (dst) dst[o] = sv;
+        if (sdst) atomicAdd(sdst + o, (unsigned long long)(long long)sv);
+        if (qdst) add_square_u128(qdst + 2 * o, sv);
+      }
     }
     if (kSens) {
       const double* gm = prm.grad_means + ((size_t)p * G + g) * O;
@@ -873,7 +955,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     // and the free slots (one of which CREATE fills).  Each dependent rule
     // drops the old counts of its touched contexts and adds the new ones; a
     // rule whose contexts all lie in `touched` is summed afresh.
-    const int ast = apply_check(rec, ctx);
+    const int ast = kL > 1 ? cwc_apply_check(content, wrap, meta, *alive_p, S, C, rec, ctx) : apply_check(rec, ctx);
     if (ast != TS_OK) {
       status = ast;
       return 1;
