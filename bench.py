@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "flat32x64"
 WORKLOAD_DESC = ("flat mass-action network, 32 species, 64 reactions (8 inflow/outflow pairs, 32 conversions, "
                  "16 bimolecular), 65536 replicas x ~1e5 events, 1000-point grid, int32 states, FP64 propensities/time")
+CWC_DESC = ("compartmentalised CWC, 3 labels below the top, 24 species, 48 rules (transport, wrap binding, create, "
+            "dissolve), <=64 compartments per term, 16384 replicas x ~1e4 events, 500-point grid, 172 observables")
 METRIC = "SSA events/sec"
 UNIT = "events/s"
 KERNEL_SOURCES = ["paper_1010_2438_gb300/csrc/flat_ssa.cu", "paper_1010_2438_gb300/csrc/ssa_device.cuh",
@@ -439,7 +441,7 @@ def main():
                                                     or args.workload != WORKLOAD)
                        else "%s (profiling case: R=%d, G=%d, horizon x%g)" % (args.workload, R, batch.G,
                                                                                args.horizon_scale),
-                       "description": WORKLOAD_DESC, "P": batch.P, "R": R,
+                       "description": WORKLOAD_DESC if args.workload == WORKLOAD else CWC_DESC, "P": batch.P, "R": R,
                            "G": batch.G, "S": batch.model.n_species, "M": batch.model.n_rules,
                            "events_per_step_per_gpu": events, "statuses": statuses,
                            "layout": ["auto(queue)", "static", "queue"][args.layout],
