@@ -10,24 +10,28 @@
 //                        l is a_l itself (l >= M: +0); with B > 1 it is the
 //                        block sum and the a_j are recomputed from the counts
 //                        when needed instead of being stored
-//   node[31][T]  double  internal tree nodes, root = node[30] = a0
+//   node[16][T]  double  level-1 tree nodes (children: leaves 2n, 2n+1)
 //   cnt[S][T]    int32   species counts
-// plus, for the score replay, H_i as doubles [M][T].  The replay's integrals,
+// and, in registers, the 15 upper nodes (levels 2-5, root = a0), which the
+// descent selects among without a shared-memory round trip.  For the score
+// replay H_i as doubles [M][T] joins shared memory.  The replay's integrals,
 // their times, the firing counts and the partials, touched a few at a time
 // per event, live in global memory per trajectory, so that the replay keeps
 // almost the forward pass's residency.
-// Keeping only the tree and the counts (504 + 4S bytes per trajectory) is
-// what lets 8-10 warps share an SM: GB300's FP64 pipe (~1.6 lane-ops per
-// clock per SM) has long latency, and hiding it needs resident warps.
+// Keeping only the leaves, the level-1 nodes and the counts (384 + 4S bytes
+// per trajectory) is what lets 12 warps share an SM: GB300's FP64 pipe
+// (~1.6 lane-ops per clock per SM) has long latency, and hiding it needs
+// resident warps.
 //
 // Per event the thread: draws Philox(n, 0, r, p); computes tau with the
 // fixed integer logarithm and one IEEE division; records grid points passed;
 // descends the tree (integer compares of non-negative doubles, one FP64
 // subtraction per level); applies the stoichiometry change; rebuilds only the
 // leaves holding a rule whose propensity reads a changed species (Gibson-
-// Bruck dependency graph) and the internal nodes above them.  a0 is always
-// the tree root, never a running sum, so values equal a full rebuild bit for
-// bit.
+// Bruck dependency graph) and the level-1 nodes above them, then the 15
+// register nodes (a warp's lanes fire different rules, so between them they
+// dirty nearly every upper node anyway).  a0 is always the tree root, never
+// a running sum, so values equal a full rebuild bit for bit.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -56,13 +60,13 @@ __host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
 }
 
 __host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
-  int doubles = 32 + TREE_NODES + (sens ? M : 0);
+  int doubles = 32 + 16 + (sens ? M : 0);
   int ints = S;
   return doubles * 8 + ints * 4;
 }
 
 template <bool kQueue, bool kSens>
-__global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ FlatParams prm,
+__global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatParams prm,
                                                        const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
@@ -76,10 +80,10 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   // Per-thread arrays [index][T]: each pointer below already points at this
   // thread's column, so element i of the array is ptr[i * T].
   double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
-  const int n_dbl_rows = 32 + TREE_NODES + (kSens ? M : 0);
+  const int n_dbl_rows = 32 + 16 + (kSens ? M : 0);
   double* leaf = dbase + tid;                                   // [32][T]
-  double* node = dbase + 32 * T + tid;                          // [31][T]
-  double* Hd = dbase + (32 + TREE_NODES) * T + tid;             // score replay only: [M][T]
+  double* node = dbase + 32 * T + tid;                          // [16][T] level-1 nodes
+  double* Hd = dbase + (32 + 16) * T + tid;                     // score replay only: [M][T]
   // score replay, per trajectory in global memory (set by start()):
   double* Iac = nullptr;    // [M] int_0^tl_i H_i dt
   double* tl = nullptr;     // [M]
@@ -142,6 +146,27 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
   const long long Q = prm.Q;
   const long long qstride = (long long)gridDim.x * T;
   bool first = true;
+  // upper tree nodes: level 2 (nodes 16..23), level 3 (24..27), level 4 (28,
+  // 29) and the root (30) = a0.  Indexed with constants only, so they stay in
+  // registers.
+  double u2[8], u3[4], u4[2], root = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) u2[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u3[k] = 0.0;
+  u4[0] = u4[1] = 0.0;
+
+  // levels 2-5 from the level-1 nodes, each node the sum of its left and
+  // right child
+  auto rebuild_upper = [&]() {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u2[k] = __dadd_rn(NODE(2 * k), NODE(2 * k + 1));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u3[k] = __dadd_rn(u2[2 * k], u2[2 * k + 1]);
+    u4[0] = __dadd_rn(u3[0], u3[1]);
+    u4[1] = __dadd_rn(u3[2], u3[3]);
+    root = __dadd_rn(u4[0], u4[1]);
+  };
 
   // observables of the current term at grid point g
   auto record = [&](int g) {
@@ -290,11 +315,8 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       }
     }
     for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
-    for (int nd = 0; nd < TREE_NODES; ++nd) {
-      const double a = nd < 16 ? LEAF(2 * nd) : NODE(2 * nd - 32);
-      const double b = nd < 16 ? LEAF(2 * nd + 1) : NODE(2 * nd - 31);
-      NODE(nd) = __dadd_rn(a, b);
-    }
+    for (int nd = 0; nd < 16; ++nd) NODE(nd) = __dadd_rn(LEAF(2 * nd), LEAF(2 * nd + 1));
+    rebuild_upper();
     return 0;
   };
 
@@ -311,7 +333,7 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       status = TS_EVENT_LIMIT;
       return 1;
     }
-    const double a0 = NODE(TREE_ROOT);
+    const double a0 = root;
     const long long a0b = dbits(a0);
     if (a0b == 0) {
       status = TS_ABSORBED;
@@ -344,27 +366,25 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
       status = TS_OK;
       return 2;
     }
-    // rule selection: guarded descent of x = u_sel * a0
+    // rule selection: guarded descent of x = u_sel * a0; k is the index of
+    // the chosen node within its level
     double x = __dmul_rn(u_sel, a0);
-    int nd = TREE_ROOT;
-#pragma unroll
-    for (int lvl = 5; lvl >= 2; --lvl) {
-      const double L = NODE(2 * nd - 32);
-      const double Rv = NODE(2 * nd - 31);
+    int k;
+    auto descend = [&](double L, double Rv) -> int {
       const bool left = dbits(x) < dbits(L) || dbits(Rv) == 0;
       const double xr = __dadd_rn(x, -L);
       x = left ? x : xr;
-      nd = left ? 2 * nd - 32 : 2 * nd - 31;
-    }
-    int l;
+      return left ? 0 : 1;
+    };
+    k = descend(u4[0], u4[1]);                                       // root -> node 28 + k
+    k = 2 * k + descend(k ? u3[2] : u3[0], k ? u3[3] : u3[1]);       // -> node 24 + k
     {
-      const double L = LEAF(2 * nd);
-      const double Rv = LEAF(2 * nd + 1);
-      const bool left = dbits(x) < dbits(L) || dbits(Rv) == 0;
-      const double xr = __dadd_rn(x, -L);
-      x = left ? x : xr;
-      l = left ? 2 * nd : 2 * nd + 1;
+      const double L = (k & 2) ? ((k & 1) ? u2[6] : u2[4]) : ((k & 1) ? u2[2] : u2[0]);
+      const double Rv = (k & 2) ? ((k & 1) ? u2[7] : u2[5]) : ((k & 1) ? u2[3] : u2[1]);
+      k = 2 * k + descend(L, Rv);                                    // -> node 16 + k
     }
+    k = 2 * k + descend(NODE(2 * k), NODE(2 * k + 1));               // -> level-1 node k
+    const int l = 2 * k + descend(LEAF(2 * k), LEAF(2 * k + 1));     // -> leaf l
     int j;
     if (B == 1) {
       j = l;
@@ -431,14 +451,13 @@ __global__ void __launch_bounds__(256) flat_ssa_kernel(const __grid_constant__ F
         LEAF(ll) = leaf_sum(ll);
       }
     }
-    unsigned nm = (unsigned)rec[R_NODEMASK];
+    unsigned nm = (unsigned)rec[R_NODEMASK] & 0xFFFFu;    // level-1 nodes above the dirty leaves
     while (nm) {
-      const int k = __ffs(nm) - 1;
+      const int kk = __ffs(nm) - 1;
       nm &= nm - 1u;
-      const double a = k < 16 ? LEAF(2 * k) : NODE(2 * k - 32);
-      const double b = k < 16 ? LEAF(2 * k + 1) : NODE(2 * k - 31);
-      NODE(k) = __dadd_rn(a, b);
+      NODE(kk) = __dadd_rn(LEAF(2 * kk), LEAF(2 * kk + 1));
     }
+    rebuild_upper();
     if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
       const size_t at = (size_t)q * prm.log_cap + n;
       prm.log_rule[at] = j;
