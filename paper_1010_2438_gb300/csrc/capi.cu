@@ -47,7 +47,7 @@ struct cwc_model {
   // flat compilation
   int B = 1, n_deps = 0;
   int checked_counts = 0;
-  int32_t* d_tables = nullptr;  // [M][RULE_WORDS] followed by [n_deps]
+  int32_t* d_tables = nullptr;  // [M][RULE_WORDS], [n_deps], [M] descriptors, log tables (cwc_internal.h)
   std::vector<int32_t> h_tables;
   // compartmentalised compilation
   int O = 0;
@@ -549,6 +549,19 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       kind = 3u;
     }
     tb.push_back((int32_t)(kind | (s0 << 2) | (s1 << 16)));
+  }
+  // the logarithm's per-prefix tables (u64, low word first), 16-byte aligned
+  {
+    while (tb.size() % 4) tb.push_back(0);
+    const LogConstants lct = make_log_constants();
+    for (int i = 0; i < 64; ++i) {
+      tb.push_back((int32_t)(uint32_t)lct.rj[i]);
+      tb.push_back((int32_t)(uint32_t)(lct.rj[i] >> 32));
+    }
+    for (int i = 0; i < 64; ++i) {
+      tb.push_back((int32_t)(uint32_t)lct.tj[i]);
+      tb.push_back((int32_t)(uint32_t)(lct.tj[i] >> 32));
+    }
   }
   // one trajectory's state must fit: 32 threads per block at least
   {

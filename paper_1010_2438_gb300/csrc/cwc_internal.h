@@ -22,7 +22,9 @@ constexpr int RULE_WORDS = 20;
 // After the dependents, a compiled flat model has one reactant descriptor per
 // rule (order <= 2 models): kind (0: order 0, 1: n0, 2: C(n0, 2), 3: n0 * n1)
 // in bits 0-1, species 0 in bits 2-15, species 1 in bits 16-29 (species 0
-// again when the rule has a single reactant species).
+// again when the rule has a single reactant species).  Then, padded to a
+// 16-byte boundary, the logarithm's 64 rj and 64 tj words (u64 each, low
+// word first; see LogConstants), which the kernel indexes per lane.
 constexpr int MAX_REAC = 4;
 constexpr int MAX_DELTA = 8;
 constexpr int R_NREAC = 0, R_REAC = 1, R_NDELTA = 5, R_DELTA = 6, R_DEPOFF = 14, R_DEPCNT = 15,

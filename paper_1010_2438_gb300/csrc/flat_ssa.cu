@@ -2,10 +2,11 @@
 // (Sec. 2.2) run by one thread per trajectory over replicas x sweep points
 // (Sec. 5.2).
 //
-// Layout.  A block of T threads holds, in shared memory, the compiled rule
-// tables (shared by the block) and per-thread arrays stored [index][thread],
-// so that every thread reading "its" element i touches bank (2*tid) mod 32
-// whatever i is: data-dependent indices never conflict.
+// Layout.  The compiled rule tables stay in global memory, read through L1
+// (a few KB shared by every block, always resident there).  Shared memory
+// holds only per-thread arrays stored [index][thread], so that every thread
+// reading "its" element i touches bank (2*tid) mod 32 whatever i is: data-
+// dependent indices never conflict.
 //   leaf[32][T]  double  leaves of the 32-lane blocked tree.  With B = 1 leaf
 //                        l is a_l itself (l >= M: +0); with B > 1 it is the
 //                        block sum and the a_j are recomputed from the counts
@@ -19,9 +20,9 @@
 // per event, live in global memory per trajectory, so that the replay keeps
 // almost the forward pass's residency.
 // Keeping only the leaves, the level-1 nodes and the counts (384 + 4S bytes
-// per trajectory) is what lets 12 warps share an SM: GB300's FP64 pipe
-// (~1.6 lane-ops per clock per SM) has long latency, and hiding it needs
-// resident warps.
+// per trajectory) in shared memory, and no tables, is what lets 14 warps
+// share an SM at S = 32: GB300's FP64 pipe (~1.6 lane-ops per clock per SM)
+// has long latency, and hiding it needs resident warps.
 //
 // Per event the thread: draws Philox(n, 0, r, p); computes tau with the
 // fixed integer logarithm and one IEEE division; records grid points passed;
@@ -51,12 +52,14 @@ __device__ __forceinline__ long long grab_next(WorkspaceHeader* ws) {
   return (long long)(base + (unsigned long long)__popc(mask & ((1u << lane) - 1u)));
 }
 
-// Shared-memory table region: rules, dependents, reactant descriptors, then
-// (16-byte aligned) the logarithm's 64 + 64 table words.  Must match on host
-// and device.
+// Shared memory set aside for tables: none.  The kernel reads the rules, the
+// dependents, the reactant descriptors and the logarithm's 64 + 64 table
+// words from the model's device table (layout in cwc_internal.h) through
+// L1; in shared memory they cost the block two warps of residency at S = 32.
 __host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
-  int words = M * RULE_WORDS + n_deps + M;
-  return ((words * 4 + 15) / 16) * 16 + 128 * 8;
+  (void)M;
+  (void)n_deps;
+  return 0;
 }
 
 __host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
@@ -73,9 +76,11 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   const int tid = threadIdx.x;
   const int S = prm.S, M = prm.M, B = prm.B, G = prm.G;
 
-  int32_t* s_rules = reinterpret_cast<int32_t*>(smem);
-  int32_t* s_deps = s_rules + M * RULE_WORDS;
-  const uint32_t* s_desc = reinterpret_cast<const uint32_t*>(s_deps + prm.n_deps);
+  // model tables in global memory: rules, dependents, reactant descriptors,
+  // then (16-byte aligned) the logarithm's rj and tj words
+  const int32_t* __restrict__ g_rules = prm.rules;
+  const int32_t* __restrict__ g_deps = g_rules + M * RULE_WORDS;
+  const uint32_t* __restrict__ g_desc = reinterpret_cast<const uint32_t*>(g_deps + prm.n_deps);
   const int tbl_words = M * RULE_WORDS + prm.n_deps + M;
   // Per-thread arrays [index][T]: each pointer below already points at this
   // thread's column, so element i of the array is ptr[i * T].
@@ -96,13 +101,9 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
 #define NODE(i) node[(i) * T]
 #define CNT(s) cnt[(s) * T]
 
-  unsigned long long* s_rj = reinterpret_cast<unsigned long long*>(smem + ((tbl_words * 4 + 15) / 16) * 16);
-  unsigned long long* s_tj = s_rj + 64;
-  for (int i = tid; i < tbl_words; i += T) s_rules[i] = prm.rules[i];   // rules then deps, contiguous
-  for (int i = tid; i < 64; i += T) {
-    s_rj[i] = lc.rj[i];
-    s_tj[i] = lc.tj[i];
-  }
+  const unsigned long long* __restrict__ g_rj =
+      reinterpret_cast<const unsigned long long*>(g_rules + ((tbl_words + 3) & ~3));
+  const unsigned long long* __restrict__ g_tj = g_rj + 64;
   // grid check, once per block: finite, grid[0] >= 0, strictly increasing
   bool bad_grid = false;
   for (int g = tid; g < G; g += T) {
@@ -212,7 +213,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   auto count_h = [&](int i) -> unsigned long long {
     if (!checked) {
       // one descriptor load, both count loads in flight together, no branches
-      const uint32_t d = s_desc[i];
+      const uint32_t d = g_desc[i];
       const uint32_t kind = d & 3u;
       const unsigned n0 = (unsigned)CNT((d >> 2) & 0x3fffu);
       const unsigned n1 = (unsigned)CNT((d >> 16) & 0x3fffu);
@@ -220,7 +221,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       const unsigned long long prod = (unsigned long long)(kind == 0u ? 1u : n0) * m;
       return kind == 2u ? prod >> 1 : prod;
     }
-    const int32_t* rec = s_rules + i * RULE_WORDS;
+    const int32_t* rec = g_rules + i * RULE_WORDS;
     const int nr = rec[R_NREAC];
     unsigned long long hh = 1ull;
     for (int a = 0; a < nr; ++a) {
@@ -354,7 +355,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     const uint4 w = philox4x32_10(make_uint4(n, 0u, (uint32_t)r + prm.r_offset, (uint32_t)p), prm.key0, prm.key1);
     const double u_tau = uniform52(w.x, w.y);
     const double u_sel = uniform52(w.z, w.w);
-    const double tau = __ddiv_rn(-log_spec_q(u_tau, lc, s_rj, s_tj), a0);
+    const double tau = __ddiv_rn(-log_spec_q(u_tau, lc, g_rj, g_tj), a0);
     const double tn = __dadd_rn(t, tau);
     const long long tnb = dbits(tn);
     while (gi < G && gbits < tnb) {
@@ -411,7 +412,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     // equals the sum of its children; the clamp only keeps indices in range.
     j = min(max(j, 0), M - 1);
     // apply the stoichiometry change (checked first: nothing changes on overflow)
-    const int32_t* rec = s_rules + j * RULE_WORDS;
+    const int32_t* rec = g_rules + j * RULE_WORDS;
     const int nd_ = rec[R_NDELTA];
     for (int d = 0; d < nd_; ++d) {
       const int v = rec[R_DELTA + d];
@@ -429,7 +430,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       Nf[j] = __dadd_rn(Nf[j], 1.0);
       const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
       for (int e = 0; e < dcnt; ++e) {
-        const int i = s_deps[doff + e];
+        const int i = g_deps[doff + e];
         const double hd = u63_to_double_rn(count_h(i));
         Iac[i] = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(tn, -tl[i])));
         tl[i] = tn;
@@ -440,7 +441,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       // the leaves are the propensities: recompute the dependents
       const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
       for (int e = 0; e < dcnt; ++e) {
-        const int i = s_deps[doff + e];
+        const int i = g_deps[doff + e];
         LEAF(i) = prop_of(i);
       }
     } else {
