@@ -852,10 +852,19 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // one event or the end of the trajectory: 0 = running, 1 = ended with grid
   // points left to fill, 2 = ended with the grid complete (or left to a resume)
   auto step = [&]() -> int {
-    if (ovf) {
+    // the same order of checks as the written specification: overflow of a
+    // count or of a0 first, then the event cap, then absorption.  On overflow
+    // the score's integrals stop at the last applied event (time t) and H
+    // counts as 0 after it; the lazily kept integrals are first brought up to t.
+    const double a0 = NODE(TREE_ROOT);
+    const long long a0b = dbits(a0);
+    if (ovf || a0b >= 0x7FF0000000000000ll) {
       status = TS_PROP_OVERFLOW;
       if (kSens)
-        for (int i = gl; i < M; i += kL) HV(i) = 0ull;
+        for (int i = gl; i < M; i += kL) {
+          integrate(i, t);
+          HV(i) = 0ull;
+        }
       grp.sync();
       return 1;
     }
@@ -863,17 +872,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       status = TS_EVENT_LIMIT;
       return 1;
     }
-    const double a0 = NODE(TREE_ROOT);
-    const long long a0b = dbits(a0);
     if (a0b == 0) {
       status = TS_ABSORBED;
-      return 1;
-    }
-    if (a0b >= 0x7FF0000000000000ll) {
-      status = TS_PROP_OVERFLOW;
-      if (kSens)
-        for (int i = gl; i < M; i += kL) HV(i) = 0ull;
-      grp.sync();
       return 1;
     }
     // the deadline is read every 1024 events, never before a trajectory has

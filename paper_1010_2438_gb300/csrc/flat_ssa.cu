@@ -321,29 +321,35 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     return 0;
   };
 
+  // propensity overflow: the current term's H is unusable, so the score's
+  // integrals stop at the last applied event (time t) and H counts as 0
+  // after it; the lazily kept integrals are first brought up to t
+  auto freeze_h = [&]() {
+    for (int i = 0; i < M; ++i) {
+      Iac[i] = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(t, -tl[i])));
+      tl[i] = t;
+      Hd[i * T] = 0.0;
+    }
+  };
+
   // one event or the end of the trajectory: 0 = running, 1 = ended with grid
   // points left to fill, 2 = ended with the grid complete (or left to a resume)
   auto step = [&]() -> int {
-    if (ovf) {
+    // the same order of checks as the written specification: overflow of a
+    // count product or of a0 first, then the event cap, then absorption
+    const double a0 = root;
+    const long long a0b = dbits(a0);
+    if (ovf || a0b >= 0x7FF0000000000000ll) {
       status = TS_PROP_OVERFLOW;
-      if (kSens)
-        for (int i = 0; i < M; ++i) Hd[i * T] = 0.0;
+      if (kSens) freeze_h();
       return 1;
     }
     if ((long long)n == prm.max_events) {
       status = TS_EVENT_LIMIT;
       return 1;
     }
-    const double a0 = root;
-    const long long a0b = dbits(a0);
     if (a0b == 0) {
       status = TS_ABSORBED;
-      return 1;
-    }
-    if (a0b >= 0x7FF0000000000000ll) {
-      status = TS_PROP_OVERFLOW;
-      if (kSens)
-        for (int i = 0; i < M; ++i) Hd[i * T] = 0.0;
       return 1;
     }
     // the deadline is read every 1024 events, never before a trajectory has

@@ -183,6 +183,32 @@ def test_cwc_sensitivity_partials_match_oracle(lanes):
     assert np.all(np.abs(gg - ograd) <= 1e-9 * (np.abs(ograd) + scale))
 
 
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_cwc_sensitivity_after_propensity_overflow_matches_oracle(lanes):
+    """Every rate scaled by f and the grid by 1/f keeps the dynamics but puts
+    a0 at ~60 % of the largest double, so that most terms overflow it part-way
+    through the grid.  The score's integrals then stop at the last applied
+    event and H counts as zero after it (the oracle's convention); partials
+    within the tolerance of the test above."""
+    b0 = W.cwc3x24(R=32, G=8)
+    f = 0.6 * 1.7976931348623157e308 / (9.6e3 / float(b0.grid[-1]))   # a0 ~ 9.6e3 / horizon
+    b = W.Batch(b0.model, b0.rates * f, b0.init, b0.grid * 0.5 / f, b0.R, b0.seed)
+    st = oracle.simulate(b, states=False, threads=8)["status"]
+    assert np.sum(st == capi.CWC_TRAJ_PROP_OVERFLOW) >= b.R // 2
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    means = torch.from_numpy(oracle.mean_observables(b, threads=8)).cuda()
+    rng = np.random.default_rng(13)
+    gm = torch.from_numpy(rng.standard_normal((1, b.G, cm.n_observables)) * 1e-3).cuda()
+    res = api.sensitivity(cm, rates, init, grid, b.R, b.seed, means, gm, partials=True, lanes=lanes)
+    torch.cuda.synchronize()
+    gp = res["partials"].cpu().numpy().reshape(b.R, -1)
+    _, op = oracle.sensitivity(b, means.cpu().numpy(), gm.cpu().numpy(), threads=8)
+    scale = np.mean(np.abs(op))
+    assert scale > 0
+    assert np.all(np.abs(gp - op) <= 1e-9 * (np.abs(op) + scale))
+
+
 def test_cwc_autograd_function():
     b0 = W.cwc3x24(R=64, G=6)
     b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.2, b0.R, b0.seed)

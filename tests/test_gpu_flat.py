@@ -234,6 +234,32 @@ def test_sensitivity_partials_match_oracle():
     assert np.all(np.abs(gg - ograd) <= 1e-9 * (np.abs(ograd) + scale))
 
 
+def test_sensitivity_after_propensity_overflow_matches_oracle():
+    """A birth-death process whose total propensity overflows to +inf once the
+    count reaches 2 (k_death = 1e308): most trajectories stop with
+    PROP_OVERFLOW part-way through the grid.  The score's integrals then stop
+    at the last applied event and H counts as zero after it (the oracle's
+    convention); the partials must agree to the same tolerance as above."""
+    model = W.birth_death()
+    rates = np.array([[1e307, 1e308]])
+    init = np.array([[1]], np.int32)
+    b = W.Batch(model, rates, init, W.uniform_grid(1e-305, 9), 128, 23)
+    cm = api.CompiledModel(b.model)
+    rates_d, init_d, grid_d = api.device_inputs(b)
+    means = torch.from_numpy(oracle.mean_observables(b, threads=8)).cuda()
+    rng = np.random.default_rng(5)
+    gm = torch.from_numpy(rng.standard_normal((1, b.G, b.model.n_observables))).cuda()
+    res = api.sensitivity(cm, rates_d, init_d, grid_d, b.R, b.seed, means, gm, partials=True)
+    torch.cuda.synchronize()
+    st = oracle.simulate(b, states=False, threads=8)["status"]
+    assert np.sum(st == capi.CWC_TRAJ_PROP_OVERFLOW) >= b.R // 2
+    gp = res["partials"].cpu().numpy().reshape(b.R, -1)
+    ograd, op = oracle.sensitivity(b, means.cpu().numpy(), gm.cpu().numpy(), threads=8)
+    scale = np.mean(np.abs(op))
+    assert scale > 0
+    assert np.all(np.abs(gp - op) <= 1e-9 * (np.abs(op) + scale))
+
+
 def test_autograd_function_forward_and_backward():
     b0 = W.flat8x12(R=256, G=10)
     b = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.1, b0.R, b0.seed)
