@@ -21,7 +21,7 @@ cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queu
                         int blocks_per_sm_cap, cudaStream_t stream, int* used_blocks);
 size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens);
 int flat_table_bytes_host(int M, int n_deps);
-int flat_best_threads(const FlatParams& prm, bool queue, bool sens);
+int flat_auto_threads(const FlatParams& prm, bool queue, bool sens);
 cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order, cudaStream_t stream);
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
 cudaError_t launch_stats(const unsigned long long* sums, const unsigned long long* sumsq, double* variance,
@@ -287,7 +287,7 @@ FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
 
 int pick_threads(const cwc_model* m, const cwc_sim_args* a, const FlatParams& prm, bool queue, bool sens) {
   if (a->block_threads > 0) return a->block_threads;
-  return cover_sms(flat_best_threads(prm, queue, sens), prm.Q);
+  return flat_auto_threads(prm, queue, sens);
 }
 
 }  // namespace

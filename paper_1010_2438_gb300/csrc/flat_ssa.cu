@@ -596,29 +596,51 @@ size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens) {
 
 int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps); }
 
-// Block size with the most resident warps per SM (ties: the larger block).
+// Automatic block size.  A batch larger than the GPU's resident capacity
+// takes the block size with the most resident warps per SM (ties: the larger
+// block).  A batch that fits in one resident wave at some block size takes,
+// among those sizes, the one whose busiest SM holds the fewest trajectories,
+// ceil(blocks / SMs) * T, since that SM sets the time of the launch (ties:
+// the larger block); e.g. 32,768 trajectories at 224 per block fill 147 SMs
+// with one block each instead of doubling up 19 SMs with 192-thread blocks.
 template <bool kQueue, bool kSens>
-static int best_threads_t(const FlatParams& prm) {
+static int auto_threads_t(const FlatParams& prm) {
   auto kern = flat_ssa_kernel<kQueue, kSens>;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    sms = 1;
+  int per_sm[9] = {0};                  // per_sm[T / 32], T = 32..256
   int best_T = 32, best_warps = -1;
   for (int T = 32; T <= 256; T += 32) {
     const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
     if (smem > 227 * 1024) break;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem) != cudaSuccess) break;
-    const int warps = per_sm * T / 32;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[T / 32], kern, T, smem) != cudaSuccess) break;
+    const int warps = per_sm[T / 32] * T / 32;
     if (warps >= best_warps) {
       best_warps = warps;
       best_T = T;
     }
   }
-  return best_T;
+  long long best_load = -1;
+  int pick = best_T;
+  for (int T = 256; T >= 32; T -= 32) {
+    if (per_sm[T / 32] < 1) continue;
+    const long long blocks = (prm.Q + T - 1) / T;
+    if (blocks > (long long)sms * per_sm[T / 32]) continue;          // more than one resident wave
+    const long long load = (blocks + sms - 1) / sms * T;             // trajectories on the busiest SM
+    if (best_load < 0 || load < best_load) {
+      best_load = load;
+      pick = T;
+    }
+  }
+  return pick;
 }
 
-int flat_best_threads(const FlatParams& prm, bool queue, bool sens) {
-  if (queue) return sens ? best_threads_t<true, true>(prm) : best_threads_t<true, false>(prm);
-  return sens ? best_threads_t<false, true>(prm) : best_threads_t<false, false>(prm);
+int flat_auto_threads(const FlatParams& prm, bool queue, bool sens) {
+  if (queue) return sens ? auto_threads_t<true, true>(prm) : auto_threads_t<true, false>(prm);
+  return sens ? auto_threads_t<false, true>(prm) : auto_threads_t<false, false>(prm);
 }
 
 cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queue, bool sens, int T,
