@@ -24,6 +24,7 @@ int flat_table_bytes_host(int M, int n_deps);
 int flat_auto_threads(const FlatParams& prm, bool queue, bool sens);
 cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order, cudaStream_t stream);
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
+cudaError_t launch_reciprocal(const double* k, double* inv, long long n, cudaStream_t st);
 cudaError_t launch_stats(const unsigned long long* sums, const unsigned long long* sumsq, double* variance,
                          double* ci90, long long n, int R, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, double* grad, int P, int R, int M, cudaStream_t st);
@@ -101,7 +102,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout: [header 256 B][sums P*G*O int64 if needed][partials Q*M double if needed]
 struct WsLayout {
-  size_t header = 0, sums = 0, sumsq = 0, partials = 0, slabs = 0, order = 0, sens_acc = 0, total = 0;
+  size_t header = 0, sums = 0, sumsq = 0, partials = 0, slabs = 0, order = 0, sens_acc = 0, inv_rates = 0, total = 0;
   bool need_sumsq = false;
   bool need_order = false;        // flat queue layout over several sweep points
   bool need_header = false, need_sums = false, need_partials = false;
@@ -204,6 +205,8 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
   if (m->flat && sens) {   // the flat replay's per-trajectory integrals, times and firing counts
     w.sens_acc = off;
     off = align256(off + (size_t)a->P * a->R * 3 * m->M * sizeof(double));
+    w.inv_rates = off;     // 1 / k per sweep point and rule
+    off = align256(off + (size_t)a->P * m->M * sizeof(double));
   }
   w.need_order = m->flat && chosen_layout(a) == CWC_LAYOUT_QUEUE && a->P > 1 && a->P <= 65536;
   if (w.need_order) {
@@ -680,6 +683,10 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     prm.grad_means = sens->grad_means;
     prm.partials = sens->partials != nullptr ? sens->partials : reinterpret_cast<double*>(ws + w.partials);
     prm.sens_acc = reinterpret_cast<double*>(ws + w.sens_acc);
+    double* inv = reinterpret_cast<double*>(ws + w.inv_rates);
+    e = launch_reciprocal(a->rates, inv, (long long)a->P * m->M, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reciprocal kernel launch");
+    prm.inv_rates = inv;
   }
   const LogConstants lc = make_log_constants();
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;

@@ -105,6 +105,7 @@ struct FlatParams {
   const double* grad_means;        // [P][G][S]
   double* partials;                // [Q][M]
   double* sens_acc;                // score replay: [Q][3][M] int_0^tl H_i dt, tl_i, firings N_i
+  const double* inv_rates;         // score replay: [P][M] 1 / k_j
   // scheduling
   WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)
   int32_t* ckpt;                   // [Q][S + CKPT_HEADER_WORDS] trajectory checkpoints (or null)

@@ -94,6 +94,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   double* tl = nullptr;     // [M]
   double* Nf = nullptr;     // [M] firings (whole numbers)
   double* part = nullptr;   // [M] the trajectory's partials
+  const double* ik = nullptr;   // [M] 1 / k_i of this sweep point
   int32_t* ibase = reinterpret_cast<int32_t*>(dbase + (size_t)n_dbl_rows * T);
   int32_t* cnt = ibase + tid;                                   // [S][T]
 
@@ -197,7 +198,10 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       const double gt = prm.grid[g];
       for (int i = 0; i < M; ++i) {
         const double Ig = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(gt, -tl[i])));
-        const double Si = __dadd_rn(__ddiv_rn(Nf[i], kp[i]), -Ig);
+        // N_i / k_i as N_i * (1 / k_i) (one extra rounding; the division when
+        // 1 / k_i overflows, for subnormal k_i)
+        const double nk = dbits(ik[i]) < 0x7FF0000000000000ll ? __dmul_rn(Nf[i], ik[i]) : __ddiv_rn(Nf[i], kp[i]);
+        const double Si = __dadd_rn(nk, -Ig);
         part[i] = __dadd_rn(part[i], __dmul_rn(c, Si));
       }
     }
@@ -297,6 +301,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       tl = Iac + M;
       Nf = tl + M;
       part = prm.partials + (size_t)q * M;
+      ik = prm.inv_rates + (size_t)p * M;
       for (int i = 0; i < M; ++i) part[i] = 0.0;
     }
     if (bad) {

@@ -88,6 +88,21 @@ cudaError_t launch_means(const unsigned long long* sums, double* means, long lon
   return cudaGetLastError();
 }
 
+// inv[i] = 1 / k[i] (IEEE division), once per call of the score replay, so
+// that a trajectory's grid points multiply by 1/k_j instead of dividing by k_j.
+__global__ void reciprocal_kernel(const double* __restrict__ k, double* __restrict__ inv, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    inv[i] = __ddiv_rn(1.0, k[i]);
+}
+
+cudaError_t launch_reciprocal(const double* k, double* inv, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  reciprocal_kernel<<<(unsigned)blocks, 256, 0, st>>>(k, inv, n);
+  return cudaGetLastError();
+}
+
 // The simulation's fixed logarithm over an array (for checking it against
 // the oracle bit for bit).  Inputs outside [2^-53, 1), the range of the
 // uniforms, give NaN.
