@@ -1,0 +1,173 @@
+"""The synthetic inputs that stand in for the paper's workloads (its E. coli
+and Lotka-Volterra models come without parameters): each generator must build
+what the input recipe states, deterministically from its seed.  CPU only; the
+generators hold no simulation arithmetic."""
+import numpy as np
+import pytest
+
+from paper_1010_2438_gb300 import workloads as W
+
+FLAT = [
+    # name, builder, S, M, inflow/outflow pairs, conversions, bimolecular, x_lo, x_hi
+    ("flat8x12", W.flat8x12, 8, 12, 0, 8, 4, 50, 500),
+    ("flat32x64", W.flat32x64, 32, 64, 8, 32, 16, 100, 5000),
+    ("flat16x24", W.flat16x24, 16, 24, 2, 16, 4, 50, 500),
+]
+
+
+def _orders(model):
+    return model.lhs[:, 0, :].sum(axis=1)
+
+
+def _strongly_connected(S, edges):
+    adj = [set() for _ in range(S)]
+    radj = [set() for _ in range(S)]
+    for a, b in edges:
+        adj[a].add(b)
+        radj[b].add(a)
+
+    def reach(g):
+        seen, stack = {0}, [0]
+        while stack:
+            for v in g[stack.pop()]:
+                if v not in seen:
+                    seen.add(v)
+                    stack.append(v)
+        return len(seen) == S
+    return reach(adj) and reach(radj)
+
+
+@pytest.mark.parametrize("name,build,S,M,pairs,n1,n2,x_lo,x_hi", FLAT)
+def test_flat_network_composition(name, build, S, M, pairs, n1, n2, x_lo, x_hi):
+    b = build(R=4, G=10)
+    m = b.model
+    assert (m.n_species, m.n_rules, m.n_labels, m.max_compartments) == (S, M, 1, 1)
+    assert np.all(m.kind == W.LOCAL) and np.all(m.ctx_label == 0)
+    assert np.all(m.lhs[:, 1:, :] == 0) and np.all(m.rhs[:, 1:, :] == 0)
+    order = _orders(m)
+    prod = m.rhs[:, 0, :].sum(axis=1)
+    inflow = [j for j in range(M) if order[j] == 0]
+    outflow = [j for j in range(M) if order[j] == 1 and prod[j] == 0]
+    assert len(inflow) == pairs and len(outflow) == pairs
+    # each inflow species has its outflow, on distinct species
+    in_sp = sorted(int(np.argmax(m.rhs[j, 0])) for j in inflow)
+    out_sp = sorted(int(np.argmax(m.lhs[j, 0])) for j in outflow)
+    assert in_sp == out_sp and len(set(in_sp)) == pairs
+    conv = [j for j in range(M) if order[j] == 1 and prod[j] == 1]
+    bi = [j for j in range(M) if order[j] == 2]
+    assert len(conv) == n1 and len(bi) == n2
+    # every reaction but the pairs conserves the molecule count
+    for j in conv + bi:
+        assert m.lhs[j, 0].sum() == m.rhs[j, 0].sum()
+    # stoichiometry 1-2 per species, both bimolecular forms (A + B and 2A)
+    assert m.lhs.max() <= 2 and m.rhs.max() <= 2
+    assert any(m.lhs[j, 0].max() == 2 for j in bi) and any(m.lhs[j, 0].max() == 1 for j in bi)
+    # the conversions contain a cycle through every species: no sink species
+    edges = [(int(np.argmax(m.lhs[j, 0])), int(np.argmax(m.rhs[j, 0]))) for j in conv]
+    assert all(a != b for a, b in edges)
+    assert _strongly_connected(S, edges)
+
+
+@pytest.mark.parametrize("name,build,S,M,pairs,n1,n2,x_lo,x_hi", FLAT)
+def test_flat_rates_counts_and_grid(name, build, S, M, pairs, n1, n2, x_lo, x_hi):
+    b = build(R=4, G=10)
+    m = b.model
+    omega = 0.5 * (x_lo + x_hi)
+    order = _orders(m)
+    # log-uniform over [1e-3, 1] in concentration units, volume-scaled by omega^(1 - order)
+    k = b.rates[0] / omega ** (1.0 - order)
+    assert b.rates.shape == (1, M) and np.all(k >= 1e-3 * (1 - 1e-12)) and np.all(k <= 1.0 * (1 + 1e-12))
+    assert np.log10(k).max() - np.log10(k).min() > 1.5          # spread over the decades
+    assert b.init.shape == (1, S) and b.init.dtype == np.int32
+    assert np.all(b.init >= x_lo) and np.all(b.init <= x_hi)
+    T = b.grid[-1]
+    assert b.grid[0] == 0.0 and T > 0
+    assert np.allclose(b.grid, np.arange(10) * T / 9, rtol=0, atol=1e-15 * T)
+    assert np.all(np.diff(b.grid) > 0)
+
+
+@pytest.mark.parametrize("build", [W.flat8x12, W.flat32x64, W.flat16x24, W.cwc3x24, W.sweep256x256])
+def test_generators_are_deterministic(build):
+    a, b = build(R=2, G=5), build(R=2, G=5)
+    for x, y in ((a.rates, b.rates), (a.init, b.init), (a.grid, b.grid), (a.model.lhs, b.model.lhs),
+                 (a.model.rhs, b.model.rhs), (a.model.kind, b.model.kind)):
+        assert np.array_equal(x, y)
+    assert a.seed == b.seed
+
+
+def test_sweep_rate_vectors():
+    base = W.flat32x64(R=2, G=5)
+    sw = W.sweep256x256(P=256, R=2, G=5)
+    assert sw.rates.shape == (256, 64) and sw.P == 256
+    assert np.array_equal(sw.model.lhs, base.model.lhs)
+    ratio = np.log10(sw.rates / base.rates[0])
+    # common two-decade factor times a per-rate jitter of +-1/4 decade
+    assert np.all(ratio >= -1.25 - 1e-12) and np.all(ratio <= 1.25 + 1e-12)
+    common = ratio.mean(axis=1)
+    assert common.max() - common.min() > 1.6                   # points ~2 decades apart
+    assert np.all(ratio.max(axis=1) - ratio.min(axis=1) <= 0.5 + 1e-12)
+    assert np.all(ratio.max(axis=1) - ratio.min(axis=1) > 0.2)   # the vectors differ in shape
+
+
+def test_cwc3x24_rules():
+    b = W.cwc3x24(R=2, G=5)
+    m = b.model
+    assert (m.n_species, m.n_labels, m.max_compartments, m.n_rules) == (24, 4, 64, 48)
+    kinds = np.bincount(m.kind, minlength=4)
+    assert kinds.tolist() == [24, 12, 6, 6]
+    for lab in range(4):
+        assert np.sum((m.kind == W.LOCAL) & (m.ctx_label == lab)) == 6
+    # containment: top holds labels 1 and 2, label 1 holds label 3
+    allowed = {(0, 1), (0, 2), (1, 3)}
+    for j in range(m.n_rules):
+        if m.kind[j] != W.LOCAL:
+            assert (int(m.ctx_label[j]), int(m.child_label[j])) in allowed
+    pc = np.where(m.kind == W.PARENT_CHILD)[0]
+    into = [j for j in pc if m.lhs[j, 0].sum() == 1 and m.rhs[j, 2].sum() == 1 and m.lhs[j, 1].sum() == 0]
+    out = [j for j in pc if m.lhs[j, 2].sum() == 1 and m.rhs[j, 0].sum() == 1]
+    wrap = [j for j in pc if m.lhs[j, 1].sum() == 1]
+    assert (len(into), len(out), len(wrap)) == (6, 4, 2)
+    # the token is touched only by CREATE (parent content -> new wrap) and DISSOLVE (wrap)
+    tok = W.CWC_TOKEN
+    for j in range(m.n_rules):
+        uses = m.lhs[j, :, tok].any() or m.rhs[j, :, tok].any()
+        assert uses == (m.kind[j] in (W.CREATE, W.DISSOLVE))
+    for j in np.where(m.kind == W.CREATE)[0]:
+        assert m.lhs[j, 0, tok] == 1 and m.rhs[j, 1, tok] == 1 and m.rhs[j, 2].sum() == 20
+    for j in np.where(m.kind == W.DISSOLVE)[0]:
+        assert m.lhs[j, 1, tok] == 1 and m.lhs[j].sum() == 1
+    structural = np.isin(m.kind, [W.CREATE, W.DISSOLVE])
+    assert np.all(b.rates[0, structural] >= 0.1 * (1 - 1e-12)) and np.all(b.rates[0, structural] <= 1.0)
+
+
+def test_cwc3x24_initial_term():
+    b = W.cwc3x24(R=2, G=5)
+    S, tok = 24, W.CWC_TOKEN
+    img = b.init[0]
+    assert img.shape == (64, W.slot_image_width(S))
+    alive = img[:, 0] == 1
+    assert alive.sum() == 33 and np.all(alive[:33]) and not alive[33:].any()
+    labels, parents = img[:33, 1], img[:33, 2]
+    assert labels[0] == 0 and parents[0] == -1
+    assert np.sum(labels == 1) == 8 and np.sum(labels == 2) == 8 and np.sum(labels == 3) == 16
+    for c in range(1, 33):
+        assert labels[parents[c]] == {1: 0, 2: 0, 3: 1}[int(labels[c])]
+        assert img[c, 3 + tok] == 1                                 # one token in every wrap
+    wrap, content = img[:, 3:3 + S], img[:, 3 + S:]
+    assert wrap[:, tok].sum() + content[:, tok].sum() == 63          # so at most 64 compartments
+    mol = content[:33, :tok]
+    assert np.all(mol >= 10) and np.all(mol <= 200)
+    assert np.all(wrap[:33, :tok] == 0)
+
+
+@pytest.mark.parametrize("n", [2, 4, 32])
+def test_lotka_volterra_chain(n):
+    b = W.lotka_volterra(n, R=2, G=5)
+    m = b.model
+    assert m.n_species == n and m.n_rules == n + 1
+    assert m.lhs[0, 0, 0] == 1 and m.rhs[0, 0, 0] == 2                # prey birth
+    for i in range(n - 1):                                            # S_i + S_(i+1) -> 2 S_(i+1)
+        assert m.lhs[i + 1, 0, i] == 1 and m.lhs[i + 1, 0, i + 1] == 1 and m.rhs[i + 1, 0, i + 1] == 2
+    assert m.lhs[n, 0, n - 1] == 1 and m.rhs[n].sum() == 0            # last predator death
+    assert np.all(b.init == 1000)
+    assert b.rates[0, 0] == 10.0 and b.rates[0, -1] == 10.0 and np.all(b.rates[0, 1:-1] == 0.01)
