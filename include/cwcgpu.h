@@ -299,8 +299,10 @@ cwc_status cwc_simulate(const cwc_model* model, const cwc_sim_args* args, void* 
  *   grad_rates         device double [P][M]   (output)
  *   partials           device double [P][R][M] per-trajectory terms
  *                      (output if non-NULL, else kept in the workspace)
- * The sum over r is a fixed pairwise tree, so results are identical from
- * run to run.  Workspace: cwc_sensitivity_workspace_size().
+ * A trajectory that stops with CWC_TRAJ_PROP_OVERFLOW counts H_j as 0 after
+ * its last applied event; any other stop keeps the last H_j up to the end of
+ * the grid.  The sum over r is a fixed pairwise tree, so results are
+ * identical from run to run.  Workspace: cwc_sensitivity_workspace_size().
  * Errors as cwc_simulate, plus CWC_ERR_INVALID_ARG for missing
  * means/grad_means/grad_rates.
  */
