@@ -390,8 +390,8 @@ def main():
             # fraction, from the ncu capture of the profiling case
             issue = {"frac": tj.get("issue_active_frac"), "fp64_pipe_frac": tj.get("fp64_pipe_frac"),
                      "warps_per_sm": tj.get("warps_per_sm"),
-                     "source": "ncu smsp__issue_active / sm__pipe_fp64_cycles_active, profiling case "
-                               "(profiles/flat_ssa_kernel_flat32x64.md)"}
+                     "source": "ncu smsp__issue_active / sm__pipe_fp64_cycles_active of the profiling case, "
+                               "captured on the same kernel sources (hash-checked)"}
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9, "unit": "GFLOP/s (FP64)",
                 "frac": achieved / FP64_PEAK_OPS, "traffic": traffic, "issue": issue,
                 "note": "FP64 pipe (the path's only floating-point unit; the logarithm is integer): %.1f algorithmic "

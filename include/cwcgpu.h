@@ -251,20 +251,35 @@ typedef struct {
  * a service with a fixed device-memory budget reserved up front).  The paper
  * has no counterpart: this is an interface convenience of this library.
  *
- * The scratch it needs (the work-queue ticket, the deadline timestamp and,
- * when only `means` is requested, the int64 replica sums) lives in one
- * statically sized device array of CWC_NOALLOC_SCRATCH_BYTES inside the
- * library; every GPU that loads the library holds that array until the
- * process exits.  args->workspace and args->workspace_bytes are ignored.
- * A call whose scratch would exceed the array (256 bytes + 8 * P * G * O when
- * means are requested without sums) returns CWC_ERR_INVALID_ARG and enqueues
- * nothing.  It calls no cudaMalloc or cudaFree.
+ * The scratch it needs lives in one statically sized device array of
+ * CWC_NOALLOC_SCRATCH_BYTES inside the library; every GPU that loads the
+ * library holds that array until the process exits.  args->workspace and
+ * args->workspace_bytes are ignored.  The scratch is exactly what
+ * cwc_simulate_workspace_size reports for the same arguments, so a call fits
+ * when that size is <= CWC_NOALLOC_SCRATCH_BYTES.  Its parts, each rounded up
+ * to 256 bytes:
+ *   - 256 bytes: work-queue ticket and deadline timestamp;
+ *   - 8 * P * G * O: int64 replica sums, when means, variance or ci90 are
+ *     requested without sums;
+ *   - 16 * P * G * O: 128-bit sums of squares, when variance or ci90 are
+ *     requested without sumsq;
+ *   - 12 * P: the longest-first sweep order of a flat model in the queue
+ *     layout with P > 1;
+ *   - compartment models: one term slab per resident lane group of the
+ *     launch, about 13 KB each for 64 slots x 24 species; a compartment
+ *     batch therefore fits only while it occupies a few dozen lane groups
+ *     (roughly 70-80 trajectories at 4 lanes each for such a model).
+ * A call that needs more returns CWC_ERR_INVALID_ARG and enqueues nothing.
+ * It calls no cudaMalloc or cudaFree.
  *
  * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.  All
- * calls on a device share the one array and each clears what must start at
- * zero, so calls whose work overlaps on the GPU (different streams, or
- * different host threads) race on it: serialise them.
+ * that device current and caches it for the life of the process; make that
+ * first call before any stream capture.  The cached address does not survive
+ * a reset of the device's primary context (cudaDeviceReset): do not call this
+ * entry point on a device after resetting it.  All calls on a device share
+ * the one array and each clears what must start at zero, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * it: serialise them.
  */
 #define CWC_NOALLOC_SCRATCH_BYTES (1u << 20)
 cwc_status cwc_simulate_noalloc(const cwc_model* model, const cwc_sim_args* args, void* stream);

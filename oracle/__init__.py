@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 from concurrent.futures import ThreadPoolExecutor
 from typing import Dict, Optional
 
@@ -24,6 +25,7 @@ from . import build as _build
 ST_OK, ST_ABSORBED, ST_INT_OVERFLOW, ST_PROP_OVERFLOW, ST_CAPACITY, ST_EVENT_LIMIT, ST_BAD_INPUT = range(7)
 
 _lib = None
+_lib_lock = threading.Lock()
 
 
 class _Model(ctypes.Structure):
@@ -36,30 +38,35 @@ class _Model(ctypes.Structure):
 
 def lib():
     global _lib
-    if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
-        L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
-        L.oracle_philox_array.argtypes = [vp, vp, vp, i64]
-        L.oracle_u52.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
-        L.oracle_u52.restype = dbl
-        L.oracle_log_spec.argtypes = [dbl]
-        L.oracle_log_spec.restype = dbl
-        L.oracle_log_spec_array.argtypes = [vp, vp, i64]
-        L.oracle_tree_sum.argtypes = [vp, i32]
-        L.oracle_tree_sum.restype = dbl
-        L.oracle_select.argtypes = [vp, i32, dbl]
-        L.oracle_select.restype = i32
-        L.oracle_num_observables.argtypes = [vp]
-        L.oracle_num_observables.restype = i32
-        L.oracle_rule_totals.argtypes = [vp, vp, vp]
-        L.oracle_rule_totals.restype = ctypes.c_int
-        L.oracle_simulate.argtypes = [
-            vp, vp, i32, i32, vp, i32, vp, i32, u64, i64, i64, i64,
-            vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
-        L.oracle_simulate.restype = ctypes.c_int
-        _lib = L
+    with _lib_lock:
+        return _lib if _lib is not None else _load()
+
+
+def _load():
+    global _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
+    L.oracle_philox_array.argtypes = [vp, vp, vp, i64]
+    L.oracle_u52.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+    L.oracle_u52.restype = dbl
+    L.oracle_log_spec.argtypes = [dbl]
+    L.oracle_log_spec.restype = dbl
+    L.oracle_log_spec_array.argtypes = [vp, vp, i64]
+    L.oracle_tree_sum.argtypes = [vp, i32]
+    L.oracle_tree_sum.restype = dbl
+    L.oracle_select.argtypes = [vp, i32, dbl]
+    L.oracle_select.restype = i32
+    L.oracle_num_observables.argtypes = [vp]
+    L.oracle_num_observables.restype = i32
+    L.oracle_rule_totals.argtypes = [vp, vp, vp]
+    L.oracle_rule_totals.restype = ctypes.c_int
+    L.oracle_simulate.argtypes = [
+        vp, vp, i32, i32, vp, i32, vp, i32, u64, i64, i64, i64,
+        vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+    L.oracle_simulate.restype = ctypes.c_int
+    _lib = L
     return _lib
 
 

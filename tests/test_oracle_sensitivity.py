@@ -6,9 +6,12 @@ d E[f(X(g))]/d k_j = E[(f(X(g)) - E f) S_j(g)].  With an upstream gradient
 G[g, o] of L = sum_g,o G[g,o] E[X_o(g)], the oracle returns per trajectory
 sum_g c(g) S_j(g), c(g) = sum_o G[g,o] (X_o(g) - mean_o(g)).
 
-Tolerances are stated in Monte-Carlo standard errors (SE) of the estimates,
-with fixed seeds: every entry within 4 SE (chance of a 4-SE excursion per
-entry ~6e-5) and at least 90% of entries within 2.5 SE.
+Tolerance, stated in Monte-Carlo standard errors (SE) of the estimates, with
+fixed seeds: at least 99 % of the entries within 3 SE and none beyond 5 SE;
+with fewer than 100 entries (where 99 % would allow no miss anyway) every
+entry within 3 SE.  For a comparison with finite differences the SE is
+sqrt(SE_LR^2 + SE_FD^2).  The same rule is used by the GPU tests
+(tests/test_gpu_lr_fd.py).
 """
 import math
 
@@ -36,12 +39,17 @@ def lr_per_grid_point(batch, threads=8):
     return est, se
 
 
-def check_z(z, bound=4.0, frac_bound=2.5, frac=0.9):
-    z = np.abs(np.asarray(z)).ravel()
+def check_z(z):
+    """>= 99 % of |z| within 3 and none beyond 5; every |z| within 3 when
+    there are fewer than 100 entries."""
+    z = np.abs(np.asarray(z, np.float64)).ravel()
     print("z-scores:", np.round(z, 2))
-    z = z[np.isfinite(z)]
-    assert np.all(z <= bound), z.max()
-    assert np.mean(z <= frac_bound) >= frac
+    assert np.all(np.isfinite(z))
+    if z.size < 100:
+        assert np.all(z <= 3.0), z.max()
+    else:
+        assert np.mean(z <= 3.0) >= 0.99, np.mean(z <= 3.0)
+        assert np.all(z <= 5.0), z.max()
 
 
 def test_birth_death_lr_matches_analytic_gradient():

@@ -45,9 +45,9 @@ def _outputs(cm, batch, rates, init, grid):
     return a, d
 
 
-def test_noalloc_matches_workspace_entry_point_twice():
-    b0 = W.sweep256x256(P=3, R=700)
-    batch = W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.02, b0.R, b0.seed)
+def _compare_twice(batch):
+    """cwc_simulate with a caller-owned workspace, then cwc_simulate_noalloc
+    twice on fresh outputs: all three must agree bit for bit."""
     cm = api.CompiledModel(batch.model)
     rates, init, grid = api.device_inputs(batch)
     stream = torch.cuda.current_stream().cuda_stream
@@ -55,7 +55,7 @@ def test_noalloc_matches_workspace_entry_point_twice():
     # reference: cwc_simulate with a caller-owned workspace
     a_ref, ref = _outputs(cm, batch, rates, init, grid)
     nbytes = capi.cwc_simulate_workspace_size(cm.handle, a_ref)
-    assert nbytes > 0            # this configuration does use scratch (queue ticket, sums)
+    assert 0 < nbytes <= capi.CWC_NOALLOC_SCRATCH_BYTES   # uses scratch, and it fits the fixed array
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
     a_ref.workspace = (ws.data_ptr() + 255) & ~255
     a_ref.workspace_bytes = nbytes
@@ -70,6 +70,21 @@ def test_noalloc_matches_workspace_entry_point_twice():
         for k in ref:
             assert torch.equal(got[k], ref[k]), (call, k)
         assert torch.all(got["events"] > 0)
+
+
+def test_noalloc_matches_workspace_entry_point_twice():
+    """A flat network over three sweep points: the queue ticket, the sweep
+    order and the replica sums behind the means live in the scratch."""
+    b0 = W.sweep256x256(P=3, R=700)
+    _compare_twice(W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.02, b0.R, b0.seed))
+
+
+def test_noalloc_compartment_model_matches_workspace_entry_point_twice():
+    """The 24-species compartment workload with 40 replicas: here the scratch
+    also holds one term slab per resident lane group, which is what makes
+    a compartment batch fit the fixed array only when it is small."""
+    b0 = W.cwc3x24(R=40, G=25)
+    _compare_twice(W.Batch(b0.model, b0.rates, b0.init, b0.grid * 0.1, b0.R, b0.seed))
 
 
 def test_noalloc_rejects_scratch_beyond_its_limit():
