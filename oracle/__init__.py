@@ -13,6 +13,7 @@ disjoint trajectory ranges in parallel.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 import threading
 from concurrent.futures import ThreadPoolExecutor
@@ -32,7 +33,7 @@ class _Model(ctypes.Structure):
     _fields_ = [
         ("S", ctypes.c_int32), ("L", ctypes.c_int32), ("C", ctypes.c_int32), ("M", ctypes.c_int32),
         ("kind", ctypes.c_void_p), ("ctx_label", ctypes.c_void_p), ("child_label", ctypes.c_void_p),
-        ("lhs", ctypes.c_void_p), ("rhs", ctypes.c_void_p),
+        ("grand_label", ctypes.c_void_p), ("lhs", ctypes.c_void_p), ("rhs", ctypes.c_void_p),
     ]
 
 
@@ -79,9 +80,11 @@ class _ModelHandle:
 
     def __init__(self, model):
         m = model.contiguous()
-        self.arrays = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs)
+        lhs5, rhs5, grand = m.rows5()        # pattern rows 0-4 (rows 3-4 zero for the 3-row kinds)
+        self.arrays = (m.kind, m.ctx_label, m.child_label, grand, lhs5, rhs5)
         self.struct = _Model(m.n_species, m.n_labels, m.max_compartments, m.n_rules,
-                             _ptr(m.kind), _ptr(m.ctx_label), _ptr(m.child_label), _ptr(m.lhs), _ptr(m.rhs))
+                             _ptr(m.kind), _ptr(m.ctx_label), _ptr(m.child_label), _ptr(grand),
+                             _ptr(lhs5), _ptr(rhs5))
 
     @property
     def ref(self):
@@ -146,8 +149,15 @@ def simulate(batch, q_begin: int = 0, q_end: Optional[int] = None, *, states: bo
              log_cap: int = 0, means: Optional[np.ndarray] = None,
              grad_means: Optional[np.ndarray] = None, threads: int = 1,
              rates: Optional[np.ndarray] = None, seed: Optional[int] = None,
-             max_events: Optional[int] = None) -> Dict[str, np.ndarray]:
+             max_events: Optional[int] = None, schedule: str = "static") -> Dict[str, np.ndarray]:
     """Run trajectories q in [q_begin, q_end) (q = p*R + r) of ``batch``.
+
+    With ``threads > 1`` the trajectories are split over threads either
+    statically (``schedule="static"``: one contiguous range per thread) or on
+    demand (``schedule="farm"``: each thread takes the next unstarted
+    trajectory whenever it finishes one, the task farm of independent
+    simulation instances of Sec. 5.2, so uneven trajectory lengths do not
+    leave threads idle).  Results do not depend on the split.
 
     Returns a dict with ``status``, ``events``, ``hash``, ``final_t`` [nq],
     ``states`` [nq, G, O] (if requested), ``log_rule/log_slot/log_t``
@@ -207,12 +217,31 @@ def simulate(batch, q_begin: int = 0, q_end: Optional[int] = None, *, states: bo
         rc = run(q_begin, q_end)
         if rc != 0:
             raise ValueError("oracle rejected the model")
-    else:
+    elif schedule == "farm":
+        tickets = itertools.count(q_begin)
+        lock = threading.Lock()
+
+        def worker(_):
+            rc = 0
+            while True:
+                with lock:
+                    q = next(tickets)
+                if q >= q_end:
+                    return rc
+                rc |= run(q, q + 1)
+
+        with ThreadPoolExecutor(threads) as ex:
+            rcs = list(ex.map(worker, range(threads)))
+        if any(rcs):
+            raise ValueError("oracle rejected the model")
+    elif schedule == "static":
         bounds = [q_begin + (nq * i) // threads for i in range(threads + 1)]
         with ThreadPoolExecutor(threads) as ex:
             rcs = list(ex.map(lambda i: run(bounds[i], bounds[i + 1]), range(threads)))
         if any(rcs):
             raise ValueError("oracle rejected the model")
+    else:
+        raise ValueError("schedule must be 'static' or 'farm'")
     return out
 
 

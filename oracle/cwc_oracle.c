@@ -27,10 +27,15 @@
  *   tree_sum        error bound against an exactly rounded sum (math.fsum).
  *   select_rule     never picks a zero entry; frequencies vs a_j / a0.
  *   propensities    Sec. 2.2 worked example (rate 4k); brute-force counting
- *                   of distinct reactant tuples on small terms.
+ *                   of distinct reactant tuples on small terms, and of
+ *                   distinct occurrences of FUSION / NESTED left-hand sides
+ *                   (identified atoms and compartments) on random terms.
+ *   context choice  chi-square laws where the chosen compartment changes the
+ *                   outcome; exact recomputation of the integer draw.
  *   simulate        closed-form laws (birth-death Poisson / binomial mixture,
- *                   isomerisation binomial), chemical master equation via
- *                   matrix exponential, conservation invariants.
+ *                   isomerisation binomial, depth-two transport binomial),
+ *                   chemical master equation via matrix exponential (incl.
+ *                   fusion of empty compartments), conservation invariants.
  *   sensitivities   analytic birth-death gradient; central finite
  *                   differences with common random numbers.
  */
@@ -52,13 +57,33 @@ enum {
   ST_BAD_INPUT = 6       /* rates, initial term or grid invalid             */
 };
 
-enum { K_LOCAL = 0, K_PARENT_CHILD = 1, K_CREATE = 2, K_DISSOLVE = 3 };
+/* Rule kinds.  A rule's left-hand side is matched in the content of a
+ * compartment of its label l (Sec. 2.1); with the compartment patterns it may
+ * contain, the kinds are
+ *   LOCAL         l: p X -> p' X
+ *   PARENT_CHILD  l: p X (w x | q Y)^l' -> p' X (w' x | q' Y)^l'
+ *   CREATE        l: p X -> p' X (w' | q')^l'
+ *   DISSOLVE      l: p X (w x | q Y)^l' -> p' X x Y
+ *   FUSION        l: p X (w1 x1 | q1 Y1)^l' (w2 x2 | q2 Y2)^l'
+ *                      -> p' X (w' x1 x2 | q' Y1 Y2)^l'      (two compartments)
+ *   NESTED        l: p X (w x | q Y (v z | u Z)^l'')^l'
+ *                      -> p' X (w' x | q' Y (v' z | u' Z)^l'')^l'   (depth two) */
+enum { K_LOCAL = 0, K_PARENT_CHILD = 1, K_CREATE = 2, K_DISSOLVE = 3, K_FUSION = 4, K_NESTED = 5 };
+
+/* Pattern rows of lhs / rhs ([M][ROWS][S]):
+ *   0  the context's content (the parent's, for rules with a compartment)
+ *   1  wrap of the (first) child      2  content of the (first) child
+ *   3  FUSION: wrap of the second child, NESTED: wrap of the grandchild
+ *   4  FUSION: content of the second child, NESTED: content of the grandchild
+ * CREATE's rhs rows 1, 2 are the new compartment's wrap and content; FUSION's
+ * rhs rows 1, 2 are added to the merged wrap and content. */
+#define ROWS 5
 
 typedef struct {
   int32_t S, L, C, M;
-  const int32_t *kind, *ctx_label, *child_label;
-  const int32_t *lhs; /* [M][3][S]: context content, child wrap, child content */
-  const int32_t *rhs; /* [M][3][S] */
+  const int32_t *kind, *ctx_label, *child_label, *grand_label;
+  const int32_t *lhs; /* [M][ROWS][S] */
+  const int32_t *rhs; /* [M][ROWS][S] */
 } oracle_model;
 
 /* ------------------------------------------------------------------------ */
@@ -293,24 +318,62 @@ static int pattern_count(const int32_t* pattern, const int32_t* multiset, int32_
 /* Is slot c a context of rule j?  LOCAL/CREATE: slot of the rule's label.    */
 /* PARENT_CHILD/DISSOLVE: a child slot of label child_label whose parent has  */
 /* the rule's label.                                                          */
+/* NESTED: a grandchild slot of label grand_label whose parent has label     */
+/* child_label and whose grandparent has the rule's label.  FUSION's contexts */
+/* are pairs of slots (is_pair below), never single slots.                    */
 static int is_context(const oracle_model* m, const term_t* t, int j, int c) {
   if (!t->alive[c]) return 0;
   int kind = m->kind[j];
   if (kind == K_LOCAL || kind == K_CREATE) return t->label[c] == m->ctx_label[j];
+  if (kind == K_FUSION) return 0;
   if (c == 0) return 0;
   int q = t->parent[c];
+  if (kind == K_NESTED) {
+    if (t->label[c] != m->grand_label[j] || q == 0) return 0;
+    return t->label[q] == m->child_label[j] && t->label[t->parent[q]] == m->ctx_label[j];
+  }
   return t->label[c] == m->child_label[j] && t->label[q] == m->ctx_label[j];
+}
+
+/* FUSION: are the two patterns identical?  Then the occurrences (d1, d2) and */
+/* (d2, d1) are the same subterm and only d1 < d2 counts.                      */
+static int fusion_symmetric(const oracle_model* m, int j) {
+  const int32_t* lhs = m->lhs + (size_t)j * ROWS * m->S;
+  for (int x = 0; x < m->S; x++)
+    if (lhs[m->S + x] != lhs[3 * m->S + x] || lhs[2 * m->S + x] != lhs[4 * m->S + x]) return 0;
+  return 1;
+}
+
+/* Is the ordered pair (d1, d2) an occurrence context of FUSION rule j: two   */
+/* distinct alive children of label child_label under the same parent, whose */
+/* label is the rule's?                                                        */
+static int is_pair(const oracle_model* m, const term_t* t, int j, int d1, int d2) {
+  if (d1 == d2 || d1 == 0 || d2 == 0 || !t->alive[d1] || !t->alive[d2]) return 0;
+  if (t->label[d1] != m->child_label[j] || t->label[d2] != m->child_label[j]) return 0;
+  if (t->parent[d1] != t->parent[d2]) return 0;
+  if (t->label[t->parent[d1]] != m->ctx_label[j]) return 0;
+  if (d1 > d2 && fusion_symmetric(m, j)) return 0;
+  return 1;
 }
 
 /* Match(rule, term, context): number of distinct reactant combinations of   */
 /* rule j at context c (Sec. 2.2).  -1 on overflow.                           */
 static int match_count(const oracle_model* m, const term_t* t, int j, int c, int64_t* h) {
   const int32_t S = m->S;
-  const int32_t* lhs = m->lhs + (size_t)j * 3 * S;
+  const int32_t* lhs = m->lhs + (size_t)j * ROWS * S;
   int kind = m->kind[j];
   int64_t acc = 1;
   if (kind == K_LOCAL || kind == K_CREATE) {
     if (pattern_count(lhs, t->content + (size_t)c * S, S, &acc)) return -1;
+  } else if (kind == K_NESTED) {
+    /* c is the grandchild; rows: grandparent content, child wrap and content, */
+    /* grandchild wrap and content                                            */
+    int q = t->parent[c], a = t->parent[q];
+    if (pattern_count(lhs, t->content + (size_t)a * S, S, &acc)) return -1;
+    if (pattern_count(lhs + S, t->wrap + (size_t)q * S, S, &acc)) return -1;
+    if (pattern_count(lhs + 2 * S, t->content + (size_t)q * S, S, &acc)) return -1;
+    if (pattern_count(lhs + 3 * S, t->wrap + (size_t)c * S, S, &acc)) return -1;
+    if (pattern_count(lhs + 4 * S, t->content + (size_t)c * S, S, &acc)) return -1;
   } else {
     int q = t->parent[c];
     if (pattern_count(lhs, t->content + (size_t)q * S, S, &acc)) return -1;
@@ -321,9 +384,37 @@ static int match_count(const oracle_model* m, const term_t* t, int j, int c, int
   return 0;
 }
 
+/* FUSION: occurrences at the pair (d1, d2): parent content x first child's   */
+/* wrap and content x second child's wrap and content.                        */
+static int pair_count(const oracle_model* m, const term_t* t, int j, int d1, int d2, int64_t* h) {
+  const int32_t S = m->S;
+  const int32_t* lhs = m->lhs + (size_t)j * ROWS * S;
+  int64_t acc = 1;
+  int q = t->parent[d1];
+  if (pattern_count(lhs, t->content + (size_t)q * S, S, &acc)) return -1;
+  if (pattern_count(lhs + S, t->wrap + (size_t)d1 * S, S, &acc)) return -1;
+  if (pattern_count(lhs + 2 * S, t->content + (size_t)d1 * S, S, &acc)) return -1;
+  if (pattern_count(lhs + 3 * S, t->wrap + (size_t)d2 * S, S, &acc)) return -1;
+  if (pattern_count(lhs + 4 * S, t->content + (size_t)d2 * S, S, &acc)) return -1;
+  *h = acc;
+  return 0;
+}
+
 /* H_j = sum over contexts of the combinatorial counts (int64, -1 overflow). */
 static int rule_total(const oracle_model* m, const term_t* t, int j, int64_t* H) {
   int64_t total = 0;
+  if (m->kind[j] == K_FUSION) {
+    for (int d1 = 0; d1 < t->C; d1++)
+      for (int d2 = 0; d2 < t->C; d2++) {
+        if (!is_pair(m, t, j, d1, d2)) continue;
+        int64_t h, s;
+        if (pair_count(m, t, j, d1, d2, &h)) return -1;
+        if (__builtin_add_overflow(total, h, &s)) return -1;
+        total = s;
+      }
+    *H = total;
+    return 0;
+  }
   for (int c = 0; c < t->C; c++) {
     if (!is_context(m, t, j, c)) continue;
     int64_t h;
@@ -373,9 +464,52 @@ static int fits(int64_t v) { return v >= 0 && v <= 2147483647LL; }
 /* Returns ST_OK, ST_CAPACITY or ST_INT_OVERFLOW (then nothing changed).     */
 static int apply_rule(const oracle_model* m, term_t* t, int j, int c) {
   const int S = m->S;
-  const int32_t* lhs = m->lhs + (size_t)j * 3 * S;
-  const int32_t* rhs = m->rhs + (size_t)j * 3 * S;
+  const int32_t* lhs = m->lhs + (size_t)j * ROWS * S;
+  const int32_t* rhs = m->rhs + (size_t)j * ROWS * S;
   int kind = m->kind[j];
+  if (kind == K_NESTED) {
+    /* c is the grandchild: rewrite the five matched multisets in place */
+    int q = t->parent[c], a = t->parent[q];
+    int32_t* ms[5] = {t->content + (size_t)a * S, t->wrap + (size_t)q * S, t->content + (size_t)q * S,
+                      t->wrap + (size_t)c * S, t->content + (size_t)c * S};
+    for (int row = 0; row < 5; row++)
+      for (int s = 0; s < S; s++)
+        if (!fits((int64_t)ms[row][s] + rhs[row * S + s] - lhs[row * S + s])) return ST_INT_OVERFLOW;
+    for (int row = 0; row < 5; row++)
+      for (int s = 0; s < S; s++) ms[row][s] = ms[row][s] + rhs[row * S + s] - lhs[row * S + s];
+    return ST_OK;
+  }
+  if (kind == K_FUSION) {
+    /* c encodes the pair (d1, d2); the merged compartment keeps the lower   */
+    /* slot, the higher one is freed and its children move to the survivor. */
+    int d1 = c & 0xffff, d2 = c >> 16;
+    int q = t->parent[d1];
+    int keep = d1 < d2 ? d1 : d2, gone = d1 < d2 ? d2 : d1;
+    int32_t* xp = t->content + (size_t)q * S;
+    const int32_t *w1 = t->wrap + (size_t)d1 * S, *x1 = t->content + (size_t)d1 * S;
+    const int32_t *w2 = t->wrap + (size_t)d2 * S, *x2 = t->content + (size_t)d2 * S;
+    for (int s = 0; s < S; s++) {
+      if (!fits((int64_t)xp[s] + rhs[s] - lhs[s])) return ST_INT_OVERFLOW;
+      if (!fits((int64_t)w1[s] - lhs[S + s] + (int64_t)w2[s] - lhs[3 * S + s] + rhs[S + s])) return ST_INT_OVERFLOW;
+      if (!fits((int64_t)x1[s] - lhs[2 * S + s] + (int64_t)x2[s] - lhs[4 * S + s] + rhs[2 * S + s]))
+        return ST_INT_OVERFLOW;
+    }
+    for (int s = 0; s < S; s++) {
+      int32_t wm = w1[s] - lhs[S + s] + w2[s] - lhs[3 * S + s] + rhs[S + s];
+      int32_t xm = x1[s] - lhs[2 * S + s] + x2[s] - lhs[4 * S + s] + rhs[2 * S + s];
+      xp[s] = xp[s] + rhs[s] - lhs[s];
+      t->wrap[(size_t)keep * S + s] = wm;
+      t->content[(size_t)keep * S + s] = xm;
+      t->wrap[(size_t)gone * S + s] = 0;
+      t->content[(size_t)gone * S + s] = 0;
+    }
+    for (int d = 0; d < t->C; d++)
+      if (t->alive[d] && t->parent[d] == gone) t->parent[d] = keep;
+    t->alive[gone] = 0;
+    t->label[gone] = 0;
+    t->parent[gone] = -1;
+    return ST_OK;
+  }
   if (kind == K_LOCAL) {
     int32_t* x = t->content + (size_t)c * S;
     for (int s = 0; s < S; s++)
@@ -575,9 +709,11 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
   const int S = m->S, C = m->C, M = m->M, O = num_obs(m);
   if (S < 1 || C < 1 || M < 1 || m->L < 1) return -1;
   for (int j = 0; j < M; j++) {
-    if (m->kind[j] < 0 || m->kind[j] > 3) return -1;
+    if (m->kind[j] < 0 || m->kind[j] > 5) return -1;
     if (m->ctx_label[j] < 0 || m->ctx_label[j] >= m->L) return -1;
     if (m->kind[j] != K_LOCAL && (m->child_label[j] < 1 || m->child_label[j] >= m->L)) return -1;
+    if (m->kind[j] == K_NESTED && (m->grand_label == NULL || m->grand_label[j] < 1 || m->grand_label[j] >= m->L))
+      return -1;
   }
   term_t t;
   t.S = S;
@@ -677,7 +813,18 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
       uint64_t xc = (uint64_t)(((unsigned __int128)W * (unsigned __int128)(uint64_t)x.H[j]) >> 64);
       int ctx = -1;
       uint64_t cum = 0;
-      for (int c = 0; c < C; c++) {
+      if (m->kind[j] == K_FUSION) {
+        /* pairs in ascending (d1, d2) order; the context id is d1 | d2 << 16 */
+        for (int d1 = 0; d1 < C && ctx < 0; d1++)
+          for (int d2 = 0; d2 < C; d2++) {
+            if (!is_pair(m, &t, j, d1, d2)) continue;
+            int64_t hc;
+            pair_count(m, &t, j, d1, d2, &hc);
+            cum += (uint64_t)hc;
+            if (xc < cum) { ctx = d1 | (d2 << 16); break; }
+          }
+      }
+      for (int c = 0; c < C && m->kind[j] != K_FUSION; c++) {
         if (!is_context(m, &t, j, c)) continue;
         int64_t hc;
         match_count(m, &t, j, c, &hc);

@@ -21,10 +21,19 @@ Model representation (the restricted CWC rule language of Sec. 2.1-2.2):
                    to a wrap, transport in and out);
   ``CREATE``       ``l: p X -> p' X (w' | q')^l'`` makes a new compartment;
   ``DISSOLVE``     ``l: p X (w x | q Y)^l' -> p' X x Y`` removes a child and
-                   releases its remaining wrap and content into the parent.
+                   releases its remaining wrap and content into the parent;
+  ``FUSION``       ``l: p X (w1 x1 | q1 Y1)^l' (w2 x2 | q2 Y2)^l' ->
+                   p' X (w' x1 x2 | q' Y1 Y2)^l'`` merges two sibling
+                   compartments (two compartments in one left-hand side);
+  ``NESTED``       ``l: p X (w x | q Y (v z | u Z)^l'')^l' ->
+                   p' X (w' x | q' Y (v' z | u' Z)^l'')^l'`` rewrites a
+                   compartment two levels down together with its parent and
+                   grandparent (a pattern of depth two).
 * ``lhs[j, 0/1/2, :]`` are the multiplicities of the parent (context)
   content, child wrap and child content patterns; ``rhs`` the same for the
-  right-hand side.
+  right-hand side.  ``lhs_ext[j, 0/1, :]`` (and ``rhs_ext``) are rows 3 and 4:
+  the second child's wrap and content (FUSION) or the grandchild's wrap and
+  content (NESTED); ``grand_label[j]`` is NESTED's grandchild label.
 
 Flat mass-action networks are the special case ``L = 1``, ``C = 1`` and only
 ``LOCAL`` rules on label 0.
@@ -39,8 +48,9 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-LOCAL, PARENT_CHILD, CREATE, DISSOLVE = 0, 1, 2, 3
-KIND_NAMES = {LOCAL: "LOCAL", PARENT_CHILD: "PARENT_CHILD", CREATE: "CREATE", DISSOLVE: "DISSOLVE"}
+LOCAL, PARENT_CHILD, CREATE, DISSOLVE, FUSION, NESTED = 0, 1, 2, 3, 4, 5
+KIND_NAMES = {LOCAL: "LOCAL", PARENT_CHILD: "PARENT_CHILD", CREATE: "CREATE", DISSOLVE: "DISSOLVE",
+              FUSION: "FUSION", NESTED: "NESTED"}
 
 _MASK64 = (1 << 64) - 1
 
@@ -102,6 +112,25 @@ class Model:
     lhs: np.ndarray           # int32 [M, 3, S]
     rhs: np.ndarray           # int32 [M, 3, S]
     name: str = ""
+    grand_label: Optional[np.ndarray] = None   # int32 [M] (-1 unless NESTED), or None
+    lhs_ext: Optional[np.ndarray] = None       # int32 [M, 2, S] rows 3 and 4, or None
+    rhs_ext: Optional[np.ndarray] = None       # int32 [M, 2, S]
+
+    @property
+    def has_ext(self) -> bool:
+        return self.lhs_ext is not None
+
+    def rows5(self) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(lhs [M, 5, S], rhs [M, 5, S], grand_label [M]) with rows 3-4 zero
+        and grand labels -1 when the model has no FUSION / NESTED rule."""
+        M, S = self.n_rules, self.n_species
+        z = np.zeros((M, 2, S), np.int32)
+        le = z if self.lhs_ext is None else np.asarray(self.lhs_ext, np.int32)
+        re = z if self.rhs_ext is None else np.asarray(self.rhs_ext, np.int32)
+        gl = np.full(M, -1, np.int32) if self.grand_label is None else np.asarray(self.grand_label, np.int32)
+        return (np.ascontiguousarray(np.concatenate([self.lhs, le], axis=1), np.int32),
+                np.ascontiguousarray(np.concatenate([self.rhs, re], axis=1), np.int32),
+                np.ascontiguousarray(gl, np.int32))
 
     @property
     def n_rules(self) -> int:
@@ -119,13 +148,13 @@ class Model:
         return L * S + (L - 1) * S + L
 
     def contiguous(self) -> "Model":
+        def c(a):
+            return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
         return dataclasses.replace(
             self,
-            kind=np.ascontiguousarray(self.kind, dtype=np.int32),
-            ctx_label=np.ascontiguousarray(self.ctx_label, dtype=np.int32),
-            child_label=np.ascontiguousarray(self.child_label, dtype=np.int32),
-            lhs=np.ascontiguousarray(self.lhs, dtype=np.int32),
-            rhs=np.ascontiguousarray(self.rhs, dtype=np.int32),
+            kind=c(self.kind), ctx_label=c(self.ctx_label), child_label=c(self.child_label),
+            lhs=c(self.lhs), rhs=c(self.rhs), grand_label=c(self.grand_label),
+            lhs_ext=c(self.lhs_ext), rhs_ext=c(self.rhs_ext),
         )
 
 
@@ -157,6 +186,12 @@ class RuleSpec:
     rhs_ctx: Dict[int, int] = dataclasses.field(default_factory=dict)
     rhs_wrap: Dict[int, int] = dataclasses.field(default_factory=dict)
     rhs_child: Dict[int, int] = dataclasses.field(default_factory=dict)
+    # rows 3 and 4: the second child (FUSION) or the grandchild (NESTED)
+    lhs_wrap2: Dict[int, int] = dataclasses.field(default_factory=dict)
+    lhs_child2: Dict[int, int] = dataclasses.field(default_factory=dict)
+    rhs_wrap2: Dict[int, int] = dataclasses.field(default_factory=dict)
+    rhs_child2: Dict[int, int] = dataclasses.field(default_factory=dict)
+    grand_label: int = -1
 
 
 def cwc_model(n_species: int, n_labels: int, max_compartments: int,
@@ -167,15 +202,30 @@ def cwc_model(n_species: int, n_labels: int, max_compartments: int,
     kind = np.zeros(M, np.int32)
     ctx = np.zeros(M, np.int32)
     child = np.full(M, -1, np.int32)
+    ext = any(r.kind in (FUSION, NESTED) or r.lhs_wrap2 or r.lhs_child2 or r.rhs_wrap2 or r.rhs_child2
+              for r in rules)
+    lhs_ext = np.zeros((M, 2, n_species), np.int32)
+    rhs_ext = np.zeros((M, 2, n_species), np.int32)
+    grand = np.full(M, -1, np.int32)
     for j, r in enumerate(rules):
         kind[j], ctx[j], child[j] = r.kind, r.ctx_label, r.child_label
+        grand[j] = r.grand_label
         for k, d in enumerate((r.lhs_ctx, r.lhs_wrap, r.lhs_child)):
             for s, c in d.items():
                 lhs[j, k, s] += c
         for k, d in enumerate((r.rhs_ctx, r.rhs_wrap, r.rhs_child)):
             for s, c in d.items():
                 rhs[j, k, s] += c
-    return Model(n_species, n_labels, max_compartments, kind, ctx, child, lhs, rhs, name)
+        for k, d in enumerate((r.lhs_wrap2, r.lhs_child2)):
+            for s, c in d.items():
+                lhs_ext[j, k, s] += c
+        for k, d in enumerate((r.rhs_wrap2, r.rhs_child2)):
+            for s, c in d.items():
+                rhs_ext[j, k, s] += c
+    if not ext:
+        return Model(n_species, n_labels, max_compartments, kind, ctx, child, lhs, rhs, name)
+    return Model(n_species, n_labels, max_compartments, kind, ctx, child, lhs, rhs, name,
+                 grand_label=grand, lhs_ext=lhs_ext, rhs_ext=rhs_ext)
 
 
 # ----------------------------------------------------------------------------

@@ -89,7 +89,14 @@ def lr_vs_fd(batch, G_ups, rel=0.05, chunk=16384):
         diff = (per[0] - per[1]) / (2.0 * d)                                     # [R, K]
         fd[:, j] = diff.mean(dim=0).cpu().numpy()
         fd_se[:, j] = (diff.std(dim=0) / math.sqrt(R)).cpu().numpy()
-    z = (lr - fd) / np.sqrt(lr_se ** 2 + fd_se ** 2)
+    se = np.sqrt(lr_se ** 2 + fd_se ** 2)
+    # a rule that never fires and never reaches the observables has a score
+    # and a finite difference of exactly zero, each with zero error: those
+    # entries must agree exactly and carry no z-score
+    exact = se == 0.0
+    assert np.all(lr[exact] == 0.0) and np.all(fd[exact] == 0.0)
+    z = np.where(exact, 0.0, (lr - fd) / np.where(exact, 1.0, se))
+    print("entries with zero error on both sides (exactly 0 = 0): %d" % int(exact.sum()))
     return z, lr, fd
 
 
