@@ -60,14 +60,28 @@ enum {
   CWC_TRAJ_TIMEOUT = 7        /* the call's deadline passed                        */
 };
 
-/* Rule kinds of the restricted CWC language (Sec. 2.1 rule application:
- * the left-hand side is matched against the content, or the wrap, of a
+/* Rule kinds of the CWC language this library runs (Sec. 2.1 rule
+ * application: the left-hand side, a pattern that may itself hold
+ * compartments, is matched against the content, or the wrap, of a
  * compartment of the rule's label). */
 enum {
   CWC_RULE_LOCAL = 0,        /* l: p X -> p' X                               */
   CWC_RULE_PARENT_CHILD = 1, /* l: p X (w x | q Y)^l' -> p' X (w' x | q' Y)^l' */
   CWC_RULE_CREATE = 2,       /* l: p X -> p' X (w' | q')^l'                  */
-  CWC_RULE_DISSOLVE = 3      /* l: p X (w x | q Y)^l' -> p' X x Y            */
+  CWC_RULE_DISSOLVE = 3,     /* l: p X (w x | q Y)^l' -> p' X x Y            */
+  CWC_RULE_FUSION = 4,       /* two compartments in one left-hand side:
+                                l: p X (w1 x1 | q1 Y1)^l' (w2 x2 | q2 Y2)^l'
+                                   -> p' X (w' x1 x2 | q' Y1 Y2)^l'
+                                contexts: ordered pairs of sibling l' slots
+                                (unordered when the two compartment patterns
+                                are identical); the lower slot keeps the merged
+                                compartment, the other is freed and its
+                                children move to the survivor                */
+  CWC_RULE_NESTED = 5        /* a pattern of depth two:
+                                l: p X (w x | q Y (v z | u Z)^l'')^l'
+                                   -> p' X (w' x | q' Y (v' z | u' Z)^l'')^l'
+                                contexts: grandchild slots of label l'' under
+                                a slot of label l' under one of label l     */
 };
 
 /*
@@ -83,6 +97,13 @@ enum {
  *   uses lhs row 0 and rhs rows 0..2 (rows 1, 2 = the new compartment's wrap
  *   and content); DISSOLVE uses lhs rows 0..2 and rhs row 0.  At most four
  *   species with a nonzero left-hand multiplicity per rule.
+ *   FUSION and NESTED rules need two more pattern rows and a third label
+ *   (all three pointers may be NULL when no rule is of those kinds):
+ *   grand_label[M] in [1, L) for NESTED (ignored otherwise);
+ *   lhs_ext[M][2][S] (in {0, 1, 2}) and rhs_ext[M][2][S] (<= 1000): rows 3
+ *   and 4, the second child's wrap and content (FUSION, whose rhs rows 3, 4
+ *   must be 0; its rhs rows 1, 2 are added to the merged wrap and content)
+ *   or the grandchild's wrap and content (NESTED).
  * Flat mass-action networks are L = 1, C = 1, all rules LOCAL on label 0.
  */
 typedef struct {
@@ -95,6 +116,9 @@ typedef struct {
   const int32_t* child_label;
   const int32_t* lhs;
   const int32_t* rhs;
+  const int32_t* grand_label;   /* [M] or NULL */
+  const int32_t* lhs_ext;       /* [M][2][S] or NULL */
+  const int32_t* rhs_ext;       /* [M][2][S] or NULL */
 } cwc_model_desc;
 
 typedef struct cwc_model cwc_model;
@@ -166,7 +190,9 @@ enum {
  *                                      applied event, little-endian uint32s
  *   traj_final_t  double [P][R]        time of the last applied event
  *   log_rule/log_slot int32, log_t double [P][R][log_cap]: the first log_cap
- *                                      events of each trajectory
+ *                                      events of each trajectory (the slot is
+ *                                      the context; for FUSION the pair
+ *                                      d1 | d2 << 16, also in the hash)
  *
  *   checkpoint    int32 [P][R][cwc_checkpoint_words()]  the state of each
  *                 trajectory when it stops: time, event hash, event count,

@@ -22,10 +22,15 @@ class CompiledModel:
     def __init__(self, model: Model):
         m = model.contiguous()
         self.model = m
-        self._keep = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs)
+        self._keep = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs, m.grand_label, m.lhs_ext, m.rhs_ext)
+
+        def ptr(a):
+            return None if a is None else a.ctypes.data
+
         desc = capi.cwc_model_desc(m.n_species, m.n_labels, m.n_rules, m.max_compartments,
                                    m.kind.ctypes.data, m.ctx_label.ctypes.data, m.child_label.ctypes.data,
-                                   m.lhs.ctypes.data, m.rhs.ctypes.data)
+                                   m.lhs.ctypes.data, m.rhs.ctypes.data,
+                                   ptr(m.grand_label), ptr(m.lhs_ext), ptr(m.rhs_ext))
         self.handle = capi.cwc_model_create(desc)
         self.n_observables = capi.cwc_model_num_observables(self.handle)
         self.flat = m.n_labels == 1 and m.max_compartments == 1

@@ -53,6 +53,7 @@ struct cwc_model {
   // compartmentalised compilation
   int O = 0;
   int c_n_deps = 0;
+  bool general = false;          // some rule is FUSION or NESTED
   int32_t* d_ctables = nullptr;  // [M][CWC_RULE_WORDS] followed by [c_n_deps]
   std::vector<int32_t> h_ctables;
 };
@@ -120,6 +121,7 @@ CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a, bool sens)
   prm.B = m->B;
   prm.O = m->O;
   prm.n_deps = m->c_n_deps;
+  prm.general = m->general ? 1 : 0;
   prm.Q = (long long)a->P * a->R;
   prm.smem_table_bytes = cwc_table_bytes_host(m->M, m->c_n_deps);
   prm.sens = sens ? 1 : 0;
@@ -320,33 +322,59 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
     return fail(CWC_ERR_INVALID_ARG, "sizes out of range (1<=S<=4096, 1<=L<=64, 1<=M<=65535, 1<=C<=1024)");
   if (!d->kind || !d->ctx_label || !d->child_label || !d->lhs || !d->rhs)
     return fail(CWC_ERR_INVALID_ARG, "rule arrays must not be NULL");
+  // pattern row r (0..4) of rule j: rows 0-2 from lhs / rhs, rows 3-4 from
+  // the extension arrays (all zero when those are NULL)
+  auto lrow = [&](int j, int r) -> const int32_t* {
+    if (r < 3) return d->lhs + ((size_t)j * 3 + r) * S;
+    return d->lhs_ext ? d->lhs_ext + ((size_t)j * 2 + (r - 3)) * S : nullptr;
+  };
+  auto rrow = [&](int j, int r) -> const int32_t* {
+    if (r < 3) return d->rhs + ((size_t)j * 3 + r) * S;
+    return d->rhs_ext ? d->rhs_ext + ((size_t)j * 2 + (r - 3)) * S : nullptr;
+  };
+  auto row_nonzero = [&](const int32_t* row) {
+    if (row == nullptr) return false;
+    for (int x = 0; x < S; ++x)
+      if (row[x] != 0) return true;
+    return false;
+  };
   for (int j = 0; j < M; ++j) {
     const int k = d->kind[j];
-    if (k < CWC_RULE_LOCAL || k > CWC_RULE_DISSOLVE) return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": bad kind");
-    if (d->ctx_label[j] < 0 || d->ctx_label[j] >= L)
-      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": ctx_label out of range");
+    const std::string rj = "rule " + std::to_string(j);
+    if (k < CWC_RULE_LOCAL || k > CWC_RULE_NESTED) return fail(CWC_ERR_INVALID_ARG, rj + ": bad kind");
+    if (d->ctx_label[j] < 0 || d->ctx_label[j] >= L) return fail(CWC_ERR_INVALID_ARG, rj + ": ctx_label out of range");
     if (k != CWC_RULE_LOCAL && (d->child_label[j] < 1 || d->child_label[j] >= L))
-      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": child_label out of [1, L)");
-    const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
-    const int32_t* rhs = d->rhs + (size_t)j * 3 * S;
+      return fail(CWC_ERR_INVALID_ARG, rj + ": child_label out of [1, L)");
+    if ((k == CWC_RULE_FUSION || k == CWC_RULE_NESTED) && (d->lhs_ext == nullptr || d->rhs_ext == nullptr))
+      return fail(CWC_ERR_INVALID_ARG, rj + ": FUSION and NESTED rules need lhs_ext and rhs_ext");
+    if (k == CWC_RULE_NESTED && (d->grand_label == nullptr || d->grand_label[j] < 1 || d->grand_label[j] >= L))
+      return fail(CWC_ERR_INVALID_ARG, rj + ": NESTED needs grand_label in [1, L)");
     int factors = 0;
-    for (int i = 0; i < 3 * S; ++i) {
-      if (lhs[i] < 0 || lhs[i] > 2) return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": lhs entries must be 0, 1 or 2");
-      if (rhs[i] < 0 || rhs[i] > 1000) return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": rhs entries must be in [0, 1000]");
-      factors += lhs[i] != 0;
+    for (int r = 0; r < 5; ++r) {
+      const int32_t* lo = lrow(j, r);
+      const int32_t* hi = rrow(j, r);
+      for (int x = 0; x < S; ++x) {
+        const int lv = lo ? lo[x] : 0, hv = hi ? hi[x] : 0;
+        if (lv < 0 || lv > 2) return fail(CWC_ERR_INVALID_ARG, rj + ": lhs entries must be 0, 1 or 2");
+        if (hv < 0 || hv > 1000) return fail(CWC_ERR_INVALID_ARG, rj + ": rhs entries must be in [0, 1000]");
+        factors += lv != 0;
+      }
     }
-    if (factors > MAX_REAC) return fail(CWC_ERR_UNSUPPORTED, "rule " + std::to_string(j) + ": more than 4 reactant species");
-    bool lhs_child = false, rhs_child = false;
-    for (int i = S; i < 3 * S; ++i) {
-      lhs_child |= lhs[i] != 0;
-      rhs_child |= rhs[i] != 0;
-    }
+    if (factors > MAX_REAC) return fail(CWC_ERR_UNSUPPORTED, rj + ": more than 4 reactant species");
+    const bool lhs_child = row_nonzero(lrow(j, 1)) || row_nonzero(lrow(j, 2));
+    const bool rhs_child = row_nonzero(rrow(j, 1)) || row_nonzero(rrow(j, 2));
+    const bool lhs_more = row_nonzero(lrow(j, 3)) || row_nonzero(lrow(j, 4));
+    const bool rhs_more = row_nonzero(rrow(j, 3)) || row_nonzero(rrow(j, 4));
     if (k == CWC_RULE_LOCAL && (lhs_child || rhs_child))
-      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": LOCAL rules use row 0 only");
+      return fail(CWC_ERR_INVALID_ARG, rj + ": LOCAL rules use row 0 only");
     if (k == CWC_RULE_CREATE && lhs_child)
-      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": CREATE matches the context content only");
+      return fail(CWC_ERR_INVALID_ARG, rj + ": CREATE matches the context content only");
     if (k == CWC_RULE_DISSOLVE && rhs_child)
-      return fail(CWC_ERR_INVALID_ARG, "rule " + std::to_string(j) + ": DISSOLVE writes the parent content only");
+      return fail(CWC_ERR_INVALID_ARG, rj + ": DISSOLVE writes the parent content only");
+    if (k <= CWC_RULE_DISSOLVE && (lhs_more || rhs_more))
+      return fail(CWC_ERR_INVALID_ARG, rj + ": pattern rows 3-4 belong to FUSION and NESTED rules");
+    if (k == CWC_RULE_FUSION && rhs_more)
+      return fail(CWC_ERR_INVALID_ARG, rj + ": FUSION writes the merged wrap and content through rhs rows 1-2");
   }
   cwc_model* m = new cwc_model();
   m->S = S;
@@ -372,40 +400,57 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
     // read and write sets: location key = ((role * L) + label) * S + species, role 0 content, 1 wrap
     auto key = [&](int role, int lab, int sp) { return ((long long)role * L + lab) * S + sp; };
     std::vector<std::vector<long long>> reads(M), writes(M);
+    std::vector<std::pair<int, std::vector<int32_t>>> nested_ext;
     for (int j = 0; j < M; ++j) {
-      const int32_t* lhs = d->lhs + (size_t)j * 3 * S;
-      const int32_t* rhs = d->rhs + (size_t)j * 3 * S;
       const int kind = d->kind[j], ctx = d->ctx_label[j], ch = d->child_label[j];
+      const int gr = kind == CWC_RULE_NESTED ? d->grand_label[j] : 0;
+      m->general |= kind == CWC_RULE_FUSION || kind == CWC_RULE_NESTED;
       int32_t* rec = tb.data() + (size_t)j * CWC_RULE_WORDS;
       rec[CR_KIND] = kind;
       rec[CR_CTX] = ctx;
       rec[CR_CHILD] = kind == CWC_RULE_LOCAL ? 0 : ch;
+      rec[CR_GRAND] = gr;   // the extension offset is added below
+      // the (role, label) each pattern row reads
+      const int row_role[5] = {0, 1, 0, 1, 0};
+      const int row_label[5] = {ctx, ch, ch, kind == CWC_RULE_NESTED ? gr : ch, kind == CWC_RULE_NESTED ? gr : ch};
       int nr = 0;
-      for (int row = 0; row < 3; ++row)
-        for (int s = 0; s < S; ++s)
-          if (lhs[row * S + s] > 0) {
-            rec[CR_REAC + nr++] = s | (lhs[row * S + s] << 16) | (row << 24);
-            const bool child_row = row > 0;
-            reads[j].push_back(key(row == 1 ? 1 : 0, child_row ? ch : ctx, s));
+      for (int row = 0; row < 5; ++row) {
+        const int32_t* lo = lrow(j, row);
+        if (lo == nullptr) continue;
+        for (int sp = 0; sp < S; ++sp)
+          if (lo[sp] > 0) {
+            rec[CR_REAC + nr++] = sp | (lo[sp] << 16) | (row << 24);
+            reads[j].push_back(key(row_role[row], row_label[row], sp));
           }
+      }
       rec[CR_NREAC] = nr;
-      auto put = [&](int base_n, int base_d, int row_delta_only, const int32_t* lo, const int32_t* hi, bool values) -> bool {
+      // change lists: species | delta << 16 (values = the rhs row itself)
+      // a change list at dst: count at dst[base_n], entries from dst[base_d]
+      auto put = [&](int32_t* dst, int base_n, int base_d, const int32_t* lo, const int32_t* hi, bool values) -> bool {
         int k = 0;
-        for (int s = 0; s < S; ++s) {
-          const int dv = values ? hi[s] : hi[s] - lo[s];
+        for (int sp = 0; sp < S; ++sp) {
+          const int dv = values ? (hi ? hi[sp] : 0) : (hi ? hi[sp] : 0) - (lo ? lo[sp] : 0);
           if (dv == 0) continue;
           if (k == MAX_DELTA) return false;
-          rec[base_d + k++] = (int32_t)((uint32_t)s | ((uint32_t)(dv & 0xffff) << 16));
+          dst[base_d + k++] = (int32_t)((uint32_t)sp | ((uint32_t)(dv & 0xffff) << 16));
         }
-        rec[base_n] = k;
-        (void)row_delta_only;
+        dst[base_n] = k;
         return true;
       };
-      bool ok = put(CR_ND0, CR_D0, 0, lhs, rhs, false);
-      if (kind == CWC_RULE_PARENT_CHILD) {
-        ok = ok && put(CR_ND1, CR_D1, 1, lhs + S, rhs + S, false) && put(CR_ND2, CR_D2, 2, lhs + 2 * S, rhs + 2 * S, false);
-      } else if (kind == CWC_RULE_CREATE) {
-        ok = ok && put(CR_ND1, CR_D1, 1, nullptr, rhs + S, true) && put(CR_ND2, CR_D2, 2, nullptr, rhs + 2 * S, true);
+      bool ok = put(rec, CR_ND0, CR_D0, lrow(j, 0), rrow(j, 0), false);
+      if (kind == CWC_RULE_PARENT_CHILD || kind == CWC_RULE_NESTED) {
+        ok = ok && put(rec, CR_ND1, CR_D1, lrow(j, 1), rrow(j, 1), false) &&
+             put(rec, CR_ND2, CR_D2, lrow(j, 2), rrow(j, 2), false);
+      } else if (kind == CWC_RULE_CREATE || kind == CWC_RULE_FUSION) {
+        ok = ok && put(rec, CR_ND1, CR_D1, nullptr, rrow(j, 1), true) && put(rec, CR_ND2, CR_D2, nullptr, rrow(j, 2), true);
+      }
+      if (kind == CWC_RULE_NESTED) {
+        // rows 3-4 of NESTED go to an extension record after the dependency
+        // list; its offset is known once the list is, so keep it aside
+        nested_ext.emplace_back(j, std::vector<int32_t>(XR_WORDS, 0));
+        int32_t* xr = nested_ext.back().second.data();
+        ok = ok && put(xr, XR_ND3, XR_D3, lrow(j, 3), rrow(j, 3), false) &&
+             put(xr, XR_ND4, XR_D4, lrow(j, 4), rrow(j, 4), false);
       }
       if (!ok) {
         delete m;
@@ -418,19 +463,22 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       }
     }
     std::vector<int32_t> deps_all;
+    auto general = [&](int kind) { return kind == CWC_RULE_FUSION || kind == CWC_RULE_NESTED; };
     for (int j = 0; j < M; ++j) {
       int32_t* rec = tb.data() + (size_t)j * CWC_RULE_WORDS;
       rec[CR_DEPOFF] = (int32_t)deps_all.size();
       uint32_t leafmask = 0, nodemask = 0;
       int cnt = 0;
       // rule i depends on rule j when j writes a location i reads, or when j
-      // adds, removes or re-parents a compartment that can be a context of i
+      // adds, removes or re-parents a compartment that can be a context of i.
+      // FUSION and NESTED rules are recounted after every event, and after a
+      // FUSION or NESTED event every rule is recounted.
       const int kj = d->kind[j], lj = d->ctx_label[j], cj = d->child_label[j];
       {
         for (int i = 0; i < M; ++i) {
           const int ki = d->kind[i], li = d->ctx_label[i], ci = d->child_label[i];
           const bool local_i = ki == CWC_RULE_LOCAL || ki == CWC_RULE_CREATE;
-          bool hit = false;
+          bool hit = general(kj) || general(ki);
           for (long long w : writes[j])
             for (long long r : reads[i]) hit |= (w == r);
           if (kj == CWC_RULE_CREATE)   // a new compartment of label cj under one of label lj
@@ -454,7 +502,13 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       rec[CR_LEAFMASK] = (int32_t)leafmask;
       rec[CR_NODEMASK] = (int32_t)nodemask;
     }
-    m->c_n_deps = (int)deps_all.size();
+    for (auto& ne : nested_ext) {
+      int32_t* rec = tb.data() + (size_t)ne.first * CWC_RULE_WORDS;
+      const long long off = (long long)M * CWC_RULE_WORDS + (long long)deps_all.size();
+      rec[CR_GRAND] = (rec[CR_GRAND] & 0xff) | (int32_t)(off << 8);
+      deps_all.insert(deps_all.end(), ne.second.begin(), ne.second.end());
+    }
+    m->c_n_deps = (int)deps_all.size();   // the dependency lists, then the NESTED extensions
     tb.insert(tb.end(), deps_all.begin(), deps_all.end());
     if ((size_t)cwc_table_bytes_host(M, m->c_n_deps) + 32ull * (32 + TREE_NODES + M) * 8 > 220 * 1024) {
       delete m;

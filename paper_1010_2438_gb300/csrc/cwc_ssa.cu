@@ -126,7 +126,7 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
                                                         const int32_t* __restrict__ meta, int S,
                                                         const int32_t* rec, unsigned long long m) {
   const int kind = rec[CR_KIND];
-  const bool parent_child = !(kind == 0 || kind == 2);
+  const bool parent_child = !(kind == RK_LOCAL || kind == RK_CREATE);
   const int nr = rec[CR_NREAC];
   const int ctx = rec[CR_CTX];
   bool of = false;
@@ -134,20 +134,32 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
   while (m) {
     const int c = __ffsll((long long)m) - 1;
     m &= m - 1ull;
-    int x0c = c;
-    if (parent_child) {
+    // slots read by pattern rows 0 / 1-2 / 3-4
+    int x0c = c, x12c = c;
+    if (kind == RK_NESTED) {
+      // c is the grandchild: its parent must carry the child label, its
+      // grandparent the rule's label (the root's label 0 is never a child label)
+      const int qq = (meta[c] >> 8) - 1;
+      if ((meta[qq] & 0xff) != rec[CR_CHILD]) continue;
+      const int aa = (meta[qq] >> 8) - 1;
+      if ((meta[aa] & 0xff) != ctx) continue;
+      x0c = aa;
+      x12c = qq;
+    } else if (parent_child) {
       const int qq = (meta[c] >> 8) - 1;
       if ((meta[qq] & 0xff) != ctx) continue;
       x0c = qq;
     }
     const int32_t* x0 = content + (size_t)x0c * S;
-    const int32_t* x1 = wrap + (size_t)c * S;
-    const int32_t* x2 = content + (size_t)c * S;
+    const int32_t* x1 = wrap + (size_t)x12c * S;
+    const int32_t* x2 = content + (size_t)x12c * S;
+    const int32_t* x3 = wrap + (size_t)c * S;
+    const int32_t* x4 = content + (size_t)c * S;
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
-      const int row = (v >> 24) & 3;
-      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
+      const int row = (v >> 24) & 7;
+      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : (row == 2 ? x2 : (row == 3 ? x3 : x4)));
       acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
     }
     const unsigned long long s2 = tot + acc;
@@ -155,6 +167,193 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
     tot = s2;
   }
   return of ? (tot | (1ull << 63)) : tot;
+}
+
+// FUSION: the occurrences over ordered pairs (d1, d2) of distinct sibling
+// slots of the child label under a parent of the rule's label (d1 < d2 when
+// the two compartment patterns are identical), multiplied in the oracle's
+// order: parent content, first child's wrap and content (rows 0-2), second
+// child's wrap and content (rows 3-4).  With want_pick, returns the first
+// pair in ascending (d1, d2) order whose running sum exceeds xc, as
+// d1 | d2 << 16 (the last positive pair if none does); otherwise the sum,
+// bit 63 flagging an overflow of a product or of the sum.
+__device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __restrict__ content,
+                                                          const int32_t* __restrict__ wrap,
+                                                          const int32_t* __restrict__ meta, int S,
+                                                          const int32_t* rec, unsigned long long kids,
+                                                          bool want_pick, unsigned long long xc) {
+  const int nr = rec[CR_NREAC];
+  const int ctx = rec[CR_CTX];
+  // identical compartment patterns: rows 1 / 3 and 2 / 4 hold the same entries
+  bool sym = true;
+  for (int a = 0; a < nr; ++a) {
+    const int v = rec[CR_REAC + a];
+    const int row = (v >> 24) & 7;
+    if (row == 0) continue;
+    const int twin_row = row == 1 ? 3 : row == 2 ? 4 : row == 3 ? 1 : 2;
+    bool found = false;
+    for (int b = 0; b < nr; ++b) {
+      const int u = rec[CR_REAC + b];
+      found |= ((u >> 24) & 7) == twin_row && (u & 0xffffff) == (v & 0xffffff);
+    }
+    sym = sym && found;
+  }
+  bool of = false;
+  unsigned long long tot = 0ull;
+  unsigned long long last = 0ull;
+  unsigned long long m1 = kids;
+  while (m1) {
+    const int d1 = __ffsll((long long)m1) - 1;
+    m1 &= m1 - 1ull;
+    const int qq = (meta[d1] >> 8) - 1;
+    if ((meta[qq] & 0xff) != ctx) continue;
+    const int32_t* x0 = content + (size_t)qq * S;
+    unsigned long long m2 = kids & ~(1ull << d1);
+    if (sym) m2 &= ~((2ull << d1) - 1ull);   // d2 > d1 only
+    while (m2) {
+      const int d2 = __ffsll((long long)m2) - 1;
+      m2 &= m2 - 1ull;
+      if ((meta[d2] >> 8) - 1 != qq) continue;
+      unsigned long long acc = 1ull;
+      for (int a = 0; a < nr; ++a) {
+        const int v = rec[CR_REAC + a];
+        const int row = (v >> 24) & 7;
+        const int32_t* x = row == 0 ? x0
+                           : row == 1 ? wrap + (size_t)d1 * S
+                           : row == 2 ? content + (size_t)d1 * S
+                           : row == 3 ? wrap + (size_t)d2 * S : content + (size_t)d2 * S;
+        acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
+      }
+      const unsigned long long s2 = tot + acc;
+      if (s2 < tot || (s2 >> 63) != 0ull) of = true;
+      tot = s2;
+      if (want_pick && acc != 0ull) {
+        last = (unsigned long long)d1 | ((unsigned long long)d2 << 16);
+        if (xc < tot) return last;
+      }
+    }
+  }
+  if (want_pick) return last;
+  return of ? (tot | (1ull << 63)) : tot;
+}
+
+// The overflow check and the rewrite of the two-compartment (FUSION) and
+// depth-two (NESTED) rules, out of line (rare events; one copy shared by every
+// lane-group width).  ctx is the grandchild slot (NESTED) or d1 | d2 << 16
+// (FUSION: the lower slot keeps the merged compartment, the higher is freed
+// and its children move to the survivor).
+__device__ __noinline__ int cwc_general_check(const int32_t* content, const int32_t* wrap, const int32_t* meta, int S,
+                                              const int32_t* table, const int32_t* rec, int ctx) {
+  auto fits = [](long long v) { return v >= 0 && v <= 0x7FFFFFFFll; };
+  const int nr = rec[CR_NREAC];
+  if (rec[CR_KIND] == RK_NESTED) {
+    const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
+    const int32_t* xr = table + (rec[CR_GRAND] >> 8);
+    const int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
+                            wrap + (size_t)g * S, content + (size_t)g * S};
+    const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
+    const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
+    for (int row = 0; row < 5; ++row)
+      for (int d = 0; d < nd[row]; ++d) {
+        const int v = dd[row][d];
+        if (!fits((long long)ms[row][v & 0xffff] + (v >> 16))) return TS_INT_OVERFLOW;
+      }
+    return TS_OK;
+  }
+  const int d1 = ctx & 0xffff, d2 = ctx >> 16;
+  const int qq = (meta[d1] >> 8) - 1;
+  for (int d = 0; d < rec[CR_ND0]; ++d) {
+    const int v = rec[CR_D0 + d];
+    if (!fits((long long)content[(size_t)qq * S + (v & 0xffff)] + (v >> 16))) return TS_INT_OVERFLOW;
+  }
+  for (int x = 0; x < S; ++x) {
+    long long wv = (long long)wrap[(size_t)d1 * S + x] + wrap[(size_t)d2 * S + x];
+    long long cv = (long long)content[(size_t)d1 * S + x] + content[(size_t)d2 * S + x];
+    for (int a = 0; a < nr; ++a) {
+      const int v = rec[CR_REAC + a];
+      const int row = (v >> 24) & 7;
+      if ((v & 0xffff) != x) continue;
+      if (row == 1 || row == 3) wv -= (v >> 16) & 0xff;
+      if (row == 2 || row == 4) cv -= (v >> 16) & 0xff;
+    }
+    for (int d = 0; d < rec[CR_ND1]; ++d)
+      if ((rec[CR_D1 + d] & 0xffff) == x) wv += rec[CR_D1 + d] >> 16;
+    for (int d = 0; d < rec[CR_ND2]; ++d)
+      if ((rec[CR_D2 + d] & 0xffff) == x) cv += rec[CR_D2 + d] >> 16;
+    if (!fits(wv) || !fits(cv)) return TS_INT_OVERFLOW;
+  }
+  return TS_OK;
+}
+
+// O = L*S content totals, (L-1)*S wrap totals, L alive counts (see kernel)
+__device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, int32_t* meta,
+                                               unsigned long long* chmask, unsigned long long* labmask,
+                                               unsigned long long* alive_p, long long* tot, int S, int L,
+                                               const int32_t* table, const int32_t* rec, int ctx) {
+  auto OC = [&](int l, int x) { return l * S + x; };
+  auto OW = [&](int l, int x) { return L * S + (l - 1) * S + x; };
+  auto OA = [&](int l) { return L * S + (L - 1) * S + l; };
+  if (rec[CR_KIND] == RK_NESTED) {
+    const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
+    const int la = meta[aa] & 0xff, lq = meta[qq] & 0xff, lg = meta[g] & 0xff;
+    const int32_t* xr = table + (rec[CR_GRAND] >> 8);
+    int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
+                      wrap + (size_t)g * S, content + (size_t)g * S};
+    const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
+    const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
+    for (int row = 0; row < 5; ++row)
+      for (int d = 0; d < nd[row]; ++d) {
+        const int v = dd[row][d];
+        const int x = v & 0xffff, dv = v >> 16;
+        ms[row][x] += dv;
+        const int o = row == 0 ? OC(la, x) : row == 1 ? OW(lq, x) : row == 2 ? OC(lq, x) : row == 3 ? OW(lg, x) : OC(lg, x);
+        tot[o] += dv;
+      }
+    return;
+  }
+  const int d1 = ctx & 0xffff, d2 = ctx >> 16;
+  const int keep = d1 < d2 ? d1 : d2, gone = d1 < d2 ? d2 : d1;
+  const int qq = (meta[d1] >> 8) - 1;
+  const int lq = meta[qq] & 0xff, lc = meta[d1] & 0xff;
+  const int nr = rec[CR_NREAC];
+  for (int d = 0; d < rec[CR_ND0]; ++d) {
+    const int v = rec[CR_D0 + d];
+    content[(size_t)qq * S + (v & 0xffff)] += v >> 16;
+    tot[OC(lq, v & 0xffff)] += v >> 16;
+  }
+  for (int x = 0; x < S; ++x) {
+    int dw = 0, dc = 0;   // change of the label totals: - matched atoms + added atoms
+    for (int a = 0; a < nr; ++a) {
+      const int v = rec[CR_REAC + a];
+      const int row = (v >> 24) & 7;
+      if ((v & 0xffff) != x) continue;
+      if (row == 1 || row == 3) dw -= (v >> 16) & 0xff;
+      if (row == 2 || row == 4) dc -= (v >> 16) & 0xff;
+    }
+    for (int d = 0; d < rec[CR_ND1]; ++d)
+      if ((rec[CR_D1 + d] & 0xffff) == x) dw += rec[CR_D1 + d] >> 16;
+    for (int d = 0; d < rec[CR_ND2]; ++d)
+      if ((rec[CR_D2 + d] & 0xffff) == x) dc += rec[CR_D2 + d] >> 16;
+    wrap[(size_t)keep * S + x] = wrap[(size_t)keep * S + x] + wrap[(size_t)gone * S + x] + dw;
+    content[(size_t)keep * S + x] = content[(size_t)keep * S + x] + content[(size_t)gone * S + x] + dc;
+    wrap[(size_t)gone * S + x] = 0;
+    content[(size_t)gone * S + x] = 0;
+    tot[OW(lc, x)] += dw;
+    tot[OC(lc, x)] += dc;
+  }
+  tot[OA(lc)] -= 1;
+  unsigned long long kids = chmask[gone];
+  while (kids) {
+    const int e = __ffsll((long long)kids) - 1;
+    kids &= kids - 1ull;
+    meta[e] = (meta[e] & 0xff) | ((keep + 1) << 8);
+  }
+  chmask[keep] |= chmask[gone];
+  chmask[gone] = 0ull;
+  chmask[qq] &= ~(1ull << gone);
+  labmask[lc] &= ~(1ull << gone);
+  *alive_p &= ~(1ull << gone);
+  meta[gone] = 0;
 }
 
 // With lane groups a warp holds 8 or 4 terms on different paths and runs
@@ -231,7 +430,7 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
       const int nr = rec[CR_NREAC];
       for (int a = 0; a < nr; ++a) {
         const int v = rec[CR_REAC + a];
-        if (((v >> 24) & 3) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
+        if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
       const long long nv = (long long)xp[s] + dv;
       if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
@@ -239,7 +438,9 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
     return TS_OK;
 }
 
-template <int kL, bool kQueue, bool kSens>
+// kGen: the model has FUSION or NESTED rules (a separate instantiation, so
+// that the code of those kinds costs the other models no registers)
+template <int kL, bool kQueue, bool kSens, bool kGen>
 __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ CwcParams prm,
                                                       const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -333,9 +534,10 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // are stored by pattern row, then species, so one pass multiplies in the
   // oracle's order: row 0 (the context's or the parent's content), row 1
   // (the child's wrap), row 2 (the child's content).
+  // (kinds LOCAL .. DISSOLVE; NESTED counts go through cwc_count_sum)
   auto count_at = [&](const int32_t* rec, int c) -> unsigned long long {
     const int kind = rec[CR_KIND];
-    const int32_t* x0 = content + (size_t)((kind == 0 || kind == 2) ? c : PARENT(c)) * S;
+    const int32_t* x0 = content + (size_t)((kind == RK_LOCAL || kind == RK_CREATE) ? c : PARENT(c)) * S;
     const int32_t* x1 = wrap + (size_t)c * S;
     const int32_t* x2 = content + (size_t)c * S;
     const int nr = rec[CR_NREAC];
@@ -348,20 +550,22 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     return acc;
   };
-  // candidate contexts of rule i, in ascending slot order
+  // candidate contexts of rule i, in ascending slot order (FUSION: the slots
+  // its pairs are drawn from)
   auto ctx_mask = [&](const int32_t* rec) -> unsigned long long {
     const int kind = rec[CR_KIND];
-    return (kind == 0 || kind == 2) ? labmask[rec[CR_CTX]] : labmask[rec[CR_CHILD]];
+    if (kGen && kind == RK_NESTED) return labmask[rec[CR_GRAND] & 0xff];
+    return (kind == RK_LOCAL || kind == RK_CREATE) ? labmask[rec[CR_CTX]] : labmask[rec[CR_CHILD]];
   };
   auto ctx_ok = [&](const int32_t* rec, int c) -> bool {
     const int kind = rec[CR_KIND];
-    if (kind == 0 || kind == 2) return true;
+    if (kind == RK_LOCAL || kind == RK_CREATE) return true;
     return LABEL(PARENT(c)) == rec[CR_CTX];
   };
   // sum of the counts of a rule over the contexts in m (ascending slots),
   // overflow-checked like a from-scratch H
   auto partial_h = [&](const int32_t* rec, unsigned long long m) -> unsigned long long {
-    if (kL == 1) {
+    if (kL == 1 && !(kGen && rec[CR_KIND] == RK_NESTED)) {
       unsigned long long tot = 0ull;
       while (m) {
         const int c = __ffsll((long long)m) - 1;
@@ -381,6 +585,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // H_i from scratch: sum over all its contexts
   auto total_h = [&](int i) -> unsigned long long {
     const int32_t* rec = s_rules + i * CWC_RULE_WORDS;
+    if (kGen && rec[CR_KIND] == RK_FUSION) {
+      const unsigned long long r = cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), false, 0ull);
+      if (r >> 63) ovf = true;
+      return r & ~(1ull << 63);
+    }
     return partial_h(rec, ctx_mask(rec));
   };
   auto prop_of = [&](int i) -> double { return __dmul_rn(kp[i], u63_to_double_rn(HV(i))); };
@@ -663,7 +872,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const int nr = rec[CR_NREAC];
       for (int a = 0; a < nr; ++a) {
         const int v = rec[CR_REAC + a];
-        if (((v >> 24) & 3) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
+        if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
       const long long nv = (long long)xp[s] + dv;
       if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
@@ -767,7 +976,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int nr = rec[CR_NREAC];
         for (int a = 0; a < nr; ++a) {
           const int v = rec[CR_REAC + a];
-          const int row = (v >> 24) & 3;
+          const int row = (v >> 24) & 7;
           if (row != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
         }
         return dv;
@@ -804,7 +1013,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   auto choose_context = [&](const int32_t* rec, unsigned long long xc) -> int {
     const unsigned long long m = ctx_mask(rec);
     int ctx = -1, lastc = -1;
-    if (kL == 1) {
+    if (kL == 1 && !(kGen && rec[CR_KIND] == RK_NESTED)) {
       unsigned long long mm = m, cum = 0ull;
       while (mm) {
         const int c = __ffsll((long long)mm) - 1;
@@ -949,42 +1158,56 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const uint4 w1 = philox4x32_10(make_uint4(n, 1u, rr, (uint32_t)p), prm.key0, prm.key1);
     const unsigned long long Wd = (unsigned long long)w1.x | ((unsigned long long)w1.y << 32);
     const unsigned long long xc = __umul64hi(Wd, HV(j));
-    const int ctx = choose_context(rec, xc);
+    const int ctx = (kGen && rec[CR_KIND] == RK_FUSION)
+                        ? (int)cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), true, xc)
+                        : choose_context(rec, xc);
     // 3. update.  Only contexts in `touched` can change their counts: the
     // rewritten compartments, their children (which read the parent content),
     // and the free slots (one of which CREATE fills).  Each dependent rule
     // drops the old counts of its touched contexts and adds the new ones; a
     // rule whose contexts all lie in `touched` is summed afresh.
-    const int ast = kL > 1 ? cwc_apply_check(content, wrap, meta, *alive_p, S, C, rec, ctx) : apply_check(rec, ctx);
+    const bool general_j = kGen && (rec[CR_KIND] == RK_FUSION || rec[CR_KIND] == RK_NESTED);
+    const int ast = general_j ? cwc_general_check(content, wrap, meta, S, s_rules, rec, ctx)
+                    : kL > 1  ? cwc_apply_check(content, wrap, meta, *alive_p, S, C, rec, ctx)
+                              : apply_check(rec, ctx);
     if (ast != TS_OK) {
       status = ast;
       return 1;
     }
     const int kind_j = rec[CR_KIND];
-    unsigned long long touched = chmask[ctx];
-    if (kind_j == 0 || kind_j == 2) {
+    // FUSION and NESTED events touch every slot (every dependent is recounted)
+    unsigned long long touched = general_j ? ~0ull : chmask[ctx];
+    if (kind_j == RK_LOCAL || kind_j == RK_CREATE) {
       touched |= 1ull << ctx;
-      if (kind_j == 2) touched |= ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
-    } else {
+      if (kind_j == RK_CREATE) touched |= ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
+    } else if (!general_j) {
       const int qq = PARENT(ctx);
       touched |= (1ull << qq) | chmask[qq];
     }
     if (kSens && gl == 0) Nf[j] += 1;
     const int doff = rec[CR_DEPOFF], dcnt = rec[CR_DEPCNT];
+    // FUSION and NESTED dependents, whose contexts are pairs or grandchildren
+    // rather than the touched slots, are recounted in full after the rewrite
+    auto general_rule = [&](const int32_t* ri) { return kGen && (ri[CR_KIND] == RK_FUSION || ri[CR_KIND] == RK_NESTED); };
     for (int e = gl; e < dcnt; e += kL) {
       const int i = s_deps[doff + e];
       const int32_t* ri = s_rules + i * CWC_RULE_WORDS;
       if (kSens) integrate(i, tn);
       const unsigned long long cm = ctx_mask(ri);
-      HV(i) = (cm & ~touched) == 0ull ? 0ull : HV(i) - partial_h(ri, cm & touched);
+      HV(i) = general_rule(ri) || (cm & ~touched) == 0ull ? 0ull : HV(i) - partial_h(ri, cm & touched);
     }
     grp.sync();
-    if (gl == 0) apply(rec, ctx);
+    if (gl == 0) {
+      if (kGen && general_j)
+        cwc_general_apply(content, wrap, meta, chmask, labmask, alive_p, tot, S, L, s_rules, rec, ctx);
+      else
+        apply(rec, ctx);
+    }
     grp.sync();
     for (int e = gl; e < dcnt; e += kL) {
       const int i = s_deps[doff + e];
       const int32_t* ri = s_rules + i * CWC_RULE_WORDS;
-      const unsigned long long s2 = HV(i) + partial_h(ri, ctx_mask(ri) & touched);
+      const unsigned long long s2 = general_rule(ri) ? total_h(i) : HV(i) + partial_h(ri, ctx_mask(ri) & touched);
       if ((s2 >> 63) != 0ull) ovf = true;
       HV(i) = s2;
     }
@@ -1062,9 +1285,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
 
 // ---------------------------------------------------------------------------
 
-template <int kL, bool kQueue, bool kSens>
+template <int kL, bool kQueue, bool kSens, bool kGen>
 static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, size_t* smem_out) {
-  auto kern = cwc_ssa_kernel<kL, kQueue, kSens>;
+  auto kern = cwc_ssa_kernel<kL, kQueue, kSens, kGen>;
   const size_t smem = (size_t)prm.smem_table_bytes + (size_t)(T / kL) * cwc_thread_bytes(prm.M);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1084,12 +1307,20 @@ static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, si
   return cudaSuccess;
 }
 
-template <int kL>
-static cudaError_t cwc_config_l(const CwcParams& prm, bool queue, int T, int* blocks, size_t* smem) {
+template <int kL, bool kGen>
+static cudaError_t cwc_config_g(const CwcParams& prm, bool queue, int T, int* blocks, size_t* smem) {
   const bool sens = prm.sens != 0;
   if (queue)
-    return sens ? cwc_config_t<kL, true, true>(prm, T, blocks, smem) : cwc_config_t<kL, true, false>(prm, T, blocks, smem);
-  return sens ? cwc_config_t<kL, false, true>(prm, T, blocks, smem) : cwc_config_t<kL, false, false>(prm, T, blocks, smem);
+    return sens ? cwc_config_t<kL, true, true, kGen>(prm, T, blocks, smem)
+                : cwc_config_t<kL, true, false, kGen>(prm, T, blocks, smem);
+  return sens ? cwc_config_t<kL, false, true, kGen>(prm, T, blocks, smem)
+              : cwc_config_t<kL, false, false, kGen>(prm, T, blocks, smem);
+}
+
+template <int kL>
+static cudaError_t cwc_config_l(const CwcParams& prm, bool queue, int T, int* blocks, size_t* smem) {
+  return prm.general ? cwc_config_g<kL, true>(prm, queue, T, blocks, smem)
+                     : cwc_config_g<kL, false>(prm, queue, T, blocks, smem);
 }
 
 static cudaError_t cwc_config(const CwcParams& prm, bool queue, int lanes, int T, int* blocks, size_t* smem) {
@@ -1136,21 +1367,30 @@ int cwc_table_bytes_host(int M, int n_deps) { return cwc_table_bytes(M, n_deps);
 int cwc_thread_bytes_host(int M) { return cwc_thread_bytes(M); }
 long long cwc_slab_words_host(int S, int L, int C, int M, bool sens) { return cwc_slab_words(S, L, C, M, sens); }
 
-template <int kL>
-static void cwc_launch_l(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, size_t smem,
+template <int kL, bool kGen>
+static void cwc_launch_g(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, size_t smem,
                          cudaStream_t stream) {
   const bool sens = prm.sens != 0;
   if (queue) {
     if (sens)
-      cwc_ssa_kernel<kL, true, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, true, true, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
     else
-      cwc_ssa_kernel<kL, true, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, true, false, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
   } else {
     if (sens)
-      cwc_ssa_kernel<kL, false, true><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, false, true, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
     else
-      cwc_ssa_kernel<kL, false, false><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, false, false, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
   }
+}
+
+template <int kL>
+static void cwc_launch_l(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, size_t smem,
+                         cudaStream_t stream) {
+  if (prm.general)
+    cwc_launch_g<kL, true>(prm, lc, queue, T, blocks, smem, stream);
+  else
+    cwc_launch_g<kL, false>(prm, lc, queue, T, blocks, smem, stream);
 }
 
 cudaError_t launch_cwc(const CwcParams& prm, const LogConstants& lc, bool queue, int lanes, int T, int blocks,

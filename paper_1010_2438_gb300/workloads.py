@@ -584,6 +584,88 @@ def cwc3x24(R: int = 16384, G: int = 500, use_calibrated: bool = True) -> Batch:
 # c3 = 10) and 1000 molecules of every species.
 # ----------------------------------------------------------------------------
 
+# ----------------------------------------------------------------------------
+# General patterns (Sec. 2.1: a left-hand side may hold several compartments,
+# and compartments inside compartments): cells (label 1) in the top, vesicles
+# (label 2) in cells; every rule kind, including fusion of cells and of
+# vesicles and rules that reach two membranes down.
+# ----------------------------------------------------------------------------
+
+GEN_M, GEN_V = 5, 6   # cell and vesicle tokens (one in every wrap; merged wraps hold several)
+
+
+def cwc_general(R: int = 256, G: int = 50, seed: int = 7) -> Batch:
+    """Seven species (A..E = 0..4, the cell token M = 5, the vesicle token
+    V = 6), labels top / cell / vesicle, 19 rules of all six kinds:
+    reactions in each compartment type, transport across the cell and the
+    vesicle membranes, creation and dissolution of cells (token M) and
+    vesicles (token V), fusion of two cells (identical patterns: one M in
+    each wrap) and of two vesicles (different patterns: V in the first wrap,
+    E in the second content), and two depth-two rules (E taken out of a
+    vesicle straight into the top with a B there; vesicle-membrane catalysis
+    of A -> C in the cell).  Tokens are conserved (10 M, 8 V), so at most 18
+    compartments exist besides the root (24 slots).  Rates log-uniform over
+    two decades with volume scaling for Omega = 50; initial term: the top with
+    U{20..80} of A..E and 6 free M, 4 cells each with one M in the wrap,
+    U{5..40} of A..E, one free V and one vesicle (one V in its wrap, U{2..10}
+    of A..E)."""
+    A, B, C_, D, E, M_, V = 0, 1, 2, 3, 4, GEN_M, GEN_V
+    S, L, Cmax = 7, 3, 24
+    rules = [
+        RuleSpec(LOCAL, 0, lhs_ctx={A: 1}, rhs_ctx={B: 1}),
+        RuleSpec(LOCAL, 0, lhs_ctx={B: 1, C_: 1}, rhs_ctx={D: 1}),
+        RuleSpec(LOCAL, 0, lhs_ctx={D: 1}, rhs_ctx={A: 1, C_: 1}),
+        RuleSpec(LOCAL, 1, lhs_ctx={A: 1}, rhs_ctx={C_: 1}),
+        RuleSpec(LOCAL, 1, lhs_ctx={C_: 2}, rhs_ctx={E: 1}),
+        RuleSpec(LOCAL, 2, lhs_ctx={E: 1}, rhs_ctx={D: 1}),
+        RuleSpec(LOCAL, 2, lhs_ctx={D: 1}, rhs_ctx={E: 1}),
+        RuleSpec(PARENT_CHILD, 0, 1, lhs_ctx={A: 1}, rhs_child={A: 1}),
+        RuleSpec(PARENT_CHILD, 0, 1, lhs_child={C_: 1}, rhs_ctx={C_: 1}),
+        RuleSpec(PARENT_CHILD, 1, 2, lhs_ctx={E: 1}, rhs_child={E: 1}),
+        RuleSpec(PARENT_CHILD, 1, 2, lhs_child={D: 1}, rhs_ctx={D: 1}),
+        RuleSpec(CREATE, 0, 1, lhs_ctx={M_: 1}, rhs_wrap={M_: 1}, rhs_child={A: 5}),
+        RuleSpec(DISSOLVE, 0, 1, lhs_wrap={M_: 1}),
+        RuleSpec(CREATE, 1, 2, lhs_ctx={V: 1}, rhs_wrap={V: 1}, rhs_child={E: 2}),
+        RuleSpec(DISSOLVE, 1, 2, lhs_wrap={V: 1}),
+        RuleSpec(FUSION, 0, 1, lhs_wrap={M_: 1}, lhs_wrap2={M_: 1}, rhs_wrap={M_: 2}),
+        RuleSpec(FUSION, 1, 2, lhs_wrap={V: 1}, lhs_child2={E: 1}, rhs_wrap={V: 1}, rhs_child={E: 1}),
+        RuleSpec(NESTED, 0, 1, grand_label=2, lhs_ctx={B: 1}, lhs_child2={E: 1}, rhs_ctx={C_: 1}),
+        RuleSpec(NESTED, 0, 1, grand_label=2, lhs_child={A: 1}, lhs_wrap2={V: 1},
+                 rhs_child={C_: 1}, rhs_wrap2={V: 1}),
+    ]
+    model = cwc_model(S, L, Cmax, rules, "cwc_general")
+    rng = SplitMix64(seed)
+    omega = 50.0
+    rates = np.empty(model.n_rules, np.float64)
+    for j in range(model.n_rules):
+        if model.kind[j] in (CREATE, DISSOLVE, FUSION):
+            rates[j] = rng.log_uniform(-1.5, -0.5)
+        else:
+            lhs5, _, _ = model.rows5()
+            order = int(lhs5[j].sum())
+            rates[j] = rng.log_uniform(-2.0, 0.0) * omega ** (1 - order)
+    img = empty_slot_image(model)
+    for x in range(5):
+        img[0, 3 + S + x] = rng.randint(20, 80)
+    img[0, 3 + S + M_] = 6
+    slot = 1
+    for _ in range(4):
+        cell = slot
+        img[cell, :3] = [1, 1, 0]
+        img[cell, 3 + M_] = 1
+        for x in range(5):
+            img[cell, 3 + S + x] = rng.randint(5, 40)
+        img[cell, 3 + S + V] = 1
+        ves = slot + 1
+        img[ves, :3] = [1, 2, cell]
+        img[ves, 3 + V] = 1
+        for x in range(5):
+            img[ves, 3 + S + x] = rng.randint(2, 10)
+        slot += 2
+    T = 20.0
+    return Batch(model, rates[None, :], img[None], uniform_grid(T, G), R, 1000 + seed, name="cwc_general")
+
+
 def lotka_volterra_model(n: int) -> Model:
     reactions: List[Reaction] = [({0: 1}, {0: 2})]
     for i in range(n - 1):

@@ -171,3 +171,36 @@ def test_lotka_volterra_chain(n):
     assert m.lhs[n, 0, n - 1] == 1 and m.rhs[n].sum() == 0            # last predator death
     assert np.all(b.init == 1000)
     assert b.rates[0, 0] == 10.0 and b.rates[0, -1] == 10.0 and np.all(b.rates[0, 1:-1] == 0.01)
+
+
+def test_general_pattern_workload_recipe():
+    """cwc_general: every rule kind present, FUSION with identical (cells) and
+    different (vesicles) patterns, NESTED with its grandchild label; tokens
+    M (cells) and V (vesicles): one in every wrap, conserved by every rule,
+    so at most 18 compartments besides the root exist (24 slots)."""
+    b = W.cwc_general()
+    m = b.model
+    assert set(m.kind.tolist()) == set(W.KIND_NAMES)
+    lhs5, rhs5, grand = m.rows5()
+    for j in range(m.n_rules):
+        # token balance of every rule: matched tokens + released = produced
+        for tok in (W.GEN_M, W.GEN_V):
+            if m.kind[j] == W.DISSOLVE:
+                continue                      # releases the whole wrap into the parent
+            if m.kind[j] == W.FUSION:
+                assert lhs5[j, :, tok].sum() == rhs5[j, :, tok].sum()
+            elif m.kind[j] == W.CREATE:
+                assert lhs5[j, 0, tok] == rhs5[j, 1, tok]
+            else:
+                assert lhs5[j, :, tok].sum() == rhs5[j, :, tok].sum()
+        if m.kind[j] == W.NESTED:
+            assert grand[j] == 2 and m.child_label[j] == 1 and m.ctx_label[j] == 0
+    fus = np.nonzero(m.kind == W.FUSION)[0]
+    sym = [np.array_equal(lhs5[j, 1:3], lhs5[j, 3:5]) for j in fus]
+    assert sorted(sym) == [False, True]
+    img = b.init[0]
+    S = m.n_species
+    tokens_M = img[:, 3 + W.GEN_M].sum() + img[:, 3 + S + W.GEN_M].sum()
+    tokens_V = img[:, 3 + W.GEN_V].sum() + img[:, 3 + S + W.GEN_V].sum()
+    assert (tokens_M, tokens_V) == (10, 8)
+    assert 1 + tokens_M + tokens_V <= m.max_compartments - 5
