@@ -40,18 +40,36 @@ METRIC = "SSA events/sec"
 UNIT = "events/s"
 KERNEL_SOURCES = ["paper_1010_2438_gb300/csrc/flat_ssa.cu", "paper_1010_2438_gb300/csrc/ssa_device.cuh",
                   "paper_1010_2438_gb300/csrc/cwc_internal.h"]
-# FP64 pipe of one GB300: 152 SMs x 2 FP64 lanes per clock x 2.07 GHz (the
-# nominal 1.25 TFLOP/s dense FP64 counts an FMA as two flops).  A DADD/DMUL/
-# DFMA stream measured 5.0e11 op/s on the GB300s.
-FP64_PEAK_OPS = 152 * 2 * 2.07e9
+# Nominal FP64 pipe of one GB300: 152 SMs x 2 FP64 lanes per clock x 2.07 GHz
+# (the nominal 1.25 TFLOP/s dense FP64 counts an FMA as two flops).  The
+# roofline's peak is measured live instead (cwc_fp64_peak: a DADD/DMUL stream
+# on the same GPU in the same run).
+FP64_NOMINAL_OPS = 152 * 2 * 2.07e9
 
 
-def kernel_source_hash() -> str:
+CWC_KERNEL_SOURCES = ["paper_1010_2438_gb300/csrc/cwc_ssa.cu", "paper_1010_2438_gb300/csrc/ssa_device.cuh",
+                      "paper_1010_2438_gb300/csrc/cwc_internal.h"]
+
+
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in (KERNEL_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def capture_record(name: str, workload: str, sources):
+    """The ncu counters of a kernel (profiles/<name>_traffic.txt, JSON), if
+    they were captured on the current sources of that kernel, else None."""
+    path = os.path.join(ROOT, "profiles", name + "_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    if rec.get("kernel_source_hash") != kernel_source_hash(sources) or rec.get("workload") != workload:
+        return None
+    return rec
 
 
 def fp64_ops_per_event(model) -> float:
@@ -206,8 +224,20 @@ def measure_extras(dev):
 
     out, sec = _timed(run_cwc, "cwc3x24")
     ev = int(out["events"].sum().item())
+    # roofline of the compartment kernel: no FP64-bound step (its FP64 work
+    # is the flat step's, shared by a lane group); it is latency / issue
+    # bound, so the entry reports the issue-slot fraction and the DRAM bytes
+    # per event against the algorithmic bytes (the int32 observables written
+    # at the grid points) from the ncu capture of the same kernel sources
+    alg_bytes = 4.0 * b.G * cm.n_observables * b.n_traj / ev
+    cap = capture_record("cwc_ssa_kernel_cwc3x24", "cwc3x24", CWC_KERNEL_SOURCES)
+    roof = {"bound": "issue", "algorithmic_bytes_per_event": alg_bytes,
+            "dram_bytes_per_event": None if cap is None else cap.get("dram_bytes_per_event"),
+            "issue_active_frac": None if cap is None else cap.get("issue_active_frac"),
+            "warps_per_sm": None if cap is None else cap.get("warps_per_sm"),
+            "source": "ncu capture of the profiling case on the same kernel sources (hash-checked); null if stale"}
     extras["cwc3x24"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay, "block_threads": thr,
-                         "lanes_per_trajectory": lanes,
+                         "lanes_per_trajectory": lanes, "roofline": roof,
                          "workload": "3 labels below the top, 24 species, 48 rules (transport, wrap binding, create, "
                                      "dissolve), <=64 compartments, 16384 replicas, 500-point grid"}
     del out, keep
@@ -387,24 +417,25 @@ def main():
     achieved = f_evt * events / kernel_s
     traffic = None
     issue = None
-    tpath = os.path.join(ROOT, "profiles", "flat_ssa_kernel_flat32x64_traffic.txt")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        if tj.get("kernel_source_hash") == kernel_source_hash() and tj.get("workload") == WORKLOAD:
-            traffic = tj.get("dram_bytes_per_launch")
-            # issue-rate roofline of the same kernel (warp instructions issued per
-            # scheduler cycle, of the 1 per cycle peak) and the FP64 pipe's busy
-            # fraction, from the ncu capture of the profiling case
-            issue = {"frac": tj.get("issue_active_frac"), "fp64_pipe_frac": tj.get("fp64_pipe_frac"),
-                     "warps_per_sm": tj.get("warps_per_sm"),
-                     "source": "ncu smsp__issue_active / sm__pipe_fp64_cycles_active of the profiling case, "
-                               "captured on the same kernel sources (hash-checked)"}
-    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9, "unit": "GFLOP/s (FP64)",
-                "frac": achieved / FP64_PEAK_OPS, "traffic": traffic, "issue": issue,
+    tj = capture_record("flat_ssa_kernel_flat32x64", WORKLOAD, KERNEL_SOURCES)
+    if tj is not None:
+        traffic = tj.get("dram_bytes_per_launch")
+        # issue-rate roofline of the same kernel (warp instructions issued per
+        # scheduler cycle, of the 1 per cycle peak) and the FP64 pipe's busy
+        # fraction, from the ncu capture of the profiling case
+        issue = {"frac": tj.get("issue_active_frac"), "fp64_pipe_frac": tj.get("fp64_pipe_frac"),
+                 "warps_per_sm": tj.get("warps_per_sm"),
+                 "source": "ncu smsp__issue_active / sm__pipe_fp64_cycles_active of the profiling case, "
+                           "captured on the same kernel sources (hash-checked)"}
+    peak = capi.cwc_fp64_peak(stream.cuda_stream)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GFLOP/s (FP64)",
+                "frac": achieved / peak, "peak_source": "measured in this run: cwc_fp64_peak (DADD/DMUL stream, "
+                                                        "32 warps per SM, best of 3)",
+                "nominal_peak": FP64_NOMINAL_OPS / 1e9, "frac_of_nominal": achieved / FP64_NOMINAL_OPS,
+                "traffic": traffic, "issue": issue,
                 "note": "FP64 pipe (the path's only floating-point unit; the logarithm is integer): %.1f algorithmic "
-                        "FP64 ops/event x %d events / %.4f s; peak derived from 152 SMs x 2 FP64 lanes/clk x 2.07 GHz; "
-                        "issue: ncu issue-slot fraction" % (f_evt, events, kernel_s)}
+                        "FP64 ops/event x %d events / %.4f s (CUDA events on the launching stream); frac is of the "
+                        "measured peak; issue: ncu issue-slot fraction of the same kernel" % (f_evt, events, kernel_s)}
 
     # end to end through host buffers (pinned): H2D inputs, simulate, D2H states
     e2e = None

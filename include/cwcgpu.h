@@ -150,8 +150,18 @@ enum {
   CWC_LAYOUT_AUTO = 0,        /* the autotuner's cached choice for this shape   */
   CWC_LAYOUT_STATIC = 1,      /* one thread per trajectory; a lane that finishes
                                  takes trajectory q + (threads in the grid)     */
-  CWC_LAYOUT_QUEUE = 2        /* persistent grid; a lane that finishes takes the
+  CWC_LAYOUT_QUEUE = 2,       /* persistent grid; a lane that finishes takes the
                                  next trajectory from a device work queue       */
+  CWC_LAYOUT_TAIL = 3         /* flat models, forward only (no deadline, no
+                                 checkpoint, no sensitivities): the queue layout,
+                                 then, once the queue is empty and at most
+                                 tail_threshold trajectories still run, those
+                                 stop at their next 1024-event boundary and are
+                                 finished by one warp each, longest predicted
+                                 remaining work first (prediction: events so far
+                                 x (T - t) / t).  Cuts the makespan of batches of
+                                 uneven trajectory length (parameter sweeps);
+                                 results are identical to the other layouts   */
 };
 
 /*
@@ -268,6 +278,8 @@ typedef struct {
   int64_t deadline_ns;
   void* workspace;
   size_t workspace_bytes;
+  int32_t tail_threshold;    /* CWC_LAYOUT_TAIL: hand over when at most this many
+                                trajectories run (0 = 3 per SM) */
 } cwc_sim_args;
 
 /*
@@ -395,6 +407,18 @@ const char* cwc_last_error(void);
 
 /* Library version string. */
 const char* cwc_version(void);
+
+/*
+ * The FP64 pipe's peak rate on the current device, measured (a diagnostic;
+ * the paper has no counterpart): a grid of 32 warps per SM runs eight
+ * independent chains of unfused round-to-nearest double multiplies and adds
+ * (the FP64 instructions the simulation kernels issue) for ~20 ms, timed with
+ * CUDA events (best of three after a warm-up).  *lane_ops_per_s = thread-level
+ * FP64 operations per second.  It is the denominator of the kernels' FP64
+ * roofline.  Synchronises `stream`; allocates nothing.
+ * Errors: CWC_ERR_INVALID_ARG (NULL output), CWC_ERR_CUDA.
+ */
+cwc_status cwc_fp64_peak(void* stream, double* lane_ops_per_s);
 
 #ifdef __cplusplus
 }

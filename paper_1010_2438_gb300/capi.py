@@ -20,12 +20,13 @@ STATUS_NAMES = {0: "CWC_OK", 1: "CWC_ERR_INVALID_ARG", 2: "CWC_ERR_UNSUPPORTED",
                 4: "CWC_ERR_WORKSPACE", 5: "CWC_ERR_INTERNAL"}
 (CWC_TRAJ_OK, CWC_TRAJ_ABSORBED, CWC_TRAJ_INT_OVERFLOW, CWC_TRAJ_PROP_OVERFLOW, CWC_TRAJ_CAPACITY,
  CWC_TRAJ_EVENT_LIMIT, CWC_TRAJ_BAD_INPUT, CWC_TRAJ_TIMEOUT) = range(8)
-CWC_LAYOUT_AUTO, CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE = range(3)
+CWC_LAYOUT_AUTO, CWC_LAYOUT_STATIC, CWC_LAYOUT_QUEUE, CWC_LAYOUT_TAIL = range(4)
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = ("cwc_model_create", "cwc_model_destroy", "cwc_model_num_observables", "cwc_simulate_workspace_size",
             "cwc_simulate", "cwc_simulate_noalloc", "cwc_sensitivity_workspace_size", "cwc_sensitivity",
-            "cwc_autotune", "cwc_checkpoint_words", "cwc_log_spec", "cwc_last_error", "cwc_version")
+            "cwc_autotune", "cwc_checkpoint_words", "cwc_log_spec", "cwc_last_error", "cwc_version",
+            "cwc_fp64_peak")
 CWC_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 _vp = ctypes.c_void_p
@@ -48,7 +49,7 @@ class cwc_sim_args(ctypes.Structure):
                 ("log_cap", _i32), ("log_rule", _vp), ("log_slot", _vp), ("log_t", _vp),
                 ("checkpoint", _vp), ("resume", _i32),
                 ("layout", _i32), ("block_threads", _i32), ("lanes", _i32), ("deadline_ns", _i64),
-                ("workspace", _vp), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", _vp), ("workspace_bytes", ctypes.c_size_t), ("tail_threshold", _i32)]
 
 
 class cwc_sens_args(ctypes.Structure):
@@ -100,6 +101,8 @@ def lib() -> ctypes.CDLL:
         L.cwc_checkpoint_words.restype = _i32
         L.cwc_log_spec.argtypes = [_vp, _vp, _i64, _vp]
         L.cwc_log_spec.restype = ctypes.c_int
+        L.cwc_fp64_peak.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+        L.cwc_fp64_peak.restype = ctypes.c_int
         L.cwc_last_error.argtypes = []
         L.cwc_last_error.restype = ctypes.c_char_p
         L.cwc_version.argtypes = []
@@ -163,6 +166,13 @@ def cwc_autotune(handle: int, args: cwc_sim_args, tune_events: int = 0, stream: 
     _check(lib().cwc_autotune(handle, ctypes.byref(args), tune_events, stream, ctypes.byref(lay), ctypes.byref(thr),
                               ctypes.byref(ms), ctypes.byref(lanes)))
     return lay.value, thr.value, lanes.value, ms.value
+
+
+def cwc_fp64_peak(stream: int = 0) -> float:
+    """Measured FP64 lane-operations per second of the current GPU."""
+    v = ctypes.c_double(0.0)
+    _check(lib().cwc_fp64_peak(stream, ctypes.byref(v)))
+    return v.value
 
 
 def cwc_log_spec(u_ptr: int, out_ptr: int, n: int, stream: int = 0) -> None:

@@ -23,6 +23,8 @@ size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens);
 int flat_table_bytes_host(int M, int n_deps);
 int flat_auto_threads(const FlatParams& prm, bool queue, bool sens);
 cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order, cudaStream_t stream);
+cudaError_t launch_flat_tail(const FlatParams& prm, const LogConstants& lc, int32_t* list, double* est,
+                             int32_t* order, cudaStream_t stream);
 cudaError_t launch_means(const unsigned long long* sums, double* means, long long n, int R, cudaStream_t st);
 cudaError_t launch_reciprocal(const double* k, double* inv, long long n, cudaStream_t st);
 cudaError_t launch_stats(const unsigned long long* sums, const unsigned long long* sumsq, double* variance,
@@ -104,6 +106,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace layout: [header 256 B][sums P*G*O int64 if needed][partials Q*M double if needed]
 struct WsLayout {
   size_t header = 0, sums = 0, sumsq = 0, partials = 0, slabs = 0, order = 0, sens_acc = 0, inv_rates = 0, total = 0;
+  size_t tail = 0;                // tail layout: checkpoints [Q][S+8] i32, list [Q] i32, est [Q] f64, order [Q] i32
+  bool need_tail = false;
   bool need_sumsq = false;
   bool need_order = false;        // flat queue layout over several sweep points
   bool need_header = false, need_sums = false, need_partials = false;
@@ -156,6 +160,11 @@ int chosen_lanes(const cwc_model* m, const cwc_sim_args* a) {
 
 int chosen_layout(const cwc_sim_args* a) { return a->layout == CWC_LAYOUT_AUTO ? CWC_LAYOUT_QUEUE : a->layout; }
 
+// the queue-driven layouts: the persistent grid with a work ticket
+bool queue_layout(const cwc_sim_args* a) {
+  return chosen_layout(a) == CWC_LAYOUT_QUEUE || chosen_layout(a) == CWC_LAYOUT_TAIL;
+}
+
 // Resolve CWC_LAYOUT_AUTO / block_threads 0 through the autotuner cache.
 cwc_sim_args resolve_auto(const cwc_model* m, const cwc_sim_args* a) {
   cwc_sim_args b = *a;
@@ -182,7 +191,7 @@ int cover_sms(int T, long long Q) {
 WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool sens_partials_given) {
   WsLayout w;
   const int O = m->flat ? m->S : (m->L * m->S + (m->L - 1) * m->S + m->L);
-  w.need_header = chosen_layout(a) == CWC_LAYOUT_QUEUE || a->deadline_ns > 0;
+  w.need_header = queue_layout(a) || a->deadline_ns > 0;
   const bool stats = a->variance != nullptr || a->ci90 != nullptr;
   w.need_sums = !sens && (a->means != nullptr || stats) && a->sums == nullptr;
   w.need_sumsq = !sens && stats && a->sumsq == nullptr;
@@ -205,15 +214,21 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
     off = align256(off + (size_t)a->P * a->R * m->M * sizeof(double));
   }
   if (m->flat && sens) {   // the flat replay's per-trajectory integrals, times and firing counts
-    w.sens_acc = off;
-    off = align256(off + (size_t)a->P * a->R * 3 * m->M * sizeof(double));
+    w.sens_acc = off;      // per trajectory: M (integral, time) pairs, M firing counts padded to even
+    off = align256(off + (size_t)a->P * a->R * (2 * (size_t)m->M + (((size_t)m->M + 1) & ~(size_t)1)) * sizeof(double));
     w.inv_rates = off;     // 1 / k per sweep point and rule
     off = align256(off + (size_t)a->P * m->M * sizeof(double));
   }
-  w.need_order = m->flat && chosen_layout(a) == CWC_LAYOUT_QUEUE && a->P > 1 && a->P <= 65536;
+  w.need_order = m->flat && queue_layout(a) && a->P > 1 && a->P <= 65536;
   if (w.need_order) {
     w.order = off;
     off = align256(off + (size_t)a->P * (sizeof(double) + sizeof(int32_t)));
+  }
+  w.need_tail = m->flat && !sens && chosen_layout(a) == CWC_LAYOUT_TAIL;
+  if (w.need_tail) {
+    const size_t Q = (size_t)a->P * a->R;
+    w.tail = off;
+    off = align256(off + Q * ((size_t)(m->S + CKPT_HEADER_WORDS) * 4 + 4 + 8 + 4) + 256);
   }
   if (!m->flat) {
     const CwcParams prm = cwc_shape_params(m, a, sens);
@@ -242,7 +257,11 @@ cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
     return fail(CWC_ERR_INVALID_ARG, "max_events must be in [0, 2^32-1]");
   if (a->log_cap < 0) return fail(CWC_ERR_INVALID_ARG, "log_cap must be >= 0");
   if (a->log_cap > 0 && a->log_rule == nullptr) return fail(CWC_ERR_INVALID_ARG, "log_cap > 0 needs log_rule");
-  if (a->layout < CWC_LAYOUT_AUTO || a->layout > CWC_LAYOUT_QUEUE) return fail(CWC_ERR_INVALID_ARG, "bad layout");
+  if (a->layout < CWC_LAYOUT_AUTO || a->layout > CWC_LAYOUT_TAIL) return fail(CWC_ERR_INVALID_ARG, "bad layout");
+  if (a->layout == CWC_LAYOUT_TAIL &&
+      (!m->flat || a->deadline_ns != 0 || a->checkpoint != nullptr || a->resume != 0))
+    return fail(CWC_ERR_INVALID_ARG, "CWC_LAYOUT_TAIL is for flat models without deadline or checkpoints");
+  if (a->tail_threshold < 0) return fail(CWC_ERR_INVALID_ARG, "tail_threshold must be >= 0");
   if (a->block_threads != 0 && (a->block_threads < 32 || a->block_threads > 256 || a->block_threads % 32 != 0))
     return fail(CWC_ERR_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 256]");
   if (a->lanes != 0 && !(m->flat ? a->lanes == 1 : cwc_lanes_supported(a->lanes)))
@@ -743,7 +762,25 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     prm.inv_rates = inv;
   }
   const LogConstants lc = make_log_constants();
-  const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
+  const bool queue = queue_layout(a);
+  int32_t* tail_list = nullptr;
+  double* tail_est = nullptr;
+  int32_t* tail_order = nullptr;
+  if (w.need_tail) {
+    // the thread kernel's checkpoints (the handed-over state), then the
+    // warp kernel's list, predictions and order
+    const size_t Q = (size_t)a->P * a->R;
+    unsigned char* base = ws + w.tail;
+    prm.ckpt = reinterpret_cast<int32_t*>(base);
+    base += align256(Q * (size_t)(m->S + CKPT_HEADER_WORDS) * 4);
+    tail_est = reinterpret_cast<double*>(base);
+    tail_list = reinterpret_cast<int32_t*>(tail_est + Q);
+    tail_order = tail_list + Q;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    prm.handoff = a->tail_threshold > 0 ? a->tail_threshold : 3LL * sms;
+  }
   if (w.need_order) {
     double* est = reinterpret_cast<double*>(ws + w.order);
     int32_t* order = reinterpret_cast<int32_t*>(est + a->P);
@@ -756,6 +793,10 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     return fail(CWC_ERR_INVALID_ARG, "block_threads too large for this model's shared-memory state");
   e = launch_flat(prm, lc, queue, is_sens, T, 0, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "flat SSA kernel launch");
+  if (w.need_tail) {
+    e = launch_flat_tail(prm, lc, tail_list, tail_est, tail_order, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tail kernels launch");
+  }
   if (!is_sens && a->means != nullptr) {
     e = launch_means(prm.sums, a->means, (long long)a->P * a->G * O, a->R, st);
     if (e != cudaSuccess) return cuda_fail(e, "means kernel launch");

@@ -76,12 +76,17 @@ enum : int32_t {
   TS_EVENT_LIMIT = 5, TS_BAD_INPUT = 6, TS_TIMEOUT = 7
 };
 
-// Workspace header (first 256 bytes when used): work-queue ticket and the
-// launch timestamp for deadlines.
+// Workspace header (first 256 bytes when used): work-queue ticket, the
+// launch timestamp for deadlines and, for the tail layout, the number of
+// trajectories running in the thread kernel, the number handed over to the
+// warp kernel and that kernel's ticket.
 struct WorkspaceHeader {
   unsigned long long queue_next;
   unsigned long long t_start_ns;
-  unsigned long long pad[30];
+  unsigned long long running;
+  unsigned long long tail_count;
+  unsigned long long tail_next;
+  unsigned long long pad[27];
 };
 static_assert(sizeof(WorkspaceHeader) == 256, "workspace header size");
 
@@ -118,13 +123,15 @@ struct FlatParams {
   const double* means;             // [P][G][S]
   const double* grad_means;        // [P][G][S]
   double* partials;                // [Q][M]
-  double* sens_acc;                // score replay: [Q][3][M] int_0^tl H_i dt, tl_i, firings N_i
+  double* sens_acc;                // score replay: per trajectory [M] (int_0^tl H_i dt, tl_i) pairs, then [M] firings N_i (padded to even)
   const double* inv_rates;         // score replay: [P][M] 1 / k_j
   // scheduling
   WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)
   int32_t* ckpt;                   // [Q][S + CKPT_HEADER_WORDS] trajectory checkpoints (or null)
   int resume;                      // 1: continue the TIMEOUT trajectories of ckpt
   const int32_t* order;            // queue mode: sweep points, longest expected first (or null)
+  long long handoff;               // tail layout: hand over when the queue is empty and at most
+                                   // this many trajectories run (0 = never)
   long long deadline_ns;
   int smem_table_bytes;            // bytes of the shared-memory table region
 };

@@ -25,7 +25,12 @@
 // group runs:
 //   chmask[C]  u64  children of each slot        labmask[L] u64  alive slots per label
 //   alive      u64  alive slots                  tot[O]     i64  observable totals
-//   meta[C]    i32  label | (parent + 1) << 8   wrap[C][S], content[C][S]  i32
+//   meta[C]    i32  label | (parent + 1) << 8   wrap[S][C], content[S][C]  i32
+// The counts are stored species-major: the counts of one species in all C
+// slots are contiguous (256 bytes for 64 slots), so a context scan over a
+// label's slots reads one or two cache lines per reactant species instead of
+// one line per slot, and the slabs' lines stay hot in L2 (the slabs of a
+// 16,384-term batch exceed L2).
 // The observable totals (content per label, wrap per label, alive compartments
 // per label) are kept up to date by every rewrite, so recording a grid point
 // is O stores.
@@ -123,7 +128,7 @@ __host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, 
 // Out of line for lane groups (see below).
 __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restrict__ content,
                                                         const int32_t* __restrict__ wrap,
-                                                        const int32_t* __restrict__ meta, int S,
+                                                        const int32_t* __restrict__ meta, int C,
                                                         const int32_t* rec, unsigned long long m) {
   const int kind = rec[CR_KIND];
   const bool parent_child = !(kind == RK_LOCAL || kind == RK_CREATE);
@@ -150,17 +155,17 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
       if ((meta[qq] & 0xff) != ctx) continue;
       x0c = qq;
     }
-    const int32_t* x0 = content + (size_t)x0c * S;
-    const int32_t* x1 = wrap + (size_t)x12c * S;
-    const int32_t* x2 = content + (size_t)x12c * S;
-    const int32_t* x3 = wrap + (size_t)c * S;
-    const int32_t* x4 = content + (size_t)c * S;
+    const int32_t* x0 = content + x0c;
+    const int32_t* x1 = wrap + x12c;
+    const int32_t* x2 = content + x12c;
+    const int32_t* x3 = wrap + c;
+    const int32_t* x4 = content + c;
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
       const int row = (v >> 24) & 7;
       const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : (row == 2 ? x2 : (row == 3 ? x3 : x4)));
-      acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
+      acc = mul_checked(acc, binom12(x[(v & 0xffff) * C], (v >> 16) & 0xff), &of);
     }
     const unsigned long long s2 = tot + acc;
     if (s2 < tot || (s2 >> 63) != 0ull) of = true;
@@ -179,7 +184,7 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
 // bit 63 flagging an overflow of a product or of the sum.
 __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __restrict__ content,
                                                           const int32_t* __restrict__ wrap,
-                                                          const int32_t* __restrict__ meta, int S,
+                                                          const int32_t* __restrict__ meta, int C,
                                                           const int32_t* rec, unsigned long long kids,
                                                           bool want_pick, unsigned long long xc) {
   const int nr = rec[CR_NREAC];
@@ -207,7 +212,7 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
     m1 &= m1 - 1ull;
     const int qq = (meta[d1] >> 8) - 1;
     if ((meta[qq] & 0xff) != ctx) continue;
-    const int32_t* x0 = content + (size_t)qq * S;
+    const int32_t* x0 = content + qq;
     unsigned long long m2 = kids & ~(1ull << d1);
     if (sym) m2 &= ~((2ull << d1) - 1ull);   // d2 > d1 only
     while (m2) {
@@ -219,10 +224,10 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
         const int v = rec[CR_REAC + a];
         const int row = (v >> 24) & 7;
         const int32_t* x = row == 0 ? x0
-                           : row == 1 ? wrap + (size_t)d1 * S
-                           : row == 2 ? content + (size_t)d1 * S
-                           : row == 3 ? wrap + (size_t)d2 * S : content + (size_t)d2 * S;
-        acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
+                           : row == 1 ? wrap + d1
+                           : row == 2 ? content + d1
+                           : row == 3 ? wrap + d2 : content + d2;
+        acc = mul_checked(acc, binom12(x[(v & 0xffff) * C], (v >> 16) & 0xff), &of);
       }
       const unsigned long long s2 = tot + acc;
       if (s2 < tot || (s2 >> 63) != 0ull) of = true;
@@ -243,20 +248,20 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
 // (FUSION: the lower slot keeps the merged compartment, the higher is freed
 // and its children move to the survivor).
 __device__ __noinline__ int cwc_general_check(const int32_t* content, const int32_t* wrap, const int32_t* meta, int S,
-                                              const int32_t* table, const int32_t* rec, int ctx) {
+                                              int C, const int32_t* table, const int32_t* rec, int ctx) {
   auto fits = [](long long v) { return v >= 0 && v <= 0x7FFFFFFFll; };
   const int nr = rec[CR_NREAC];
   if (rec[CR_KIND] == RK_NESTED) {
     const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
-    const int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
-                            wrap + (size_t)g * S, content + (size_t)g * S};
+    const int32_t* ms[5] = {content + aa, wrap + qq, content + qq,
+                            wrap + g, content + g};
     const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
     const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
     for (int row = 0; row < 5; ++row)
       for (int d = 0; d < nd[row]; ++d) {
         const int v = dd[row][d];
-        if (!fits((long long)ms[row][v & 0xffff] + (v >> 16))) return TS_INT_OVERFLOW;
+        if (!fits((long long)ms[row][(v & 0xffff) * C] + (v >> 16))) return TS_INT_OVERFLOW;
       }
     return TS_OK;
   }
@@ -264,11 +269,11 @@ __device__ __noinline__ int cwc_general_check(const int32_t* content, const int3
   const int qq = (meta[d1] >> 8) - 1;
   for (int d = 0; d < rec[CR_ND0]; ++d) {
     const int v = rec[CR_D0 + d];
-    if (!fits((long long)content[(size_t)qq * S + (v & 0xffff)] + (v >> 16))) return TS_INT_OVERFLOW;
+    if (!fits((long long)content[(size_t)((v & 0xffff)) * C + qq] + (v >> 16))) return TS_INT_OVERFLOW;
   }
   for (int x = 0; x < S; ++x) {
-    long long wv = (long long)wrap[(size_t)d1 * S + x] + wrap[(size_t)d2 * S + x];
-    long long cv = (long long)content[(size_t)d1 * S + x] + content[(size_t)d2 * S + x];
+    long long wv = (long long)wrap[(size_t)(x) * C + d1] + wrap[(size_t)(x) * C + d2];
+    long long cv = (long long)content[(size_t)(x) * C + d1] + content[(size_t)(x) * C + d2];
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
       const int row = (v >> 24) & 7;
@@ -288,7 +293,7 @@ __device__ __noinline__ int cwc_general_check(const int32_t* content, const int3
 // O = L*S content totals, (L-1)*S wrap totals, L alive counts (see kernel)
 __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, int32_t* meta,
                                                unsigned long long* chmask, unsigned long long* labmask,
-                                               unsigned long long* alive_p, long long* tot, int S, int L,
+                                               unsigned long long* alive_p, long long* tot, int S, int L, int C,
                                                const int32_t* table, const int32_t* rec, int ctx) {
   auto OC = [&](int l, int x) { return l * S + x; };
   auto OW = [&](int l, int x) { return L * S + (l - 1) * S + x; };
@@ -297,15 +302,15 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
     const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
     const int la = meta[aa] & 0xff, lq = meta[qq] & 0xff, lg = meta[g] & 0xff;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
-    int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
-                      wrap + (size_t)g * S, content + (size_t)g * S};
+    int32_t* ms[5] = {content + aa, wrap + qq, content + qq,
+                      wrap + g, content + g};
     const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
     const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
     for (int row = 0; row < 5; ++row)
       for (int d = 0; d < nd[row]; ++d) {
         const int v = dd[row][d];
         const int x = v & 0xffff, dv = v >> 16;
-        ms[row][x] += dv;
+        ms[row][x * C] += dv;
         const int o = row == 0 ? OC(la, x) : row == 1 ? OW(lq, x) : row == 2 ? OC(lq, x) : row == 3 ? OW(lg, x) : OC(lg, x);
         tot[o] += dv;
       }
@@ -318,7 +323,7 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
   const int nr = rec[CR_NREAC];
   for (int d = 0; d < rec[CR_ND0]; ++d) {
     const int v = rec[CR_D0 + d];
-    content[(size_t)qq * S + (v & 0xffff)] += v >> 16;
+    content[(size_t)((v & 0xffff)) * C + qq] += v >> 16;
     tot[OC(lq, v & 0xffff)] += v >> 16;
   }
   for (int x = 0; x < S; ++x) {
@@ -334,10 +339,10 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
       if ((rec[CR_D1 + d] & 0xffff) == x) dw += rec[CR_D1 + d] >> 16;
     for (int d = 0; d < rec[CR_ND2]; ++d)
       if ((rec[CR_D2 + d] & 0xffff) == x) dc += rec[CR_D2 + d] >> 16;
-    wrap[(size_t)keep * S + x] = wrap[(size_t)keep * S + x] + wrap[(size_t)gone * S + x] + dw;
-    content[(size_t)keep * S + x] = content[(size_t)keep * S + x] + content[(size_t)gone * S + x] + dc;
-    wrap[(size_t)gone * S + x] = 0;
-    content[(size_t)gone * S + x] = 0;
+    wrap[(size_t)(x) * C + keep] = wrap[(size_t)(x) * C + keep] + wrap[(size_t)(x) * C + gone] + dw;
+    content[(size_t)(x) * C + keep] = content[(size_t)(x) * C + keep] + content[(size_t)(x) * C + gone] + dc;
+    wrap[(size_t)(x) * C + gone] = 0;
+    content[(size_t)(x) * C + gone] = 0;
     tot[OW(lc, x)] += dw;
     tot[OC(lc, x)] += dc;
   }
@@ -394,35 +399,35 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
         const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
         if (freeslots == 0ull) return TS_CAPACITY;
       }
-      const int32_t* x = content + (size_t)c * S;
+      const int32_t* x = content + c;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(x[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     const int qq = PARENT(c);
-    const int32_t* xp = content + (size_t)qq * S;
-    const int32_t* w = wrap + (size_t)c * S;
-    const int32_t* xc = content + (size_t)c * S;
+    const int32_t* xp = content + qq;
+    const int32_t* w = wrap + c;
+    const int32_t* xc = content + c;
     if (kind == 1) {
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xp[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(w[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xc[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     // DISSOLVE: the parent content gains (rhs0 - lhs0) + (wrap - lhs1) + (content - lhs2)
     for (int s = 0; s < S; ++s) {
-      long long dv = (long long)w[s] + xc[s];
+      long long dv = (long long)w[(s) * C] + xc[(s) * C];
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         if ((v & 0xffff) == s) dv += v >> 16;
@@ -432,7 +437,7 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
         const int v = rec[CR_REAC + a];
         if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
-      const long long nv = (long long)xp[s] + dv;
+      const long long nv = (long long)xp[(s) * C] + dv;
       if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
     }
     return TS_OK;
@@ -509,8 +514,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   double* part = tl + (kSens ? M : 0);                                            // [M]
   int32_t* Nf = reinterpret_cast<int32_t*>(part + (kSens ? M : 0));               // [M]
   int32_t* meta = Nf + (kSens ? M : 0);                                           // [C]
-  int32_t* wrap = meta + C;                                                       // [C][S]
-  int32_t* content = wrap + (size_t)C * S;                                        // [C][S]
+  int32_t* wrap = meta + C;                                                       // [S][C]
+  int32_t* content = wrap + (size_t)C * S;                                        // [S][C]
 
   auto LABEL = [&](int c) -> int { return meta[c] & 0xff; };
   auto PARENT = [&](int c) -> int { return (meta[c] >> 8) - 1; };
@@ -537,16 +542,16 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // (kinds LOCAL .. DISSOLVE; NESTED counts go through cwc_count_sum)
   auto count_at = [&](const int32_t* rec, int c) -> unsigned long long {
     const int kind = rec[CR_KIND];
-    const int32_t* x0 = content + (size_t)((kind == RK_LOCAL || kind == RK_CREATE) ? c : PARENT(c)) * S;
-    const int32_t* x1 = wrap + (size_t)c * S;
-    const int32_t* x2 = content + (size_t)c * S;
+    const int32_t* x0 = content + ((kind == RK_LOCAL || kind == RK_CREATE) ? c : PARENT(c));
+    const int32_t* x1 = wrap + c;
+    const int32_t* x2 = content + c;
     const int nr = rec[CR_NREAC];
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
       const int row = (v >> 24) & 3;
       const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
-      acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &ovf);
+      acc = mul_checked(acc, binom12(x[(v & 0xffff) * C], (v >> 16) & 0xff), &ovf);
     }
     return acc;
   };
@@ -578,7 +583,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       }
       return tot;
     }
-    const unsigned long long r = cwc_count_sum(content, wrap, meta, S, rec, m);
+    const unsigned long long r = cwc_count_sum(content, wrap, meta, C, rec, m);
     if (r >> 63) ovf = true;
     return r;
   };
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   auto total_h = [&](int i) -> unsigned long long {
     const int32_t* rec = s_rules + i * CWC_RULE_WORDS;
     if (kGen && rec[CR_KIND] == RK_FUSION) {
-      const unsigned long long r = cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), false, 0ull);
+      const unsigned long long r = cwc_fusion_scan(content, wrap, meta, C, rec, ctx_mask(rec), false, 0ull);
       if (r >> 63) ovf = true;
       return r & ~(1ull << 63);
     }
@@ -660,8 +665,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     if (prm.ckpt != nullptr) {
       int32_t* rec = prm.ckpt + (size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W);
       if (gl == 0) {
-        *reinterpret_cast<double*>(rec) = t;
-        *reinterpret_cast<unsigned long long*>(rec + 2) = h;
+        put_f64(rec, t);
+        put_u64(rec + 2, h);
         rec[4] = (int32_t)n;
         rec[5] = gi;
         rec[6] = status;
@@ -675,8 +680,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         row[1] = a ? LABEL(c) : 0;
         row[2] = a ? PARENT(c) : -1;
         for (int x = 0; x < S; ++x) {
-          row[3 + x] = wrap[(size_t)c * S + x];
-          row[3 + S + x] = content[(size_t)c * S + x];
+          row[3 + x] = wrap[(size_t)(x) * C + c];
+          row[3 + S + x] = content[(size_t)(x) * C + c];
         }
       }
     }
@@ -727,8 +732,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     if (prm.resume) {
       const int32_t* rec = prm.ckpt + (size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W);
       if (rec[6] != TS_TIMEOUT) return 2;
-      t = *reinterpret_cast<const double*>(rec);
-      h = *reinterpret_cast<const unsigned long long*>(rec + 2);
+      t = get_f64(rec);
+      h = get_u64(rec + 2);
       n = (unsigned)rec[4];
       gi = rec[5];
       if (gi < 0 || gi > G) bad = true;
@@ -749,16 +754,16 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
           const int wv = row[3 + x], cv = row[3 + S + x];
           if (wv < 0 || cv < 0) bad = true;
           if (c == 0 && wv != 0) bad = true;
-          wrap[(size_t)c * S + x] = wv;
-          content[(size_t)c * S + x] = cv;
+          wrap[(size_t)(x) * C + c] = wv;
+          content[(size_t)(x) * C + c] = cv;
         }
         alive |= 1ull << c;
         meta[c] = (lab & 0xff) | ((par + 1) << 8);
       } else {
         meta[c] = 0;
         for (int x = 0; x < S; ++x) {
-          wrap[(size_t)c * S + x] = 0;
-          content[(size_t)c * S + x] = 0;
+          wrap[(size_t)(x) * C + c] = 0;
+          content[(size_t)(x) * C + c] = 0;
         }
       }
     }
@@ -806,8 +811,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       for (int c = 0; c < C; ++c) {
         if (!((alive >> c) & 1ull)) continue;
         const int l = LABEL(c);
-        tot[OC(l, x)] += content[(size_t)c * S + x];
-        if (l > 0) tot[OW(l, x)] += wrap[(size_t)c * S + x];
+        tot[OC(l, x)] += content[(size_t)(x) * C + c];
+        if (l > 0) tot[OW(l, x)] += wrap[(size_t)(x) * C + c];
       }
     }
     if (gl == 0) {
@@ -836,35 +841,35 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
         if (freeslots == 0ull) return TS_CAPACITY;
       }
-      const int32_t* x = content + (size_t)c * S;
+      const int32_t* x = content + c;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(x[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     const int qq = PARENT(c);
-    const int32_t* xp = content + (size_t)qq * S;
-    const int32_t* w = wrap + (size_t)c * S;
-    const int32_t* xc = content + (size_t)c * S;
+    const int32_t* xp = content + qq;
+    const int32_t* w = wrap + c;
+    const int32_t* xc = content + c;
     if (kind == 1) {
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xp[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(w[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xc[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     // DISSOLVE: the parent content gains (rhs0 - lhs0) + (wrap - lhs1) + (content - lhs2)
     for (int s = 0; s < S; ++s) {
-      long long dv = (long long)w[s] + xc[s];
+      long long dv = (long long)w[(s) * C] + xc[(s) * C];
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         if ((v & 0xffff) == s) dv += v >> 16;
@@ -874,7 +879,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int v = rec[CR_REAC + a];
         if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
-      const long long nv = (long long)xp[s] + dv;
+      const long long nv = (long long)xp[(s) * C] + dv;
       if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
     }
     return TS_OK;
@@ -885,34 +890,34 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const int kind = rec[CR_KIND];
     const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
     if (kind == 0) {
-      int32_t* x = content + (size_t)c * S;
+      int32_t* x = content + c;
       const int l = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        x[v & 0xffff] += v >> 16;
+        x[(v & 0xffff) * C] += v >> 16;
         tot[OC(l, v & 0xffff)] += v >> 16;
       }
       return;
     }
     if (kind == 1) {
       const int qq = PARENT(c);
-      int32_t* xp = content + (size_t)qq * S;
-      int32_t* w = wrap + (size_t)c * S;
-      int32_t* xc = content + (size_t)c * S;
+      int32_t* xp = content + qq;
+      int32_t* w = wrap + c;
+      int32_t* xc = content + c;
       const int lq = LABEL(qq), lc = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        xp[v & 0xffff] += v >> 16;
+        xp[(v & 0xffff) * C] += v >> 16;
         tot[OC(lq, v & 0xffff)] += v >> 16;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        w[v & 0xffff] += v >> 16;
+        w[(v & 0xffff) * C] += v >> 16;
         tot[OW(lc, v & 0xffff)] += v >> 16;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        xc[v & 0xffff] += v >> 16;
+        xc[(v & 0xffff) * C] += v >> 16;
         tot[OC(lc, v & 0xffff)] += v >> 16;
       }
       return;
@@ -921,26 +926,26 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const unsigned long long alive = *alive_p;
       const unsigned long long freeslots = ~alive & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
       const int e = __ffsll((long long)freeslots) - 1;
-      int32_t* x = content + (size_t)c * S;
+      int32_t* x = content + c;
       const int lctx = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        x[v & 0xffff] += v >> 16;
+        x[(v & 0xffff) * C] += v >> 16;
         tot[OC(lctx, v & 0xffff)] += v >> 16;
       }
-      int32_t* we = wrap + (size_t)e * S;
-      int32_t* xe = content + (size_t)e * S;
+      int32_t* we = wrap + e;
+      int32_t* xe = content + e;
       for (int s = 0; s < S; ++s) {
-        we[s] = 0;
-        xe[s] = 0;
+        we[(s) * C] = 0;
+        xe[(s) * C] = 0;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        we[v & 0xffff] = v >> 16;
+        we[(v & 0xffff) * C] = v >> 16;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        xe[v & 0xffff] = v >> 16;
+        xe[(v & 0xffff) * C] = v >> 16;
       }
       const int lab = rec[CR_CHILD];
       for (int d = 0; d < nd1; ++d) {
@@ -963,12 +968,12 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     // to the parent, children are reparented, the slot is freed
     {
       const int qq = PARENT(c);
-      int32_t* xp = content + (size_t)qq * S;
-      int32_t* w = wrap + (size_t)c * S;
-      int32_t* xc = content + (size_t)c * S;
+      int32_t* xp = content + qq;
+      int32_t* w = wrap + c;
+      int32_t* xc = content + c;
       // per-species change of the parent content: (rhs0 - lhs0) + (w - lhs1) + (xc - lhs2)
       auto delta_at = [&](int s) -> long long {
-        long long dv = (long long)w[s] + xc[s];
+        long long dv = (long long)w[(s) * C] + xc[(s) * C];
         for (int d = 0; d < nd0; ++d) {
           const int v = rec[CR_D0 + d];
           if ((v & 0xffff) == s) dv += v >> 16;
@@ -984,10 +989,10 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const int lq = LABEL(qq), ld = LABEL(c);
       for (int s = 0; s < S; ++s) {
         const long long dv = delta_at(s);
-        xp[s] = (int32_t)((long long)xp[s] + dv);
+        xp[(s) * C] = (int32_t)((long long)xp[(s) * C] + dv);
         tot[OC(lq, s)] += dv;
-        tot[OC(ld, s)] -= xc[s];
-        tot[OW(ld, s)] -= w[s];
+        tot[OC(ld, s)] -= xc[(s) * C];
+        tot[OW(ld, s)] -= w[(s) * C];
       }
       tot[OA(ld)] -= 1;
       unsigned long long kids = chmask[c];
@@ -1002,8 +1007,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       *alive_p &= ~(1ull << c);
       meta[c] = 0;
       for (int s = 0; s < S; ++s) {
-        w[s] = 0;
-        xc[s] = 0;
+        w[(s) * C] = 0;
+        xc[(s) * C] = 0;
       }
     }
   };
@@ -1038,7 +1043,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int c = r0 + gl;
         unsigned long long hc = 0ull;
         if ((rm >> gl) & 1ull) {
-          hc = cwc_count_sum(content, wrap, meta, S, rec, 1ull << c);
+          hc = cwc_count_sum(content, wrap, meta, C, rec, 1ull << c);
           if (hc >> 63) ovf = true;
           hc &= ~(1ull << 63);
         }
@@ -1159,7 +1164,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const unsigned long long Wd = (unsigned long long)w1.x | ((unsigned long long)w1.y << 32);
     const unsigned long long xc = __umul64hi(Wd, HV(j));
     const int ctx = (kGen && rec[CR_KIND] == RK_FUSION)
-                        ? (int)cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), true, xc)
+                        ? (int)cwc_fusion_scan(content, wrap, meta, C, rec, ctx_mask(rec), true, xc)
                         : choose_context(rec, xc);
     // 3. update.  Only contexts in `touched` can change their counts: the
     // rewritten compartments, their children (which read the parent content),
@@ -1167,7 +1172,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     // drops the old counts of its touched contexts and adds the new ones; a
     // rule whose contexts all lie in `touched` is summed afresh.
     const bool general_j = kGen && (rec[CR_KIND] == RK_FUSION || rec[CR_KIND] == RK_NESTED);
-    const int ast = general_j ? cwc_general_check(content, wrap, meta, S, s_rules, rec, ctx)
+    const int ast = general_j ? cwc_general_check(content, wrap, meta, S, C, s_rules, rec, ctx)
                     : kL > 1  ? cwc_apply_check(content, wrap, meta, *alive_p, S, C, rec, ctx)
                               : apply_check(rec, ctx);
     if (ast != TS_OK) {
@@ -1199,7 +1204,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     grp.sync();
     if (gl == 0) {
       if (kGen && general_j)
-        cwc_general_apply(content, wrap, meta, chmask, labmask, alive_p, tot, S, L, s_rules, rec, ctx);
+        cwc_general_apply(content, wrap, meta, chmask, labmask, alive_p, tot, S, L, C, s_rules, rec, ctx);
       else
         apply(rec, ctx);
     }

@@ -90,8 +90,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   double* node = dbase + 32 * T + tid;                          // [16][T] level-1 nodes
   double* Hd = dbase + (32 + 16) * T + tid;                     // score replay only: [M][T]
   // score replay, per trajectory in global memory (set by start()):
-  double* Iac = nullptr;    // [M] int_0^tl_i H_i dt
-  double* tl = nullptr;     // [M]
+  double2* acc = nullptr;   // [M] (int_0^tl_i H_i dt, tl_i): one 16-byte load and store per update
   double* Nf = nullptr;     // [M] firings (whole numbers)
   double* part = nullptr;   // [M] the trajectory's partials
   const double* ik = nullptr;   // [M] 1 / k_i of this sweep point
@@ -197,7 +196,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
         c = __dadd_rn(c, __dmul_rn(gm[o], __dadd_rn((double)CNT(o), -mm[o])));
       const double gt = prm.grid[g];
       for (int i = 0; i < M; ++i) {
-        const double Ig = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(gt, -tl[i])));
+        const double2 a = acc[i];
+        const double Ig = __dadd_rn(a.x, __dmul_rn(Hd[i * T], __dadd_rn(gt, -a.y)));
         // N_i / k_i as N_i * (1 / k_i) (one extra rounding; the division when
         // 1 / k_i overflows, for subnormal k_i)
         const double nk = dbits(ik[i]) < 0x7FF0000000000000ll ? __dmul_rn(Nf[i], ik[i]) : __ddiv_rn(Nf[i], kp[i]);
@@ -234,7 +234,11 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     }
     return hh;
   };
-  auto prop_of = [&](int i) -> double { return __dmul_rn(kp[i], u63_to_double_rn(count_h(i))); };
+  // a_i = k_i H_i; the score replay keeps H_i as doubles in shared memory
+  // (updated for every rule whose count changes), so it reads them there
+  auto prop_of = [&](int i) -> double {
+    return __dmul_rn(kp[i], kSens ? Hd[i * T] : u63_to_double_rn(count_h(i)));
+  };
 
   // leaf l as the blocked sum of its rules (B > 1)
   auto leaf_sum = [&](int l) -> double {
@@ -247,8 +251,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   auto finalize = [&]() {
     if (prm.ckpt != nullptr) {
       int32_t* rec = prm.ckpt + (size_t)q * (S + CKPT_HEADER_WORDS);
-      *reinterpret_cast<double*>(rec) = t;
-      *reinterpret_cast<unsigned long long*>(rec + 2) = h;
+      put_f64(rec, t);
+      put_u64(rec + 2, h);
       rec[4] = (int32_t)n;
       rec[5] = gi;
       rec[6] = status;
@@ -283,8 +287,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     if (prm.resume) {
       const int32_t* rec = prm.ckpt + (size_t)q * (S + CKPT_HEADER_WORDS);
       if (rec[6] != TS_TIMEOUT) return 2;
-      t = *reinterpret_cast<const double*>(rec);
-      h = *reinterpret_cast<const unsigned long long*>(rec + 2);
+      t = get_f64(rec);
+      h = get_u64(rec + 2);
       n = (unsigned)rec[4];
       gi = rec[5];
       if (gi < 0 || gi > G) bad = true;
@@ -297,9 +301,11 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       CNT(s) = v;
     }
     if (kSens) {
-      Iac = prm.sens_acc + (size_t)q * 3 * M;
-      tl = Iac + M;
-      Nf = tl + M;
+      // per trajectory: M (integral, time) pairs, then M firing counts padded
+      // to an even number of doubles, so every pair is 16-byte aligned
+      double* sa = prm.sens_acc + (size_t)q * (2 * M + ((M + 1) & ~1));
+      acc = reinterpret_cast<double2*>(sa);
+      Nf = sa + 2 * M;
       part = prm.partials + (size_t)q * M;
       ik = prm.inv_rates + (size_t)p * M;
       for (int i = 0; i < M; ++i) part[i] = 0.0;
@@ -315,8 +321,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     if (kSens) {
       for (int i = 0; i < M; ++i) {
         Hd[i * T] = u63_to_double_rn(count_h(i));
-        Iac[i] = 0.0;
-        tl[i] = 0.0;
+        acc[i] = make_double2(0.0, 0.0);
         Nf[i] = 0.0;
       }
     }
@@ -331,8 +336,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // after it; the lazily kept integrals are first brought up to t
   auto freeze_h = [&]() {
     for (int i = 0; i < M; ++i) {
-      Iac[i] = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(t, -tl[i])));
-      tl[i] = t;
+      const double2 a = acc[i];
+      acc[i] = make_double2(__dadd_rn(a.x, __dmul_rn(Hd[i * T], __dadd_rn(t, -a.y))), t);
       Hd[i * T] = 0.0;
     }
   };
@@ -358,10 +363,21 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       return 1;
     }
     // the deadline is read every 1024 events, never before a trajectory has
-    // applied 1024 events in this launch, so every launch makes progress
-    if ((n & 1023u) == 0u && n != n_launch && deadline != ~0ull && globaltimer_ns() > deadline) {
-      status = TS_TIMEOUT;
-      return prm.ckpt == nullptr ? 1 : 2;   // with a checkpoint the rest is recorded on resume
+    // applied 1024 events in this launch, so every launch makes progress.
+    // At the same points the tail layout hands the trajectory over to the
+    // warp-per-trajectory kernel once the queue is empty and few trajectories
+    // are left (its checkpoint record carries the state)
+    if ((n & 1023u) == 0u && n != n_launch) {
+      if (deadline != ~0ull && globaltimer_ns() > deadline) {
+        status = TS_TIMEOUT;
+        return prm.ckpt == nullptr ? 1 : 2;   // with a checkpoint the rest is recorded on resume
+      }
+      if (prm.handoff > 0 &&
+          *reinterpret_cast<volatile unsigned long long*>(&prm.ws->queue_next) >= (unsigned long long)Q &&
+          *reinterpret_cast<volatile unsigned long long*>(&prm.ws->running) <= (unsigned long long)prm.handoff) {
+        status = TS_TIMEOUT;
+        return 2;
+      }
     }
     const uint4 w = philox4x32_10(make_uint4(n, 0u, (uint32_t)r + prm.r_offset, (uint32_t)p), prm.key0, prm.key1);
     const double u_tau = uniform52(w.x, w.y);
@@ -406,9 +422,10 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       j = -1;
       double s = 0.0;
       for (int jj = j0; jj < j1; ++jj) {
-        const unsigned long long hh = count_h(jj);
-        if (hh != 0ull) {
-          const double a = __dmul_rn(kp[jj], u63_to_double_rn(hh));
+        // (the score replay has H as a double already: nonzero exactly when H is)
+        const double hdd = kSens ? Hd[jj * T] : u63_to_double_rn(count_h(jj));
+        if (dbits(hdd) != 0) {
+          const double a = __dmul_rn(kp[jj], hdd);
           s = last < 0 ? a : __dadd_rn(s, a);
           last = jj;
           if (dbits(x) < dbits(s)) {
@@ -443,8 +460,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       for (int e = 0; e < dcnt; ++e) {
         const int i = g_deps[doff + e];
         const double hd = u63_to_double_rn(count_h(i));
-        Iac[i] = __dadd_rn(Iac[i], __dmul_rn(Hd[i * T], __dadd_rn(tn, -tl[i])));
-        tl[i] = tn;
+        const double2 a = acc[i];
+        acc[i] = make_double2(__dadd_rn(a.x, __dmul_rn(Hd[i * T], __dadd_rn(tn, -a.y))), tn);
         Hd[i * T] = hd;
       }
     }
@@ -501,12 +518,14 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       if (st0 != 0) continue;
       n_launch = n;
       need_new = false;
+      if (prm.handoff > 0) atomicAdd(&prm.ws->running, 1ull);
     }
     const int ended = step();
     if (ended != 0) {
       if (ended == 1) fill();
       finalize();
       need_new = true;
+      if (prm.handoff > 0) atomicAdd(&prm.ws->running, ~0ull);   // minus one
     }
   }
 #undef LEAF

@@ -197,6 +197,23 @@ __device__ __forceinline__ void add_square_u128(unsigned long long* lohi, int x)
   if (old + v < old) atomicAdd(lohi + 1, 1ull);
 }
 
+// A double / 64-bit word stored as two int32 words (low word first, the
+// bytes of the little-endian 64-bit value) at any 4-byte-aligned address:
+// checkpoint records are int32 arrays whose length can be odd, so their
+// 64-bit fields are not always 8-byte aligned.
+__device__ __forceinline__ void put_f64(int32_t* p, double v) {
+  p[0] = __double2loint(v);
+  p[1] = __double2hiint(v);
+}
+__device__ __forceinline__ double get_f64(const int32_t* p) { return __hiloint2double(p[1], p[0]); }
+__device__ __forceinline__ void put_u64(int32_t* p, unsigned long long v) {
+  p[0] = (int32_t)(uint32_t)v;
+  p[1] = (int32_t)(uint32_t)(v >> 32);
+}
+__device__ __forceinline__ unsigned long long get_u64(const int32_t* p) {
+  return (unsigned long long)(uint32_t)p[0] | ((unsigned long long)(uint32_t)p[1] << 32);
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -77,6 +77,13 @@ def test_sweep256x256_full_size_sampled():
     pmax, pmin = int(torch.argmax(ev)), int(torch.argmin(ev))
     qs = np.unique(np.concatenate([sample_indices(b.n_traj, 10, 2), [pmax * b.R + 3, pmin * b.R + 5]]))
     check_sampled(b, res, qs)
+    # the tail layout (last trajectories finished by one warp each) gives the
+    # whole batch bit for bit
+    tail = api.simulate(cm, rates, init, grid, b.R, b.seed, b.max_events, states=True,
+                        layout=capi.CWC_LAYOUT_TAIL)
+    torch.cuda.synchronize()
+    for k in ("states", "status", "events", "hash", "final_t"):
+        assert torch.equal(tail[k], res[k]), k
 
 
 def test_flat16x24_full_size_forward_and_score_properties():

@@ -125,3 +125,27 @@ def test_general_model_checkpoint_resume_equals_one_launch():
     torch.cuda.synchronize()
     for k in ("states", "status", "events", "hash", "final_t"):
         assert torch.equal(one[k], sl[k]), k
+
+
+def test_checkpoint_records_of_odd_length():
+    """A term of 7 slots x (3 + 2 S) words makes 43-word checkpoint records,
+    so every other record's 64-bit fields (time, hash) sit on a 4-byte
+    boundary; time-sliced runs must still equal one launch."""
+    m = W.cwc_model(1, 3, 7, [W.RuleSpec(W.NESTED, 0, 1, grand_label=2, lhs_child2={0: 1}, rhs_ctx={0: 1}),
+                              W.RuleSpec(W.LOCAL, 0, lhs_ctx={0: 1}, rhs_ctx={0: 2})])
+    img = W.empty_slot_image(m)
+    img[1, :3] = [1, 1, 0]
+    img[2, :3] = [1, 2, 1]
+    img[2, 4] = 3000
+    img[3, :3] = [1, 1, 0]
+    img[4, :3] = [1, 2, 3]
+    img[4, 4] = 3000
+    b = W.Batch(m, np.array([[1.0, 0.001]]), img[None], W.uniform_grid(2.0, 9), 33, 21)
+    assert capi.cwc_checkpoint_words(api.CompiledModel(b.model).handle) % 2 == 1
+    cm = api.CompiledModel(b.model)
+    rates, init, grid = api.device_inputs(b)
+    one = api.simulate(cm, rates, init, grid, b.R, b.seed, lanes=1)
+    sl, n = api.simulate_sliced(cm, rates, init, grid, b.R, b.seed, slice_ns=50_000, lanes=1)
+    torch.cuda.synchronize()
+    for k in ("states", "status", "events", "hash", "final_t"):
+        assert torch.equal(one[k], sl[k]), k
