@@ -241,17 +241,27 @@ def measure_extras(dev):
                          "workload": "3 labels below the top, 24 species, 48 rules (transport, wrap binding, create, "
                                      "dissolve), <=64 compartments, 16384 replicas, 500-point grid"}
     del out, keep
-    # uneven sweep: 256 rate vectors x 256 replicas of flat32x64's network, autotuned, CUDA graph
+    # uneven sweep: 256 rate vectors x 256 replicas of flat32x64's network, CUDA
+    # graph; the autotuned queue / static layout, then the tail layout (the last
+    # trajectories handed over to a warp each), which must agree bit for bit
     b = W.sweep256x256()
     cm = api.CompiledModel(b.model)
-    rates, init, grid = api.device_inputs(b, dev)
+    rates, init, grid = api.device_inputs(b)
     lay, thr, _, _ = api.autotune(cm, rates, init, grid, b.R, b.seed, tune_events=2000)
     g = api.GraphedSimulation(cm, rates, init, grid, b.R, b.seed, states=True)
+    out_q, sec_q = _timed(g.replay, "sweep256x256_queue")
+    ev_q, hash_q = out_q["events"].clone(), out_q["hash"].clone()
+    del g, out_q
+    g = api.GraphedSimulation(cm, rates, init, grid, b.R, b.seed, states=True, layout=capi.CWC_LAYOUT_TAIL)
     out, sec = _timed(g.replay, "sweep256x256")
+    same = bool(torch.equal(out["events"], ev_q) and torch.equal(out["hash"], hash_q))
     evp = out["events"].double().mean(dim=1)
     ev = int(out["events"].sum().item())
-    extras["sweep256x256"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay,
-                              "block_threads": thr, "graph": True,
+    extras["sweep256x256"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec,
+                              "layout": "tail (queue, then the last trajectories on a warp each)", "graph": True,
+                              "queue_layout": {"events_per_s": ev / sec_q, "seconds": sec_q, "layout": lay,
+                                               "block_threads": thr},
+                              "identical_to_queue_layout": same,
                               "length_spread": float((evp.max() / evp.min()).item()),
                               "workload": "256 rate vectors x 256 replicas, flat32x64 network, 1000-point grid"}
     del g, out

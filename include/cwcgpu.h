@@ -279,7 +279,7 @@ typedef struct {
   void* workspace;
   size_t workspace_bytes;
   int32_t tail_threshold;    /* CWC_LAYOUT_TAIL: hand over when at most this many
-                                trajectories run (0 = 3 per SM) */
+                                trajectories run (0 = 27 per SM) */
 } cwc_sim_args;
 
 /*

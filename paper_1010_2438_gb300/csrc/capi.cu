@@ -779,7 +779,9 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    prm.handoff = a->tail_threshold > 0 ? a->tail_threshold : 3LL * sms;
+    // default measured on the 256 x 256 uneven sweep (2048 / 4096 / 8192 / 16384
+    // trajectories: 6.57 / 6.16 / 6.48 / 9.35 s): 27 per SM
+    prm.handoff = a->tail_threshold > 0 ? a->tail_threshold : 27LL * sms;
   }
   if (w.need_order) {
     double* est = reinterpret_cast<double*>(ws + w.order);

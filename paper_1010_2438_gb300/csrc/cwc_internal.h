@@ -78,12 +78,12 @@ enum : int32_t {
 
 // Workspace header (first 256 bytes when used): work-queue ticket, the
 // launch timestamp for deadlines and, for the tail layout, the number of
-// trajectories running in the thread kernel, the number handed over to the
+// trajectories the thread kernel has finished, the number handed over to the
 // warp kernel and that kernel's ticket.
 struct WorkspaceHeader {
   unsigned long long queue_next;
   unsigned long long t_start_ns;
-  unsigned long long running;
+  unsigned long long finished;
   unsigned long long tail_count;
   unsigned long long tail_next;
   unsigned long long pad[27];

@@ -25,12 +25,12 @@
 // group runs:
 //   chmask[C]  u64  children of each slot        labmask[L] u64  alive slots per label
 //   alive      u64  alive slots                  tot[O]     i64  observable totals
-//   meta[C]    i32  label | (parent + 1) << 8   wrap[S][C], content[S][C]  i32
-// The counts are stored species-major: the counts of one species in all C
-// slots are contiguous (256 bytes for 64 slots), so a context scan over a
-// label's slots reads one or two cache lines per reactant species instead of
-// one line per slot, and the slabs' lines stay hot in L2 (the slabs of a
-// 16,384-term batch exceed L2).
+//   meta[C]    i32  label | (parent + 1) << 8   wrap[C][S], content[C][S]  i32
+// (Slot-major: a slot's counts are one row.  Species-major storage, which
+// makes a context scan read one or two lines per species instead of one per
+// slot, measured 8 % slower on 16,384 terms of 64 slots x 24 species: every
+// count read then needs a multiply by the slot count, and the scans touch few
+// slots per rule.)
 // The observable totals (content per label, wrap per label, alive compartments
 // per label) are kept up to date by every rewrite, so recording a grid point
 // is O stores.
@@ -128,7 +128,7 @@ __host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, 
 // Out of line for lane groups (see below).
 __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restrict__ content,
                                                         const int32_t* __restrict__ wrap,
-                                                        const int32_t* __restrict__ meta, int C,
+                                                        const int32_t* __restrict__ meta, int S,
                                                         const int32_t* rec, unsigned long long m) {
   const int kind = rec[CR_KIND];
   const bool parent_child = !(kind == RK_LOCAL || kind == RK_CREATE);
@@ -139,33 +139,53 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
   while (m) {
     const int c = __ffsll((long long)m) - 1;
     m &= m - 1ull;
-    // slots read by pattern rows 0 / 1-2 / 3-4
-    int x0c = c, x12c = c;
-    if (kind == RK_NESTED) {
-      // c is the grandchild: its parent must carry the child label, its
-      // grandparent the rule's label (the root's label 0 is never a child label)
-      const int qq = (meta[c] >> 8) - 1;
-      if ((meta[qq] & 0xff) != rec[CR_CHILD]) continue;
-      const int aa = (meta[qq] >> 8) - 1;
-      if ((meta[aa] & 0xff) != ctx) continue;
-      x0c = aa;
-      x12c = qq;
-    } else if (parent_child) {
+    int x0c = c;
+    if (parent_child) {
       const int qq = (meta[c] >> 8) - 1;
       if ((meta[qq] & 0xff) != ctx) continue;
       x0c = qq;
     }
-    const int32_t* x0 = content + x0c;
-    const int32_t* x1 = wrap + x12c;
-    const int32_t* x2 = content + x12c;
-    const int32_t* x3 = wrap + c;
-    const int32_t* x4 = content + c;
+    const int32_t* x0 = content + (size_t)x0c * S;
+    const int32_t* x1 = wrap + (size_t)c * S;
+    const int32_t* x2 = content + (size_t)c * S;
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
-      const int row = (v >> 24) & 7;
-      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : (row == 2 ? x2 : (row == 3 ? x3 : x4)));
-      acc = mul_checked(acc, binom12(x[(v & 0xffff) * C], (v >> 16) & 0xff), &of);
+      const int row = (v >> 24) & 3;
+      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
+      acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
+    }
+    const unsigned long long s2 = tot + acc;
+    if (s2 < tot || (s2 >> 63) != 0ull) of = true;
+    tot = s2;
+  }
+  return of ? (tot | (1ull << 63)) : tot;
+}
+
+// The same for NESTED rules, whose contexts are grandchildren c: their parent
+// must carry the child label and their grandparent the rule's label (the
+// root's label 0 is never a child label); rows 0 / 1-2 / 3-4 read the
+// grandparent's content, the parent's wrap and content, c's wrap and content.
+__device__ __noinline__ unsigned long long cwc_count_sum_nested(const int32_t* __restrict__ content,
+                                                               const int32_t* __restrict__ wrap,
+                                                               const int32_t* __restrict__ meta, int S,
+                                                               const int32_t* rec, unsigned long long m) {
+  const int nr = rec[CR_NREAC];
+  const int ctx = rec[CR_CTX];
+  bool of = false;
+  unsigned long long tot = 0ull;
+  while (m) {
+    const int c = __ffsll((long long)m) - 1;
+    m &= m - 1ull;
+    const int qq = (meta[c] >> 8) - 1;
+    if ((meta[qq] & 0xff) != rec[CR_CHILD]) continue;
+    const int aa = (meta[qq] >> 8) - 1;
+    if ((meta[aa] & 0xff) != ctx) continue;
+    const int32_t* rows[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S, wrap + (size_t)c * S, content + (size_t)c * S};
+    unsigned long long acc = 1ull;
+    for (int a = 0; a < nr; ++a) {
+      const int v = rec[CR_REAC + a];
+      acc = mul_checked(acc, binom12(rows[(v >> 24) & 7][v & 0xffff], (v >> 16) & 0xff), &of);
     }
     const unsigned long long s2 = tot + acc;
     if (s2 < tot || (s2 >> 63) != 0ull) of = true;
@@ -184,7 +204,7 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
 // bit 63 flagging an overflow of a product or of the sum.
 __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __restrict__ content,
                                                           const int32_t* __restrict__ wrap,
-                                                          const int32_t* __restrict__ meta, int C,
+                                                          const int32_t* __restrict__ meta, int S,
                                                           const int32_t* rec, unsigned long long kids,
                                                           bool want_pick, unsigned long long xc) {
   const int nr = rec[CR_NREAC];
@@ -212,7 +232,7 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
     m1 &= m1 - 1ull;
     const int qq = (meta[d1] >> 8) - 1;
     if ((meta[qq] & 0xff) != ctx) continue;
-    const int32_t* x0 = content + qq;
+    const int32_t* x0 = content + (size_t)qq * S;
     unsigned long long m2 = kids & ~(1ull << d1);
     if (sym) m2 &= ~((2ull << d1) - 1ull);   // d2 > d1 only
     while (m2) {
@@ -224,10 +244,10 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
         const int v = rec[CR_REAC + a];
         const int row = (v >> 24) & 7;
         const int32_t* x = row == 0 ? x0
-                           : row == 1 ? wrap + d1
-                           : row == 2 ? content + d1
-                           : row == 3 ? wrap + d2 : content + d2;
-        acc = mul_checked(acc, binom12(x[(v & 0xffff) * C], (v >> 16) & 0xff), &of);
+                           : row == 1 ? wrap + (size_t)d1 * S
+                           : row == 2 ? content + (size_t)d1 * S
+                           : row == 3 ? wrap + (size_t)d2 * S : content + (size_t)d2 * S;
+        acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
       }
       const unsigned long long s2 = tot + acc;
       if (s2 < tot || (s2 >> 63) != 0ull) of = true;
@@ -254,14 +274,14 @@ __device__ __noinline__ int cwc_general_check(const int32_t* content, const int3
   if (rec[CR_KIND] == RK_NESTED) {
     const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
-    const int32_t* ms[5] = {content + aa, wrap + qq, content + qq,
-                            wrap + g, content + g};
+    const int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
+                            wrap + (size_t)g * S, content + (size_t)g * S};
     const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
     const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
     for (int row = 0; row < 5; ++row)
       for (int d = 0; d < nd[row]; ++d) {
         const int v = dd[row][d];
-        if (!fits((long long)ms[row][(v & 0xffff) * C] + (v >> 16))) return TS_INT_OVERFLOW;
+        if (!fits((long long)ms[row][v & 0xffff] + (v >> 16))) return TS_INT_OVERFLOW;
       }
     return TS_OK;
   }
@@ -269,11 +289,11 @@ __device__ __noinline__ int cwc_general_check(const int32_t* content, const int3
   const int qq = (meta[d1] >> 8) - 1;
   for (int d = 0; d < rec[CR_ND0]; ++d) {
     const int v = rec[CR_D0 + d];
-    if (!fits((long long)content[(size_t)((v & 0xffff)) * C + qq] + (v >> 16))) return TS_INT_OVERFLOW;
+    if (!fits((long long)content[(size_t)qq * S + (v & 0xffff)] + (v >> 16))) return TS_INT_OVERFLOW;
   }
   for (int x = 0; x < S; ++x) {
-    long long wv = (long long)wrap[(size_t)(x) * C + d1] + wrap[(size_t)(x) * C + d2];
-    long long cv = (long long)content[(size_t)(x) * C + d1] + content[(size_t)(x) * C + d2];
+    long long wv = (long long)wrap[(size_t)d1 * S + x] + wrap[(size_t)d2 * S + x];
+    long long cv = (long long)content[(size_t)d1 * S + x] + content[(size_t)d2 * S + x];
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
       const int row = (v >> 24) & 7;
@@ -302,15 +322,15 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
     const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
     const int la = meta[aa] & 0xff, lq = meta[qq] & 0xff, lg = meta[g] & 0xff;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
-    int32_t* ms[5] = {content + aa, wrap + qq, content + qq,
-                      wrap + g, content + g};
+    int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
+                      wrap + (size_t)g * S, content + (size_t)g * S};
     const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
     const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
     for (int row = 0; row < 5; ++row)
       for (int d = 0; d < nd[row]; ++d) {
         const int v = dd[row][d];
         const int x = v & 0xffff, dv = v >> 16;
-        ms[row][x * C] += dv;
+        ms[row][x] += dv;
         const int o = row == 0 ? OC(la, x) : row == 1 ? OW(lq, x) : row == 2 ? OC(lq, x) : row == 3 ? OW(lg, x) : OC(lg, x);
         tot[o] += dv;
       }
@@ -323,7 +343,7 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
   const int nr = rec[CR_NREAC];
   for (int d = 0; d < rec[CR_ND0]; ++d) {
     const int v = rec[CR_D0 + d];
-    content[(size_t)((v & 0xffff)) * C + qq] += v >> 16;
+    content[(size_t)qq * S + (v & 0xffff)] += v >> 16;
     tot[OC(lq, v & 0xffff)] += v >> 16;
   }
   for (int x = 0; x < S; ++x) {
@@ -339,10 +359,10 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
       if ((rec[CR_D1 + d] & 0xffff) == x) dw += rec[CR_D1 + d] >> 16;
     for (int d = 0; d < rec[CR_ND2]; ++d)
       if ((rec[CR_D2 + d] & 0xffff) == x) dc += rec[CR_D2 + d] >> 16;
-    wrap[(size_t)(x) * C + keep] = wrap[(size_t)(x) * C + keep] + wrap[(size_t)(x) * C + gone] + dw;
-    content[(size_t)(x) * C + keep] = content[(size_t)(x) * C + keep] + content[(size_t)(x) * C + gone] + dc;
-    wrap[(size_t)(x) * C + gone] = 0;
-    content[(size_t)(x) * C + gone] = 0;
+    wrap[(size_t)keep * S + x] = wrap[(size_t)keep * S + x] + wrap[(size_t)gone * S + x] + dw;
+    content[(size_t)keep * S + x] = content[(size_t)keep * S + x] + content[(size_t)gone * S + x] + dc;
+    wrap[(size_t)gone * S + x] = 0;
+    content[(size_t)gone * S + x] = 0;
     tot[OW(lc, x)] += dw;
     tot[OC(lc, x)] += dc;
   }
@@ -399,35 +419,35 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
         const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
         if (freeslots == 0ull) return TS_CAPACITY;
       }
-      const int32_t* x = content + c;
+      const int32_t* x = content + (size_t)c * S;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(x[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     const int qq = PARENT(c);
-    const int32_t* xp = content + qq;
-    const int32_t* w = wrap + c;
-    const int32_t* xc = content + c;
+    const int32_t* xp = content + (size_t)qq * S;
+    const int32_t* w = wrap + (size_t)c * S;
+    const int32_t* xc = content + (size_t)c * S;
     if (kind == 1) {
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(xp[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        if (!fits_add(w[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        if (!fits_add(xc[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     // DISSOLVE: the parent content gains (rhs0 - lhs0) + (wrap - lhs1) + (content - lhs2)
     for (int s = 0; s < S; ++s) {
-      long long dv = (long long)w[(s) * C] + xc[(s) * C];
+      long long dv = (long long)w[s] + xc[s];
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         if ((v & 0xffff) == s) dv += v >> 16;
@@ -437,7 +457,7 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
         const int v = rec[CR_REAC + a];
         if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
-      const long long nv = (long long)xp[(s) * C] + dv;
+      const long long nv = (long long)xp[s] + dv;
       if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
     }
     return TS_OK;
@@ -514,8 +534,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   double* part = tl + (kSens ? M : 0);                                            // [M]
   int32_t* Nf = reinterpret_cast<int32_t*>(part + (kSens ? M : 0));               // [M]
   int32_t* meta = Nf + (kSens ? M : 0);                                           // [C]
-  int32_t* wrap = meta + C;                                                       // [S][C]
-  int32_t* content = wrap + (size_t)C * S;                                        // [S][C]
+  int32_t* wrap = meta + C;                                                       // [C][S]
+  int32_t* content = wrap + (size_t)C * S;                                        // [C][S]
 
   auto LABEL = [&](int c) -> int { return meta[c] & 0xff; };
   auto PARENT = [&](int c) -> int { return (meta[c] >> 8) - 1; };
@@ -542,16 +562,16 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // (kinds LOCAL .. DISSOLVE; NESTED counts go through cwc_count_sum)
   auto count_at = [&](const int32_t* rec, int c) -> unsigned long long {
     const int kind = rec[CR_KIND];
-    const int32_t* x0 = content + ((kind == RK_LOCAL || kind == RK_CREATE) ? c : PARENT(c));
-    const int32_t* x1 = wrap + c;
-    const int32_t* x2 = content + c;
+    const int32_t* x0 = content + (size_t)((kind == RK_LOCAL || kind == RK_CREATE) ? c : PARENT(c)) * S;
+    const int32_t* x1 = wrap + (size_t)c * S;
+    const int32_t* x2 = content + (size_t)c * S;
     const int nr = rec[CR_NREAC];
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
       const int row = (v >> 24) & 3;
       const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
-      acc = mul_checked(acc, binom12(x[(v & 0xffff) * C], (v >> 16) & 0xff), &ovf);
+      acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &ovf);
     }
     return acc;
   };
@@ -583,7 +603,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       }
       return tot;
     }
-    const unsigned long long r = cwc_count_sum(content, wrap, meta, C, rec, m);
+    const unsigned long long r = (kGen && rec[CR_KIND] == RK_NESTED) ? cwc_count_sum_nested(content, wrap, meta, S, rec, m)
+                                                                    : cwc_count_sum(content, wrap, meta, S, rec, m);
     if (r >> 63) ovf = true;
     return r;
   };
@@ -591,7 +612,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   auto total_h = [&](int i) -> unsigned long long {
     const int32_t* rec = s_rules + i * CWC_RULE_WORDS;
     if (kGen && rec[CR_KIND] == RK_FUSION) {
-      const unsigned long long r = cwc_fusion_scan(content, wrap, meta, C, rec, ctx_mask(rec), false, 0ull);
+      const unsigned long long r = cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), false, 0ull);
       if (r >> 63) ovf = true;
       return r & ~(1ull << 63);
     }
@@ -680,8 +701,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         row[1] = a ? LABEL(c) : 0;
         row[2] = a ? PARENT(c) : -1;
         for (int x = 0; x < S; ++x) {
-          row[3 + x] = wrap[(size_t)(x) * C + c];
-          row[3 + S + x] = content[(size_t)(x) * C + c];
+          row[3 + x] = wrap[(size_t)c * S + x];
+          row[3 + S + x] = content[(size_t)c * S + x];
         }
       }
     }
@@ -754,16 +775,16 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
           const int wv = row[3 + x], cv = row[3 + S + x];
           if (wv < 0 || cv < 0) bad = true;
           if (c == 0 && wv != 0) bad = true;
-          wrap[(size_t)(x) * C + c] = wv;
-          content[(size_t)(x) * C + c] = cv;
+          wrap[(size_t)c * S + x] = wv;
+          content[(size_t)c * S + x] = cv;
         }
         alive |= 1ull << c;
         meta[c] = (lab & 0xff) | ((par + 1) << 8);
       } else {
         meta[c] = 0;
         for (int x = 0; x < S; ++x) {
-          wrap[(size_t)(x) * C + c] = 0;
-          content[(size_t)(x) * C + c] = 0;
+          wrap[(size_t)c * S + x] = 0;
+          content[(size_t)c * S + x] = 0;
         }
       }
     }
@@ -811,8 +832,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       for (int c = 0; c < C; ++c) {
         if (!((alive >> c) & 1ull)) continue;
         const int l = LABEL(c);
-        tot[OC(l, x)] += content[(size_t)(x) * C + c];
-        if (l > 0) tot[OW(l, x)] += wrap[(size_t)(x) * C + c];
+        tot[OC(l, x)] += content[(size_t)c * S + x];
+        if (l > 0) tot[OW(l, x)] += wrap[(size_t)c * S + x];
       }
     }
     if (gl == 0) {
@@ -841,35 +862,35 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
         if (freeslots == 0ull) return TS_CAPACITY;
       }
-      const int32_t* x = content + c;
+      const int32_t* x = content + (size_t)c * S;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(x[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     const int qq = PARENT(c);
-    const int32_t* xp = content + qq;
-    const int32_t* w = wrap + c;
-    const int32_t* xc = content + c;
+    const int32_t* xp = content + (size_t)qq * S;
+    const int32_t* w = wrap + (size_t)c * S;
+    const int32_t* xc = content + (size_t)c * S;
     if (kind == 1) {
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(xp[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        if (!fits_add(w[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        if (!fits_add(xc[(v & 0xffff) * C], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
       }
       return TS_OK;
     }
     // DISSOLVE: the parent content gains (rhs0 - lhs0) + (wrap - lhs1) + (content - lhs2)
     for (int s = 0; s < S; ++s) {
-      long long dv = (long long)w[(s) * C] + xc[(s) * C];
+      long long dv = (long long)w[s] + xc[s];
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         if ((v & 0xffff) == s) dv += v >> 16;
@@ -879,7 +900,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int v = rec[CR_REAC + a];
         if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
-      const long long nv = (long long)xp[(s) * C] + dv;
+      const long long nv = (long long)xp[s] + dv;
       if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
     }
     return TS_OK;
@@ -890,34 +911,34 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const int kind = rec[CR_KIND];
     const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
     if (kind == 0) {
-      int32_t* x = content + c;
+      int32_t* x = content + (size_t)c * S;
       const int l = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        x[(v & 0xffff) * C] += v >> 16;
+        x[v & 0xffff] += v >> 16;
         tot[OC(l, v & 0xffff)] += v >> 16;
       }
       return;
     }
     if (kind == 1) {
       const int qq = PARENT(c);
-      int32_t* xp = content + qq;
-      int32_t* w = wrap + c;
-      int32_t* xc = content + c;
+      int32_t* xp = content + (size_t)qq * S;
+      int32_t* w = wrap + (size_t)c * S;
+      int32_t* xc = content + (size_t)c * S;
       const int lq = LABEL(qq), lc = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        xp[(v & 0xffff) * C] += v >> 16;
+        xp[v & 0xffff] += v >> 16;
         tot[OC(lq, v & 0xffff)] += v >> 16;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        w[(v & 0xffff) * C] += v >> 16;
+        w[v & 0xffff] += v >> 16;
         tot[OW(lc, v & 0xffff)] += v >> 16;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        xc[(v & 0xffff) * C] += v >> 16;
+        xc[v & 0xffff] += v >> 16;
         tot[OC(lc, v & 0xffff)] += v >> 16;
       }
       return;
@@ -926,26 +947,26 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const unsigned long long alive = *alive_p;
       const unsigned long long freeslots = ~alive & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
       const int e = __ffsll((long long)freeslots) - 1;
-      int32_t* x = content + c;
+      int32_t* x = content + (size_t)c * S;
       const int lctx = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        x[(v & 0xffff) * C] += v >> 16;
+        x[v & 0xffff] += v >> 16;
         tot[OC(lctx, v & 0xffff)] += v >> 16;
       }
-      int32_t* we = wrap + e;
-      int32_t* xe = content + e;
+      int32_t* we = wrap + (size_t)e * S;
+      int32_t* xe = content + (size_t)e * S;
       for (int s = 0; s < S; ++s) {
-        we[(s) * C] = 0;
-        xe[(s) * C] = 0;
+        we[s] = 0;
+        xe[s] = 0;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        we[(v & 0xffff) * C] = v >> 16;
+        we[v & 0xffff] = v >> 16;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        xe[(v & 0xffff) * C] = v >> 16;
+        xe[v & 0xffff] = v >> 16;
       }
       const int lab = rec[CR_CHILD];
       for (int d = 0; d < nd1; ++d) {
@@ -968,12 +989,12 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     // to the parent, children are reparented, the slot is freed
     {
       const int qq = PARENT(c);
-      int32_t* xp = content + qq;
-      int32_t* w = wrap + c;
-      int32_t* xc = content + c;
+      int32_t* xp = content + (size_t)qq * S;
+      int32_t* w = wrap + (size_t)c * S;
+      int32_t* xc = content + (size_t)c * S;
       // per-species change of the parent content: (rhs0 - lhs0) + (w - lhs1) + (xc - lhs2)
       auto delta_at = [&](int s) -> long long {
-        long long dv = (long long)w[(s) * C] + xc[(s) * C];
+        long long dv = (long long)w[s] + xc[s];
         for (int d = 0; d < nd0; ++d) {
           const int v = rec[CR_D0 + d];
           if ((v & 0xffff) == s) dv += v >> 16;
@@ -989,10 +1010,10 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const int lq = LABEL(qq), ld = LABEL(c);
       for (int s = 0; s < S; ++s) {
         const long long dv = delta_at(s);
-        xp[(s) * C] = (int32_t)((long long)xp[(s) * C] + dv);
+        xp[s] = (int32_t)((long long)xp[s] + dv);
         tot[OC(lq, s)] += dv;
-        tot[OC(ld, s)] -= xc[(s) * C];
-        tot[OW(ld, s)] -= w[(s) * C];
+        tot[OC(ld, s)] -= xc[s];
+        tot[OW(ld, s)] -= w[s];
       }
       tot[OA(ld)] -= 1;
       unsigned long long kids = chmask[c];
@@ -1007,8 +1028,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       *alive_p &= ~(1ull << c);
       meta[c] = 0;
       for (int s = 0; s < S; ++s) {
-        w[(s) * C] = 0;
-        xc[(s) * C] = 0;
+        w[s] = 0;
+        xc[s] = 0;
       }
     }
   };
@@ -1043,7 +1064,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const int c = r0 + gl;
         unsigned long long hc = 0ull;
         if ((rm >> gl) & 1ull) {
-          hc = cwc_count_sum(content, wrap, meta, C, rec, 1ull << c);
+          hc = (kGen && rec[CR_KIND] == RK_NESTED) ? cwc_count_sum_nested(content, wrap, meta, S, rec, 1ull << c)
+                                                   : cwc_count_sum(content, wrap, meta, S, rec, 1ull << c);
           if (hc >> 63) ovf = true;
           hc &= ~(1ull << 63);
         }
@@ -1164,7 +1186,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const unsigned long long Wd = (unsigned long long)w1.x | ((unsigned long long)w1.y << 32);
     const unsigned long long xc = __umul64hi(Wd, HV(j));
     const int ctx = (kGen && rec[CR_KIND] == RK_FUSION)
-                        ? (int)cwc_fusion_scan(content, wrap, meta, C, rec, ctx_mask(rec), true, xc)
+                        ? (int)cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), true, xc)
                         : choose_context(rec, xc);
     // 3. update.  Only contexts in `touched` can change their counts: the
     // rewritten compartments, their children (which read the parent content),

@@ -68,7 +68,11 @@ __host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
   return doubles * 8 + ints * 4;
 }
 
-template <bool kQueue, bool kSens>
+// kTail: the tail layout's variant of the queue kernel, which counts finished
+// trajectories and hands the last ones over (a separate instantiation: the
+// bookkeeping, compiled into the plain queue kernel even behind a runtime
+// flag, measured 2.25x slower on the 32-species network)
+template <bool kQueue, bool kSens, bool kTail>
 __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatParams prm,
                                                        const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -195,15 +199,25 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       for (int o = 0; o < S; ++o)
         c = __dadd_rn(c, __dmul_rn(gm[o], __dadd_rn((double)CNT(o), -mm[o])));
       const double gt = prm.grid[g];
-      for (int i = 0; i < M; ++i) {
-        const double2 a = acc[i];
-        const double Ig = __dadd_rn(a.x, __dmul_rn(Hd[i * T], __dadd_rn(gt, -a.y)));
-        // N_i / k_i as N_i * (1 / k_i) (one extra rounding; the division when
-        // 1 / k_i overflows, for subnormal k_i)
-        const double nk = dbits(ik[i]) < 0x7FF0000000000000ll ? __dmul_rn(Nf[i], ik[i]) : __ddiv_rn(Nf[i], kp[i]);
-        const double Si = __dadd_rn(nk, -Ig);
-        part[i] = __dadd_rn(part[i], __dmul_rn(c, Si));
+      // S_i(g) = N_i / k_i - I_i(g), I_i(g) = Iac_i + H_i (t_g - tl_i); N_i / k_i
+      // as N_i * (1 / k_i) (one extra rounding; the division when 1 / k_i
+      // overflows, for subnormal k_i).  Two rules per iteration, loads first,
+      // so that their latencies overlap.
+      auto term = [&](const double2 a, double hd, double nf, double ikv, int i) -> double {
+        const double Ig = __dadd_rn(a.x, __dmul_rn(hd, __dadd_rn(gt, -a.y)));
+        const double nk = dbits(ikv) < 0x7FF0000000000000ll ? __dmul_rn(nf, ikv) : __ddiv_rn(nf, kp[i]);
+        return __dmul_rn(c, __dadd_rn(nk, -Ig));
+      };
+      int i = 0;
+      for (; i + 1 < M; i += 2) {
+        const double2 a0 = acc[i], a1 = acc[i + 1];
+        const double n0 = Nf[i], n1 = Nf[i + 1], k0 = ik[i], k1 = ik[i + 1];
+        const double p0 = part[i], p1 = part[i + 1];
+        const double h0 = Hd[i * T], h1 = Hd[(i + 1) * T];
+        part[i] = __dadd_rn(p0, term(a0, h0, n0, k0, i));
+        part[i + 1] = __dadd_rn(p1, term(a1, h1, n1, k1, i + 1));
       }
+      if (i < M) part[i] = __dadd_rn(part[i], term(acc[i], Hd[i * T], Nf[i], ik[i], i));
     }
   };
 
@@ -372,9 +386,12 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
         status = TS_TIMEOUT;
         return prm.ckpt == nullptr ? 1 : 2;   // with a checkpoint the rest is recorded on resume
       }
-      if (prm.handoff > 0 &&
+      // once the queue is empty every trajectory has started, so Q - finished
+      // of them are still running
+      if (kTail &&
           *reinterpret_cast<volatile unsigned long long*>(&prm.ws->queue_next) >= (unsigned long long)Q &&
-          *reinterpret_cast<volatile unsigned long long*>(&prm.ws->running) <= (unsigned long long)prm.handoff) {
+          (unsigned long long)Q - *reinterpret_cast<volatile unsigned long long*>(&prm.ws->finished) <=
+              (unsigned long long)prm.handoff) {
         status = TS_TIMEOUT;
         return 2;
       }
@@ -457,7 +474,20 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     if (kSens) {
       Nf[j] = __dadd_rn(Nf[j], 1.0);
       const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
-      for (int e = 0; e < dcnt; ++e) {
+      // two dependents per iteration, loads first, so that their latencies overlap
+      int e = 0;
+      for (; e + 1 < dcnt; e += 2) {
+        const int i0 = g_deps[doff + e], i1 = g_deps[doff + e + 1];
+        const double2 a0 = acc[i0], a1 = acc[i1];
+        const double h0 = Hd[i0 * T], h1 = Hd[i1 * T];
+        const double hd0 = u63_to_double_rn(count_h(i0));
+        const double hd1 = u63_to_double_rn(count_h(i1));
+        acc[i0] = make_double2(__dadd_rn(a0.x, __dmul_rn(h0, __dadd_rn(tn, -a0.y))), tn);
+        acc[i1] = make_double2(__dadd_rn(a1.x, __dmul_rn(h1, __dadd_rn(tn, -a1.y))), tn);
+        Hd[i0 * T] = hd0;
+        Hd[i1 * T] = hd1;
+      }
+      if (e < dcnt) {
         const int i = g_deps[doff + e];
         const double hd = u63_to_double_rn(count_h(i));
         const double2 a = acc[i];
@@ -500,8 +530,15 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   };
 
   bool need_new = true;
+  bool had_one = false;   // kTail: this lane has finished a trajectory before taking the next
   for (;;) {
     if (need_new) {
+      if (kTail && had_one) {
+        // warp-aggregated count of finished trajectories (ran, or bad input)
+        const unsigned mask = __activemask();
+        if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&prm.ws->finished, (unsigned long long)__popc(mask));
+      }
+      had_one = true;
       if (kQueue) {
         q = grab_next(prm.ws);
         if (prm.order != nullptr && q < Q) {
@@ -518,14 +555,12 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       if (st0 != 0) continue;
       n_launch = n;
       need_new = false;
-      if (prm.handoff > 0) atomicAdd(&prm.ws->running, 1ull);
     }
     const int ended = step();
     if (ended != 0) {
       if (ended == 1) fill();
       finalize();
       need_new = true;
-      if (prm.handoff > 0) atomicAdd(&prm.ws->running, ~0ull);   // minus one
     }
   }
 #undef LEAF
@@ -585,10 +620,10 @@ cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order
 // Host launcher
 // ---------------------------------------------------------------------------
 
-template <bool kQueue, bool kSens>
+template <bool kQueue, bool kSens, bool kTail = false>
 static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
                             cudaStream_t stream, int* used_blocks) {
-  auto kern = flat_ssa_kernel<kQueue, kSens>;
+  auto kern = flat_ssa_kernel<kQueue, kSens, kTail>;
   const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -629,7 +664,7 @@ int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps
 // with one block each instead of doubling up 19 SMs with 192-thread blocks.
 template <bool kQueue, bool kSens>
 static int auto_threads_t(const FlatParams& prm) {
-  auto kern = flat_ssa_kernel<kQueue, kSens>;
+  auto kern = flat_ssa_kernel<kQueue, kSens, false>;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       sms < 1)
@@ -670,6 +705,7 @@ int flat_auto_threads(const FlatParams& prm, bool queue, bool sens) {
 cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queue, bool sens, int T,
                         int blocks_per_sm_cap, cudaStream_t stream, int* used_blocks) {
   if (queue) {
+    if (!sens && prm.handoff > 0) return launch_t<true, false, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
     return sens ? launch_t<true, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks)
                 : launch_t<true, false>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
   }
