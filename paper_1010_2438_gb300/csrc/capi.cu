@@ -214,8 +214,8 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
     off = align256(off + (size_t)a->P * a->R * m->M * sizeof(double));
   }
   if (m->flat && sens) {   // the flat replay's per-trajectory integrals, times and firing counts
-    w.sens_acc = off;      // per trajectory: M (integral, time) pairs, M firing counts padded to even
-    off = align256(off + (size_t)a->P * a->R * (2 * (size_t)m->M + (((size_t)m->M + 1) & ~(size_t)1)) * sizeof(double));
+    w.sens_acc = off;      // per trajectory: V [M], firing counts [M]
+    off = align256(off + (size_t)a->P * a->R * 2 * (size_t)m->M * sizeof(double));
     w.inv_rates = off;     // 1 / k per sweep point and rule
     off = align256(off + (size_t)a->P * m->M * sizeof(double));
   }

@@ -123,7 +123,7 @@ struct FlatParams {
   const double* means;             // [P][G][S]
   const double* grad_means;        // [P][G][S]
   double* partials;                // [Q][M]
-  double* sens_acc;                // score replay: per trajectory [M] (int_0^tl H_i dt, tl_i) pairs, then [M] firings N_i (padded to even)
+  double* sens_acc;                // score replay: per trajectory V_i [M] (see the kernel), then [M] firings N_i
   const double* inv_rates;         // score replay: [P][M] 1 / k_j
   // scheduling
   WorkspaceHeader* ws;             // queue ticket / start time (may be null in static mode)

@@ -94,8 +94,13 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   double* node = dbase + 32 * T + tid;                          // [16][T] level-1 nodes
   double* Hd = dbase + (32 + 16) * T + tid;                     // score replay only: [M][T]
   // score replay, per trajectory in global memory (set by start()):
-  double2* acc = nullptr;   // [M] (int_0^tl_i H_i dt, tl_i): one 16-byte load and store per update
-  double* Nf = nullptr;     // [M] firings (whole numbers)
+  // V_i = N_i / k_i - I_i(t_i) + H_i t_i (t_i: the last change of rule i's
+  // count or firings), so that the score at grid time t_g is S_i(g) =
+  // V_i - H_i t_g: a change of H_i from h to h' at time t adds (h' - h) t, a
+  // firing adds 1 / k_i.  (When 1 / k_i overflows, for subnormal k_i, the
+  // firings are counted in Nf instead and S_i(g) adds N_i / k_i.)
+  double* Vv = nullptr;     // [M]
+  double* Nf = nullptr;     // [M] firings of rules whose 1 / k_i overflows
   double* part = nullptr;   // [M] the trajectory's partials
   const double* ik = nullptr;   // [M] 1 / k_i of this sweep point
   int32_t* ibase = reinterpret_cast<int32_t*>(dbase + (size_t)n_dbl_rows * T);
@@ -199,25 +204,22 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       for (int o = 0; o < S; ++o)
         c = __dadd_rn(c, __dmul_rn(gm[o], __dadd_rn((double)CNT(o), -mm[o])));
       const double gt = prm.grid[g];
-      // S_i(g) = N_i / k_i - I_i(g), I_i(g) = Iac_i + H_i (t_g - tl_i); N_i / k_i
-      // as N_i * (1 / k_i) (one extra rounding; the division when 1 / k_i
-      // overflows, for subnormal k_i).  Two rules per iteration, loads first,
-      // so that their latencies overlap.
-      auto term = [&](const double2 a, double hd, double nf, double ikv, int i) -> double {
-        const double Ig = __dadd_rn(a.x, __dmul_rn(hd, __dadd_rn(gt, -a.y)));
-        const double nk = dbits(ikv) < 0x7FF0000000000000ll ? __dmul_rn(nf, ikv) : __ddiv_rn(nf, kp[i]);
-        return __dmul_rn(c, __dadd_rn(nk, -Ig));
+      // S_i(g) = V_i - H_i t_g (+ N_i / k_i when 1 / k_i overflows); two rules
+      // per iteration, loads first, so that their latencies overlap
+      auto term = [&](double v, double hd, double ikv, int i) -> double {
+        double Si = __dadd_rn(v, -__dmul_rn(hd, gt));
+        if (dbits(ikv) >= 0x7FF0000000000000ll) Si = __dadd_rn(Si, __ddiv_rn(Nf[i], kp[i]));
+        return __dmul_rn(c, Si);
       };
       int i = 0;
       for (; i + 1 < M; i += 2) {
-        const double2 a0 = acc[i], a1 = acc[i + 1];
-        const double n0 = Nf[i], n1 = Nf[i + 1], k0 = ik[i], k1 = ik[i + 1];
+        const double v0 = Vv[i], v1 = Vv[i + 1], k0 = ik[i], k1 = ik[i + 1];
         const double p0 = part[i], p1 = part[i + 1];
         const double h0 = Hd[i * T], h1 = Hd[(i + 1) * T];
-        part[i] = __dadd_rn(p0, term(a0, h0, n0, k0, i));
-        part[i + 1] = __dadd_rn(p1, term(a1, h1, n1, k1, i + 1));
+        part[i] = __dadd_rn(p0, term(v0, h0, k0, i));
+        part[i + 1] = __dadd_rn(p1, term(v1, h1, k1, i + 1));
       }
-      if (i < M) part[i] = __dadd_rn(part[i], term(acc[i], Hd[i * T], Nf[i], ik[i], i));
+      if (i < M) part[i] = __dadd_rn(part[i], term(Vv[i], Hd[i * T], ik[i], i));
     }
   };
 
@@ -315,11 +317,9 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       CNT(s) = v;
     }
     if (kSens) {
-      // per trajectory: M (integral, time) pairs, then M firing counts padded
-      // to an even number of doubles, so every pair is 16-byte aligned
-      double* sa = prm.sens_acc + (size_t)q * (2 * M + ((M + 1) & ~1));
-      acc = reinterpret_cast<double2*>(sa);
-      Nf = sa + 2 * M;
+      double* sa = prm.sens_acc + (size_t)q * 2 * M;   // per trajectory: V [M], Nf [M]
+      Vv = sa;
+      Nf = sa + M;
       part = prm.partials + (size_t)q * M;
       ik = prm.inv_rates + (size_t)p * M;
       for (int i = 0; i < M; ++i) part[i] = 0.0;
@@ -335,7 +335,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     if (kSens) {
       for (int i = 0; i < M; ++i) {
         Hd[i * T] = u63_to_double_rn(count_h(i));
-        acc[i] = make_double2(0.0, 0.0);
+        Vv[i] = 0.0;
         Nf[i] = 0.0;
       }
     }
@@ -350,8 +350,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // after it; the lazily kept integrals are first brought up to t
   auto freeze_h = [&]() {
     for (int i = 0; i < M; ++i) {
-      const double2 a = acc[i];
-      acc[i] = make_double2(__dadd_rn(a.x, __dmul_rn(Hd[i * T], __dadd_rn(t, -a.y))), t);
+      Vv[i] = __dadd_rn(Vv[i], __dmul_rn(-Hd[i * T], t));   // H_i drops to 0 at t
       Hd[i * T] = 0.0;
     }
   };
@@ -472,26 +471,17 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       CNT(v & 0xffff) += v >> 16;
     }
     if (kSens) {
-      Nf[j] = __dadd_rn(Nf[j], 1.0);
+      if (dbits(ik[j]) < 0x7FF0000000000000ll)
+        Vv[j] = __dadd_rn(Vv[j], ik[j]);
+      else
+        Nf[j] = __dadd_rn(Nf[j], 1.0);
       const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
-      // two dependents per iteration, loads first, so that their latencies overlap
-      int e = 0;
-      for (; e + 1 < dcnt; e += 2) {
-        const int i0 = g_deps[doff + e], i1 = g_deps[doff + e + 1];
-        const double2 a0 = acc[i0], a1 = acc[i1];
-        const double h0 = Hd[i0 * T], h1 = Hd[i1 * T];
-        const double hd0 = u63_to_double_rn(count_h(i0));
-        const double hd1 = u63_to_double_rn(count_h(i1));
-        acc[i0] = make_double2(__dadd_rn(a0.x, __dmul_rn(h0, __dadd_rn(tn, -a0.y))), tn);
-        acc[i1] = make_double2(__dadd_rn(a1.x, __dmul_rn(h1, __dadd_rn(tn, -a1.y))), tn);
-        Hd[i0 * T] = hd0;
-        Hd[i1 * T] = hd1;
-      }
-      if (e < dcnt) {
+      // V_i += (h' - h) t for the rules whose count changed (h, h' < 2^53 in
+      // practice, so h' - h is exact)
+      for (int e = 0; e < dcnt; ++e) {
         const int i = g_deps[doff + e];
         const double hd = u63_to_double_rn(count_h(i));
-        const double2 a = acc[i];
-        acc[i] = make_double2(__dadd_rn(a.x, __dmul_rn(Hd[i * T], __dadd_rn(tn, -a.y))), tn);
+        Vv[i] = __dadd_rn(Vv[i], __dmul_rn(__dadd_rn(hd, -Hd[i * T]), tn));
         Hd[i * T] = hd;
       }
     }

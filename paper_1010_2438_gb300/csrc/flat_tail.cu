@@ -70,15 +70,23 @@ __global__ void tail_rank_kernel(const __grid_constant__ FlatParams prm, const i
   }
 }
 
-// 3. a warp per handed-over trajectory, resumed from its checkpoint
-__global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ FlatParams prm,
-                                                        const __grid_constant__ LogConstants lc,
-                                                        const int32_t* __restrict__ order) {
+// 3. a group of kG lanes (8, 16 or 32) per handed-over trajectory, resumed
+// from its checkpoint.  Lane gl of the group owns the LPL = 32 / kG leaves
+// gl*LPL .. gl*LPL + LPL - 1 and the tree nodes above them inside the lane;
+// the upper log2(kG) levels are built by xor butterflies across the group.
+template <int kG>
+__global__ void __launch_bounds__(128) flat_group_kernel(const __grid_constant__ FlatParams prm,
+                                                         const __grid_constant__ LogConstants lc,
+                                                         const int32_t* __restrict__ order) {
+  constexpr int LPL = 32 / kG;                              // leaves per lane
+  constexpr int LG = LPL == 4 ? 2 : (LPL == 2 ? 1 : 0);     // tree levels inside a lane
+  constexpr int KG = 5 - LG;                                // tree levels across the group
   extern __shared__ __align__(16) unsigned char smem[];
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const int gl = lane & (kG - 1);
+  const unsigned gmask = kG == 32 ? 0xffffffffu : (((1u << kG) - 1u) << (lane & ~(kG - 1)));
   const int S = prm.S, M = prm.M, B = prm.B, G = prm.G;
-  int32_t* cnt = reinterpret_cast<int32_t*>(smem) + (size_t)(threadIdx.x >> 5) * S;   // this warp's counts
+  int32_t* cnt = reinterpret_cast<int32_t*>(smem) + (size_t)(threadIdx.x / kG) * S;   // this group's counts
   const int32_t* __restrict__ g_rules = prm.rules;
   const int32_t* __restrict__ g_deps = g_rules + M * RULE_WORDS;
   const uint32_t* __restrict__ g_desc = reinterpret_cast<const uint32_t*>(g_deps + prm.n_deps);
@@ -89,6 +97,7 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
   const bool checked = prm.checked_counts != 0;
   const long long T_bits = dbits(prm.grid[G - 1]);
   const unsigned long long K = prm.ws->tail_count;
+  auto any = [&](bool v) { return (__ballot_sync(gmask, v) & gmask) != 0u; };
 
   bool ovf = false;
   // H_i at the current counts (the thread kernel's count_h)
@@ -114,8 +123,8 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
 
   for (;;) {
     unsigned long long it = 0;
-    if (lane == 0) it = atomicAdd(&prm.ws->tail_next, 1ull);
-    it = __shfl_sync(full, it, 0);
+    if (gl == 0) it = atomicAdd(&prm.ws->tail_next, 1ull);
+    it = __shfl_sync(gmask, it, 0, kG);
     if (it >= K) break;
     const long long q = order[it];
     const int p = (int)(q / prm.R);
@@ -126,8 +135,8 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
     unsigned long long h = get_u64(ck + 2);
     unsigned n = (unsigned)ck[4];
     int gi = ck[5];
-    for (int s = lane; s < S; s += 32) cnt[s] = ck[CKPT_HEADER_WORDS + s];
-    __syncwarp();
+    for (int s = gl; s < S; s += kG) cnt[s] = ck[CKPT_HEADER_WORDS + s];
+    __syncwarp(gmask);
     ovf = false;
     auto prop_of = [&](int i) -> double { return __dmul_rn(kp[i], u63_to_double_rn(count_h(i))); };
     auto leaf_sum = [&](int l) -> double {
@@ -136,51 +145,67 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
       for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, prop_of(jj));
       return s;
     };
-    // lv0 = this lane's leaf; lvk = its level-k ancestor (lv5 = a0 on every lane)
-    double lv0 = leaf_sum(lane), lv1, lv2, lv3, lv4, lv5;
+    // lf: this lane's leaves; a1 / a2: its level-1 / level-2 nodes (LPL = 4, 2);
+    // up[k]: its ancestor at level LG + 1 + k (up[KG - 1] = a0 on every lane)
+    double lf[LPL], a1[2], a2 = 0.0, up[KG];
+#pragma unroll
+    for (int k = 0; k < LPL; ++k) lf[k] = leaf_sum(gl * LPL + k);
+    a1[0] = a1[1] = 0.0;
+    auto local_top = [&]() -> double { return LPL == 4 ? a2 : (LPL == 2 ? a1[0] : lf[0]); };
     auto rebuild = [&]() {
-      lv1 = __dadd_rn(lv0, __shfl_xor_sync(full, lv0, 1));
-      lv2 = __dadd_rn(lv1, __shfl_xor_sync(full, lv1, 2));
-      lv3 = __dadd_rn(lv2, __shfl_xor_sync(full, lv2, 4));
-      lv4 = __dadd_rn(lv3, __shfl_xor_sync(full, lv3, 8));
-      lv5 = __dadd_rn(lv4, __shfl_xor_sync(full, lv4, 16));
+      if (LPL == 4) {
+        a1[0] = __dadd_rn(lf[0], lf[1]);
+        a1[1] = __dadd_rn(lf[2 % LPL], lf[3 % LPL]);
+        a2 = __dadd_rn(a1[0], a1[1]);
+      } else if (LPL == 2) {
+        a1[0] = __dadd_rn(lf[0], lf[1 % LPL]);
+      }
+      double v = local_top();
+#pragma unroll
+      for (int k = 0; k < KG; ++k) {
+        v = __dadd_rn(v, __shfl_xor_sync(gmask, v, 1 << k, kG));
+        up[k] = v;
+      }
     };
     rebuild();
-    ovf = __any_sync(full, ovf);
+    ovf = any(ovf);
     long long gbits = gi < G ? dbits(prm.grid[gi]) : 0;
     int status = TS_OK;
 
-    // observables of grid point g, lane by lane
+    // observables of grid point g, spread over the group's lanes
     auto record = [&](int g) {
       if (prm.states != nullptr) {
         int32_t* dst = prm.states + ((size_t)q * G + g) * S;
-        for (int s = lane; s < S; s += 32) dst[s] = cnt[s];
+        for (int s = gl; s < S; s += kG) dst[s] = cnt[s];
       }
       if (prm.sums != nullptr) {
         unsigned long long* dst = prm.sums + ((size_t)p * G + g) * S;
-        for (int s = lane; s < S; s += 32) atomicAdd(dst + s, (unsigned long long)(long long)cnt[s]);
+        for (int s = gl; s < S; s += kG) atomicAdd(dst + s, (unsigned long long)(long long)cnt[s]);
       }
       if (prm.sumsq != nullptr) {
         unsigned long long* dst = prm.sumsq + ((size_t)p * G + g) * S * 2;
-        for (int s = lane; s < S; s += 32) add_square_u128(dst + 2 * s, cnt[s]);
+        for (int s = gl; s < S; s += kG) add_square_u128(dst + 2 * s, cnt[s]);
       }
     };
 
-    // the next 32 events' random numbers: lane k holds event n0 + k's
+    // the next 32 events' random numbers: lane gl holds events n0 + gl + kG*s
     unsigned n0 = n;
-    double myL = 0.0, myU = 0.0;
+    double myL[LPL], myU[LPL];
     auto draw = [&]() {
       n0 = n;
-      const uint4 w = philox4x32_10(make_uint4(n0 + (unsigned)lane, 0u, (uint32_t)r + prm.r_offset, (uint32_t)p),
-                                    prm.key0, prm.key1);
-      myU = uniform52(w.z, w.w);
-      myL = -log_spec_q(uniform52(w.x, w.y), lc, g_rj, g_tj);
+#pragma unroll
+      for (int s2 = 0; s2 < LPL; ++s2) {
+        const uint4 w = philox4x32_10(make_uint4(n0 + (unsigned)(gl + kG * s2), 0u, (uint32_t)r + prm.r_offset,
+                                                 (uint32_t)p), prm.key0, prm.key1);
+        myU[s2] = uniform52(w.z, w.w);
+        myL[s2] = -log_spec_q(uniform52(w.x, w.y), lc, g_rj, g_tj);
+      }
     };
     draw();
 
     bool fill_rest = true;
     for (;;) {
-      const double a0 = lv5;
+      const double a0 = up[KG - 1];
       const long long a0b = dbits(a0);
       if (ovf || a0b >= 0x7FF0000000000000ll) {
         status = TS_PROP_OVERFLOW;
@@ -195,9 +220,17 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
         break;
       }
       if (n - n0 >= 32u) draw();
-      const int k = (int)(n - n0);
-      const double Lk = __shfl_sync(full, myL, k);
-      const double u_sel = __shfl_sync(full, myU, k);
+      const int ev = (int)(n - n0);
+      const int slot = ev / kG;
+      double Lsel = myL[0], Usel = myU[0];
+#pragma unroll
+      for (int s2 = 1; s2 < LPL; ++s2)
+        if (slot == s2) {
+          Lsel = myL[s2];
+          Usel = myU[s2];
+        }
+      const double Lk = __shfl_sync(gmask, Lsel, ev & (kG - 1), kG);
+      const double u_sel = __shfl_sync(gmask, Usel, ev & (kG - 1), kG);
       const double tau = __ddiv_rn(Lk, a0);
       const double tn = __dadd_rn(t, tau);
       const long long tnb = dbits(tn);
@@ -211,8 +244,7 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
         fill_rest = false;
         break;
       }
-      // guarded descent of x = u_sel * a0; the children of node i at level
-      // lvl sit on lanes (2i) << (lvl - 1) and (2i + 1) << (lvl - 1)
+      // guarded descent of x = u_sel * a0 (the same on every lane of the group)
       double x = __dmul_rn(u_sel, a0);
       int i = 0;
       auto descend = [&](double Lv, double Rv) {
@@ -221,11 +253,25 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
         x = left ? x : xr;
         i = 2 * i + (left ? 0 : 1);
       };
-      descend(__shfl_sync(full, lv4, 0), __shfl_sync(full, lv4, 16));
-      descend(__shfl_sync(full, lv3, (2 * i) << 3), __shfl_sync(full, lv3, (2 * i + 1) << 3));
-      descend(__shfl_sync(full, lv2, (2 * i) << 2), __shfl_sync(full, lv2, (2 * i + 1) << 2));
-      descend(__shfl_sync(full, lv1, (2 * i) << 1), __shfl_sync(full, lv1, (2 * i + 1) << 1));
-      descend(__shfl_sync(full, lv0, 2 * i), __shfl_sync(full, lv0, 2 * i + 1));
+      // across lanes: node i at level L has its children at level L-1 on lanes
+      // (2i) << (L-1-LG) and (2i+1) << (L-1-LG)
+#pragma unroll
+      for (int L = 5; L > LG; --L) {
+        const int sh = L - 1 - LG;
+        const double reg = (L - 1 == LG) ? local_top() : up[(L - 2 - LG) < 0 ? 0 : (L - 2 - LG)];
+        descend(__shfl_sync(gmask, reg, (2 * i) << sh, kG), __shfl_sync(gmask, reg, (2 * i + 1) << sh, kG));
+      }
+      // inside the owning lane
+      if (LPL == 4) {
+        const int owner = i;
+        descend(__shfl_sync(gmask, a1[0], owner, kG), __shfl_sync(gmask, a1[1], owner, kG));
+        const bool hi = (i & 1) != 0;
+        descend(__shfl_sync(gmask, hi ? lf[2 % LPL] : lf[0], owner, kG),
+                __shfl_sync(gmask, hi ? lf[3 % LPL] : lf[1 % LPL], owner, kG));
+      } else if (LPL == 2) {
+        const int owner = i;
+        descend(__shfl_sync(gmask, lf[0], owner, kG), __shfl_sync(gmask, lf[1 % LPL], owner, kG));
+      }
       const int l = i;
       int j;
       if (B == 1) {
@@ -251,27 +297,29 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
       }
       j = min(max(j, 0), M - 1);
       // the stoichiometry change, checked first (nothing changes on overflow);
-      // lane d handles change d (distinct species)
+      // lane d handles change d (distinct species, at most 8 <= kG)
       const int32_t* rec = g_rules + j * RULE_WORDS;
       const int nd_ = rec[R_NDELTA];
       int sp = 0, dv = 0;
-      if (lane < nd_) {
-        const int v = rec[R_DELTA + lane];
+      if (gl < nd_) {
+        const int v = rec[R_DELTA + gl];
         sp = v & 0xffff;
         dv = v >> 16;
       }
-      const bool bad = lane < nd_ && dv > 0 && cnt[sp] > 0x7FFFFFFF - dv;
-      if (__any_sync(full, bad)) {
+      if (any(gl < nd_ && dv > 0 && cnt[sp] > 0x7FFFFFFF - dv)) {
         status = TS_INT_OVERFLOW;
         break;
       }
-      if (lane < nd_) cnt[sp] += dv;
-      __syncwarp();
+      if (gl < nd_) cnt[sp] += dv;
+      __syncwarp(gmask);
       // dirty leaves (the leaves of the fired rule's dependents), then the tree
-      if (((unsigned)rec[R_LEAFMASK] >> lane) & 1u) lv0 = leaf_sum(lane);
-      ovf = __any_sync(full, ovf);
+      const unsigned lm = (unsigned)rec[R_LEAFMASK] >> (gl * LPL);
+#pragma unroll
+      for (int k = 0; k < LPL; ++k)
+        if ((lm >> k) & 1u) lf[k] = leaf_sum(gl * LPL + k);
+      ovf = any(ovf);
       rebuild();
-      if (lane == 0 && prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
+      if (gl == 0 && prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
         const size_t at = (size_t)q * prm.log_cap + n;
         prm.log_rule[at] = j;
         if (prm.log_slot) prm.log_slot[at] = 0;
@@ -283,7 +331,7 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
     }
     if (fill_rest)
       for (; gi < G; ++gi) record(gi);
-    if (lane == 0) {
+    if (gl == 0) {
       put_f64(ck, t);
       put_u64(ck + 2, h);
       ck[4] = (int32_t)n;
@@ -294,10 +342,13 @@ __global__ void __launch_bounds__(128) flat_warp_kernel(const __grid_constant__ 
       if (prm.traj_hash) prm.traj_hash[q] = h;
       if (prm.traj_final_t) prm.traj_final_t[q] = t;
     }
-    for (int s = lane; s < S; s += 32) ck[CKPT_HEADER_WORDS + s] = cnt[s];
-    __syncwarp();   // the counts are reused by this warp's next trajectory
+    for (int s = gl; s < S; s += kG) ck[CKPT_HEADER_WORDS + s] = cnt[s];
+    __syncwarp(gmask);   // the counts are reused by this group's next trajectory
   }
 }
+
+// lanes per handed-over trajectory
+constexpr int kTailLanes = 16;
 
 // Steps 1-3 on `stream` after the thread kernel's launch: list, est and order
 // hold Q entries each (workspace).
@@ -314,13 +365,18 @@ cudaError_t launch_flat_tail(const FlatParams& prm, const LogConstants& lc, int3
   tail_rank_kernel<<<(unsigned)sms, 256, 0, stream>>>(prm, list, est, order);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)4 * prm.S * sizeof(int32_t);
+  auto kern = flat_group_kernel<kTailLanes>;
+  const size_t smem = (size_t)(128 / kTailLanes) * prm.S * sizeof(int32_t);
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(flat_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  // up to 8 warps per SM; warps without a trajectory return at once
-  flat_warp_kernel<<<(unsigned)(2 * sms), 128, smem, stream>>>(prm, lc, order);
+  // a resident grid; groups without a trajectory return at once
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  kern<<<(unsigned)(per_sm * sms), 128, smem, stream>>>(prm, lc, order);
   return cudaGetLastError();
 }
 
