@@ -157,11 +157,12 @@ enum {
                                  then, once the queue is empty and at most
                                  tail_threshold trajectories still run, those
                                  stop at their next 1024-event boundary and are
-                                 finished by one warp each, longest predicted
-                                 remaining work first (prediction: events so far
-                                 x (T - t) / t).  Cuts the makespan of batches of
-                                 uneven trajectory length (parameter sweeps);
-                                 results are identical to the other layouts   */
+                                 finished by a group of 16 lanes each, longest
+                                 predicted remaining work first (prediction: events
+                                 so far x (T - t) / t).  Shortens the makespan of
+                                 batches of uneven trajectory length (parameter
+                                 sweeps); results are identical to the other
+                                 layouts                                        */
 };
 
 /*
@@ -279,7 +280,7 @@ typedef struct {
   void* workspace;
   size_t workspace_bytes;
   int32_t tail_threshold;    /* CWC_LAYOUT_TAIL: hand over when at most this many
-                                trajectories run (0 = 27 per SM) */
+                                trajectories run (0 = 108 per SM) */
 } cwc_sim_args;
 
 /*

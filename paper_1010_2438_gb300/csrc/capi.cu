@@ -779,9 +779,10 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // default measured on the 256 x 256 uneven sweep (2048 / 4096 / 8192 / 16384
-    // trajectories: 6.57 / 6.16 / 6.48 / 9.35 s): 27 per SM
-    prm.handoff = a->tail_threshold > 0 ? a->tail_threshold : 27LL * sms;
+    // default measured on the 256 x 256 uneven sweep with 16 lanes per handed-
+    // over trajectory (4104 / 8192 / 16384 trajectories: 6.71 / 6.40 / 6.09 s;
+    // the queue layout 7.91 s): 108 per SM
+    prm.handoff = a->tail_threshold > 0 ? a->tail_threshold : 108LL * sms;
   }
   if (w.need_order) {
     double* est = reinterpret_cast<double*>(ws + w.order);

@@ -1,5 +1,5 @@
 // The tail of a batch of flat-network trajectories of uneven length (the
-// uneven parameter sweeps of Sec. 5.2): a warp per trajectory.
+// uneven parameter sweeps of Sec. 5.2): a group of lanes per trajectory.
 //
 // One thread per trajectory is the efficient layout while tens of thousands
 // of trajectories share the GPU, but once the work queue is empty the makespan
@@ -14,18 +14,20 @@
 //      simulated time observed in the first part of the run, times the time
 //      left to the horizon T),
 //   2. order them longest-predicted-first, and
-//   3. finish them with one warp each, which cuts the per-event latency:
-//        - lane k draws Philox(n0 + k) and computes its uniform and logarithm
-//          for the warp's next 32 events at once, so the integer work that
-//          dominates one lane's event is spread over the warp;
-//        - lane l owns leaf l of the 32-lane blocked tree and recomputes it
-//          when the fired rule dirtied it, all lanes at once;
-//        - the five tree levels are rebuilt with xor butterflies (every lane
-//          of a pair adds the same two values; IEEE addition is commutative,
-//          so each node equals the written tree's left + right);
+//   3. finish them with a group of kG lanes each, which cuts the per-event
+//      latency:
+//        - the group's lanes draw the Philox words and compute the uniforms
+//          and logarithms of its next 32 events at once (32 / kG each), so
+//          the integer work that dominates one lane's event is spread out;
+//        - each lane owns 32 / kG leaves of the 32-lane blocked tree and the
+//          nodes above them inside the lane, and recomputes the leaves the
+//          fired rule dirtied;
+//        - the levels above are rebuilt with xor butterflies across the group
+//          (every lane of a pair adds the same two values; IEEE addition is
+//          commutative, so each node equals the written tree's left + right);
 //        - the guarded descent reads a node's children from the lanes that
 //          hold them (shuffles); every lane walks it identically;
-//        - grid records write the counts lane by lane (coalesced rows).
+//        - grid records write the counts lane by lane.
 // Every arithmetic step is the thread kernel's, in the same order, so the
 // results are identical bit for bit whichever kernel finishes a trajectory.
 #include <cuda_runtime.h>
