@@ -258,7 +258,7 @@ def measure_extras(dev):
     evp = out["events"].double().mean(dim=1)
     ev = int(out["events"].sum().item())
     extras["sweep256x256"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec,
-                              "layout": "tail (queue, then the last trajectories on a warp each)", "graph": True,
+                              "layout": "tail (queue, then the last trajectories on a lane group each)", "graph": True,
                               "queue_layout": {"events_per_s": ev / sec_q, "seconds": sec_q, "layout": lay,
                                                "block_threads": thr},
                               "identical_to_queue_layout": same,
