@@ -34,6 +34,7 @@ class _Model(ctypes.Structure):
         ("S", ctypes.c_int32), ("L", ctypes.c_int32), ("C", ctypes.c_int32), ("M", ctypes.c_int32),
         ("kind", ctypes.c_void_p), ("ctx_label", ctypes.c_void_p), ("child_label", ctypes.c_void_p),
         ("grand_label", ctypes.c_void_p), ("lhs", ctypes.c_void_p), ("rhs", ctypes.c_void_p),
+        ("rate_law", ctypes.c_void_p), ("rate_par", ctypes.c_void_p),
     ]
 
 
@@ -63,6 +64,8 @@ def _load():
     L.oracle_num_observables.restype = i32
     L.oracle_rule_totals.argtypes = [vp, vp, vp]
     L.oracle_rule_totals.restype = ctypes.c_int
+    L.oracle_rule_h.argtypes = [vp, vp, vp]
+    L.oracle_rule_h.restype = ctypes.c_int
     L.oracle_simulate.argtypes = [
         vp, vp, i32, i32, vp, i32, vp, i32, u64, i64, i64, i64,
         vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
@@ -81,10 +84,12 @@ class _ModelHandle:
     def __init__(self, model):
         m = model.contiguous()
         lhs5, rhs5, grand = m.rows5()        # pattern rows 0-4 (rows 3-4 zero for the 3-row kinds)
-        self.arrays = (m.kind, m.ctx_label, m.child_label, grand, lhs5, rhs5)
+        law = None if m.rate_law is None else np.ascontiguousarray(m.rate_law, np.int32)
+        par = None if m.rate_par is None else np.ascontiguousarray(m.rate_par, np.float64)
+        self.arrays = (m.kind, m.ctx_label, m.child_label, grand, lhs5, rhs5, law, par)
         self.struct = _Model(m.n_species, m.n_labels, m.max_compartments, m.n_rules,
                              _ptr(m.kind), _ptr(m.ctx_label), _ptr(m.child_label), _ptr(grand),
-                             _ptr(lhs5), _ptr(rhs5))
+                             _ptr(lhs5), _ptr(rhs5), _ptr(law), _ptr(par))
 
     @property
     def ref(self):
@@ -138,6 +143,17 @@ def rule_totals(model, term) -> np.ndarray:
     rc = lib().oracle_rule_totals(h.ref, _ptr(t), _ptr(out))
     if rc != 0:
         raise ValueError("invalid term or int64 overflow")
+    return out
+
+
+def rule_h(model, counts) -> np.ndarray:
+    """h_j of every rule of a flat model at ``counts`` [S], as doubles: the
+    number of reactant combinations, or the Michaelis-Menten value."""
+    h = _ModelHandle(model)
+    x = np.ascontiguousarray(np.asarray(counts, dtype=np.int32))
+    out = np.zeros(model.n_rules, np.float64)
+    if lib().oracle_rule_h(h.ref, _ptr(x), _ptr(out)) != 0:
+        raise ValueError("int64 overflow")
     return out
 
 

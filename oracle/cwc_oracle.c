@@ -79,12 +79,33 @@ enum { K_LOCAL = 0, K_PARENT_CHILD = 1, K_CREATE = 2, K_DISSOLVE = 3, K_FUSION =
  * rhs rows 1, 2 are added to the merged wrap and content. */
 #define ROWS 5
 
+/* Rate laws (Sec. 2.2: mass action, "but more flexible approaches are also
+ * considered"): rate_law[j] = 0 for mass action, where h_j is the number of
+ * reactant combinations; rate_law[j] = 1 + s for Michaelis-Menten kinetics
+ * of substrate s with constant K_j = rate_par[j] > 0 (flat models, LOCAL
+ * rules with one or two reactant species of multiplicity 1, the other one
+ * the enzyme E):  h_j = RN(RN(n_E * n_s) / RN(K_j + n_s)), or
+ * RN(n_s / RN(K_j + n_s)) without an enzyme, each an IEEE double operation
+ * in this order.  Both arrays may be NULL (all mass action). */
 typedef struct {
   int32_t S, L, C, M;
   const int32_t *kind, *ctx_label, *child_label, *grand_label;
   const int32_t *lhs; /* [M][ROWS][S] */
   const int32_t *rhs; /* [M][ROWS][S] */
+  const int32_t *rate_law; /* [M] or NULL */
+  const double *rate_par;  /* [M] or NULL */
 } oracle_model;
+
+/* Michaelis-Menten value of rule j at a flat term's counts x (see above). */
+static double mm_value(const oracle_model* m, int j, const int32_t* x) {
+  const int32_t* lhs = m->lhs + (size_t)j * ROWS * m->S;
+  const int sub = m->rate_law[j] - 1;
+  double num = (double)x[sub];
+  for (int s = 0; s < m->S; s++)
+    if (lhs[s] != 0 && s != sub) num = num * (double)x[s];   /* the enzyme, if any */
+  const double den = m->rate_par[j] + (double)x[sub];
+  return num / den;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
@@ -660,7 +681,8 @@ typedef struct {
   double* partial;        /* [M] or NULL */
   int64_t* N;             /* [M] */
   double* I;              /* [M] */
-  int64_t* H;             /* [M] */
+  int64_t* H;             /* [M] combinatorial counts (mass action) */
+  double* Hs;             /* [M] h_j as a double: (double)H_j, or the rate-law value */
   int32_t* obs;           /* [O] */
 } traj_ctx;
 
@@ -673,7 +695,7 @@ static void record(traj_ctx* x, const term_t* t, int g, double now) {
       cg = cg + x->gmeans[(size_t)g * x->O + o] * ((double)x->obs[o] - x->means[(size_t)g * x->O + o]);
     double dt = x->grid[g] - now;
     for (int j = 0; j < x->M; j++) {
-      double Ig = x->I[j] + (double)x->H[j] * dt;
+      double Ig = x->I[j] + x->Hs[j] * dt;
       double Sj = (double)x->N[j] / x->k[j] - Ig;
       x->partial[j] = x->partial[j] + cg * Sj;
     }
@@ -710,6 +732,22 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
   if (S < 1 || C < 1 || M < 1 || m->L < 1) return -1;
   for (int j = 0; j < M; j++) {
     if (m->kind[j] < 0 || m->kind[j] > 5) return -1;
+    if (m->rate_law != NULL && m->rate_law[j] != 0) {
+      /* Michaelis-Menten: flat models, LOCAL, one or two reactant species of
+         multiplicity 1 among which the substrate, K > 0 finite */
+      const int sub = m->rate_law[j] - 1;
+      const int32_t* lhs = m->lhs + (size_t)j * ROWS * m->S;
+      int nreac = 0, bad = 0;
+      for (int r = 0; r < ROWS; r++)
+        for (int x = 0; x < m->S; x++)
+          if (lhs[r * m->S + x] != 0) {
+            nreac++;
+            if (r != 0 || lhs[x] != 1) bad = 1;
+          }
+      if (m->L != 1 || m->C != 1 || m->kind[j] != K_LOCAL || sub < 0 || sub >= m->S || lhs[sub] != 1 ||
+          nreac < 1 || nreac > 2 || bad || m->rate_par == NULL || !(m->rate_par[j] > 0.0) || !isfinite(m->rate_par[j]))
+        return -1;
+    }
     if (m->ctx_label[j] < 0 || m->ctx_label[j] >= m->L) return -1;
     if (m->kind[j] != K_LOCAL && (m->child_label[j] < 1 || m->child_label[j] >= m->L)) return -1;
     if (m->kind[j] == K_NESTED && (m->grand_label == NULL || m->grand_label[j] < 1 || m->grand_label[j] >= m->L))
@@ -733,6 +771,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
   x.N = malloc(sizeof(int64_t) * M);
   x.I = malloc(sizeof(double) * M);
   x.H = malloc(sizeof(int64_t) * M);
+  x.Hs = malloc(sizeof(double) * M);
   x.obs = malloc(sizeof(int32_t) * O);
   const double T = grid[G - 1];
   const int grid_ok = valid_grid(grid, G);
@@ -749,6 +788,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
       x.N[j] = 0;
       x.I[j] = 0.0;
       x.H[j] = 0;
+      x.Hs[j] = 0.0;
       if (x.partial) x.partial[j] = 0.0;
     }
     double tnow = 0.0;
@@ -768,8 +808,14 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
       /* 1. Match: every rule at every compartment. */
       int overflow = 0;
       for (int j = 0; j < M; j++) {
-        if (rule_total(m, &t, j, &x.H[j])) { overflow = 1; break; }
-        a[j] = x.k[j] * (double)x.H[j];
+        if (m->rate_law != NULL && m->rate_law[j] > 0) {
+          x.H[j] = 0;
+          x.Hs[j] = mm_value(m, j, t.content);
+        } else {
+          if (rule_total(m, &t, j, &x.H[j])) { overflow = 1; break; }
+          x.Hs[j] = (double)x.H[j];
+        }
+        a[j] = x.k[j] * x.Hs[j];
       }
       double a0 = 0.0;
       if (!overflow) {
@@ -779,7 +825,10 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
       if (overflow) {
         /* H of the current term is unusable: record states, keep the score unchanged */
         st = ST_PROP_OVERFLOW;
-        for (int j = 0; j < M; j++) x.H[j] = 0;
+        for (int j = 0; j < M; j++) {
+          x.H[j] = 0;
+          x.Hs[j] = 0.0;
+        }
         for (; gi < G; gi++) record(&x, &t, gi, tnow);
         break;
       }
@@ -811,6 +860,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
       draw(seed, (uint32_t)n, 1, (uint32_t)r, (uint32_t)p, wc);
       uint64_t W = (uint64_t)wc[0] | ((uint64_t)wc[1] << 32);
       uint64_t xc = (uint64_t)(((unsigned __int128)W * (unsigned __int128)(uint64_t)x.H[j]) >> 64);
+      if (m->rate_law != NULL && m->rate_law[j] > 0) xc = 0; /* flat: the root is the only context */
       int ctx = -1;
       uint64_t cum = 0;
       if (m->kind[j] == K_FUSION) {
@@ -839,7 +889,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
         break;
       }
       if (x.partial) {
-        for (int i = 0; i < M; i++) x.I[i] = x.I[i] + (double)x.H[i] * (tnext - tnow);
+        for (int i = 0; i < M; i++) x.I[i] = x.I[i] + x.Hs[i] * (tnext - tnow);
         x.N[j] += 1;
       }
       if (log_cap > 0 && n < log_cap) {
@@ -866,6 +916,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
   free(x.N);
   free(x.I);
   free(x.H);
+  free(x.Hs);
   free(x.obs);
   return 0;
 }
@@ -891,6 +942,35 @@ int oracle_rule_totals(const oracle_model* m, const int32_t* init, int64_t* H_ou
   free(t.parent);
   free(t.wrap);
   free(t.content);
+  return rc;
+}
+
+/* h_j as a double of every rule at a flat term's counts [S]: the number of
+ * reactant combinations, or the Michaelis-Menten value (for the pins).
+ * Returns -1 on an int64 overflow. */
+int oracle_rule_h(const oracle_model* m, const int32_t* counts, double* h_out) {
+  term_t t;
+  int32_t alive = 1, label = 0, parent = -1, wrap0 = 0;
+  int32_t* wrap = calloc((size_t)m->S, sizeof(int32_t));
+  t.S = m->S;
+  t.C = 1;
+  t.alive = &alive;
+  t.label = &label;
+  t.parent = &parent;
+  t.wrap = wrap;
+  t.content = (int32_t*)counts;
+  (void)wrap0;
+  int rc = 0;
+  for (int j = 0; j < m->M && rc == 0; j++) {
+    if (m->rate_law != NULL && m->rate_law[j] > 0) {
+      h_out[j] = mm_value(m, j, counts);
+    } else {
+      int64_t H;
+      if (rule_total(m, &t, j, &H)) rc = -1;
+      else h_out[j] = (double)H;
+    }
+  }
+  free(wrap);
   return rc;
 }
 

@@ -115,6 +115,8 @@ class Model:
     grand_label: Optional[np.ndarray] = None   # int32 [M] (-1 unless NESTED), or None
     lhs_ext: Optional[np.ndarray] = None       # int32 [M, 2, S] rows 3 and 4, or None
     rhs_ext: Optional[np.ndarray] = None       # int32 [M, 2, S]
+    rate_law: Optional[np.ndarray] = None      # int32 [M]: 0 mass action, 1 + s Michaelis-Menten of substrate s
+    rate_par: Optional[np.ndarray] = None      # float64 [M]: the Michaelis constant K (molecules)
 
     @property
     def has_ext(self) -> bool:
@@ -154,15 +156,20 @@ class Model:
             self,
             kind=c(self.kind), ctx_label=c(self.ctx_label), child_label=c(self.child_label),
             lhs=c(self.lhs), rhs=c(self.rhs), grand_label=c(self.grand_label),
-            lhs_ext=c(self.lhs_ext), rhs_ext=c(self.rhs_ext),
+            lhs_ext=c(self.lhs_ext), rhs_ext=c(self.rhs_ext), rate_law=c(self.rate_law),
+            rate_par=None if self.rate_par is None else np.ascontiguousarray(self.rate_par, dtype=np.float64),
         )
 
 
 Reaction = Tuple[Dict[int, int], Dict[int, int]]
 
 
-def flat_model(n_species: int, reactions: Sequence[Reaction], name: str = "") -> Model:
-    """Flat mass-action network: every reaction is a LOCAL rule of the root."""
+def flat_model(n_species: int, reactions: Sequence[Reaction], name: str = "",
+               michaelis_menten: Optional[Dict[int, Tuple[int, float]]] = None) -> Model:
+    """Flat network: every reaction is a LOCAL rule of the root, with mass-
+    action kinetics unless ``michaelis_menten[j] = (substrate, K)`` makes
+    reaction j's rate k_j n_E n_S / (K + n_S) (the enzyme E the other
+    reactant, if any; both reactants of multiplicity 1)."""
     M = len(reactions)
     lhs = np.zeros((M, 3, n_species), np.int32)
     rhs = np.zeros((M, 3, n_species), np.int32)
@@ -171,8 +178,15 @@ def flat_model(n_species: int, reactions: Sequence[Reaction], name: str = "") ->
             lhs[j, 0, s] += c
         for s, c in prod.items():
             rhs[j, 0, s] += c
+    law = par = None
+    if michaelis_menten:
+        law = np.zeros(M, np.int32)
+        par = np.zeros(M, np.float64)
+        for j, (sub, K) in michaelis_menten.items():
+            law[j] = 1 + sub
+            par[j] = K
     return Model(n_species, 1, 1, np.zeros(M, np.int32), np.zeros(M, np.int32),
-                 np.full(M, -1, np.int32), lhs, rhs, name)
+                 np.full(M, -1, np.int32), lhs, rhs, name, rate_law=law, rate_par=par)
 
 
 @dataclasses.dataclass
