@@ -18,6 +18,7 @@ cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -283,6 +284,31 @@ def measure_extras(dev):
         del keep, out
     extras["lotka_volterra"] = {"by_species": lv, "workload": "n-species Lotka-Volterra chain, 32768 replicas, "
                                                             "horizon 1, 100-point grid (Gillespie 1977 constants)"}
+    # Michaelis-Menten kinetics (the flat kernel's rate-law variant): a 20-stage
+    # kinase cascade, 41 species, 40 reactions, beside the same network with
+    # mass-action rates (another process, for the cost of the law's division)
+    mm = {}
+    for law in ("michaelis_menten", "mass_action"):
+        b = W.mm_cascade(stages=20, R=65536, G=100, T=20.0)
+        model = b.model if law == "michaelis_menten" else dataclasses.replace(b.model, rate_law=None, rate_par=None)
+        rates_np = b.rates if law == "michaelis_menten" else b.rates * 0.01
+        b = W.Batch(model, rates_np, b.init, b.grid, b.R, b.seed, name=b.name)
+        cm = api.CompiledModel(b.model)
+        rates, init, grid = api.device_inputs(b, dev)
+        keep = {}
+
+        def run_mm():
+            keep["o"] = api.simulate(cm, rates, init, grid, b.R, b.seed, states=True, out=keep.get("o"))
+            return keep["o"]
+
+        out, sec = _timed(run_mm, "mm_cascade20_" + law)
+        ev = int(out["events"].sum().item())
+        mm[law] = {"events_per_s": ev / sec, "events": ev, "seconds": sec}
+        del keep, out
+    extras["mm_cascade20"] = dict(mm["michaelis_menten"], mass_action_same_network=mm["mass_action"],
+                                  workload="20-stage kinase cascade with Michaelis-Menten rates (41 species, 40 "
+                                           "reactions), 65536 replicas, horizon 20, 100-point grid; the mass-action "
+                                           "line runs the same reactions with k / 100")
     # likelihood-ratio sensitivities: 16 species x 24 reactions, 131,072 replicas, 100-point grid
     b = W.flat16x24()
     cm = api.CompiledModel(b.model)
@@ -454,24 +480,32 @@ def main():
         init_h = torch.from_numpy(np.ascontiguousarray(batch.init)).pin_memory()
         grid_h = torch.from_numpy(np.ascontiguousarray(batch.grid)).pin_memory()
         host_out = torch.empty(tuple(out["states"].shape), dtype=torch.int32, pin_memory=True)
-        bufs = {"out": out}
         e2e_steps = min(args.steps, 3)
-        api.simulate_host(cm, rates_h, init_h, grid_h, R, batch.seed, batch.max_events, dev_bufs=bufs,
-                          host_out=host_out, replica_offset=r_off)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e2e_steps):
+
+        def time_host(direct):
+            bufs = {"out": out}
             api.simulate_host(cm, rates_h, init_h, grid_h, R, batch.seed, batch.max_events, dev_bufs=bufs,
-                              host_out=host_out, replica_offset=r_off)
-        e1.record(stream)
-        barrier()
-        te = e0.elapsed_time(e1) / 1e3
-        ev_e, te = shard.combine(float(events * e2e_steps), te, device=dev)
+                              host_out=host_out, replica_offset=r_off, direct=direct)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(e2e_steps):
+                api.simulate_host(cm, rates_h, init_h, grid_h, R, batch.seed, batch.max_events, dev_bufs=bufs,
+                                  host_out=host_out, replica_offset=r_off, direct=direct)
+            e1.record(stream)
+            barrier()
+            return shard.combine(float(events * e2e_steps), e0.elapsed_time(e1) / 1e3, device=dev)
+
+        ev_c, te_c = time_host(False)
+        ev_e, te = time_host(True)
         h2d = rates_h.numel() * 8 + init_h.numel() * 4 + grid_h.numel() * 8
         e2e = {"value": ev_e / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": host_out.numel() * 4, "steps": e2e_steps}
+               "d2h_bytes_per_step": host_out.numel() * 4, "steps": e2e_steps,
+               "d2h": "the kernel stores the grid states into page-locked host memory while it runs (NVLink-C2C); "
+                      "inputs copied host to device each step",
+               "copy_after": {"value": ev_c / te_c, "unit": UNIT,
+                              "d2h": "states to device memory, then one copy to page-locked host memory"}}
 
     extras = None
     if world == 1 and not args.no_extras:

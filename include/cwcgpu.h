@@ -105,6 +105,18 @@ enum {
  *   must be 0; its rhs rows 1, 2 are added to the merged wrap and content)
  *   or the grandchild's wrap and content (NESTED).
  * Flat mass-action networks are L = 1, C = 1, all rules LOCAL on label 0.
+ *   Rate laws (Sec. 2.2 takes mass action as the usual rate and allows other
+ *   kinetics; both pointers may be NULL, meaning mass action throughout):
+ *   rate_law[M]: 0 = mass action, h_j = the number of reactant
+ *   combinations; 1 + s = Michaelis-Menten kinetics of substrate species s,
+ *   rate_par[M] = the Michaelis constant K_j (in molecules, > 0, finite;
+ *   read only for those rules).  A Michaelis-Menten rule belongs to a flat
+ *   model, is LOCAL and has one or two reactant species, each of
+ *   multiplicity 1, among them s; the other one, if any, is the enzyme E:
+ *       h_j = RN(RN(n_E * n_s) / RN(K_j + n_s))   or   RN(n_s / RN(K_j + n_s)),
+ *   each step one IEEE double operation, a_j = RN(k_j * h_j).  Anything else
+ *   is CWC_ERR_INVALID_ARG.  Such models run the flat kernel's
+ *   Michaelis-Menten variant and not CWC_LAYOUT_TAIL.
  */
 typedef struct {
   int32_t n_species;
@@ -119,6 +131,8 @@ typedef struct {
   const int32_t* grand_label;   /* [M] or NULL */
   const int32_t* lhs_ext;       /* [M][2][S] or NULL */
   const int32_t* rhs_ext;       /* [M][2][S] or NULL */
+  const int32_t* rate_law;      /* [M] or NULL (all mass action) */
+  const double* rate_par;       /* [M] or NULL */
 } cwc_model_desc;
 
 typedef struct cwc_model cwc_model;
@@ -152,8 +166,9 @@ enum {
                                  takes trajectory q + (threads in the grid)     */
   CWC_LAYOUT_QUEUE = 2,       /* persistent grid; a lane that finishes takes the
                                  next trajectory from a device work queue       */
-  CWC_LAYOUT_TAIL = 3         /* flat models, forward only (no deadline, no
-                                 checkpoint, no sensitivities): the queue layout,
+  CWC_LAYOUT_TAIL = 3         /* flat mass-action models, forward only (no
+                                 deadline, no checkpoint, no sensitivities): the
+                                 queue layout,
                                  then, once the queue is empty and at most
                                  tail_threshold trajectories still run, those
                                  stop at their next 1024-event boundary and are
@@ -180,7 +195,13 @@ enum {
  *   max_events  per trajectory, 0 .. 2^32-1
  *
  * Outputs (device, each may be NULL):
- *   states        int32 [P][R][G][O]   observables at each grid point
+ *   states        int32 [P][R][G][O]   observables at each grid point; device
+ *                                      memory or page-locked host memory
+ *                                      (cudaHostAlloc / cudaHostRegister),
+ *                                      which the kernel writes directly over
+ *                                      the host link while it runs (no copy
+ *                                      afterwards); pageable host memory is
+ *                                      CWC_ERR_INVALID_ARG
  *   sums          int64 [P][G][O]      exact sums over replicas (zeroed by
  *                                      the call before accumulation)
  *   means         double [P][G][O]     sums / R (one IEEE division)

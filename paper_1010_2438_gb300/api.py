@@ -22,7 +22,8 @@ class CompiledModel:
     def __init__(self, model: Model):
         m = model.contiguous()
         self.model = m
-        self._keep = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs, m.grand_label, m.lhs_ext, m.rhs_ext)
+        self._keep = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs, m.grand_label, m.lhs_ext, m.rhs_ext,
+                      m.rate_law, m.rate_par)
 
         def ptr(a):
             return None if a is None else a.ctypes.data
@@ -30,7 +31,8 @@ class CompiledModel:
         desc = capi.cwc_model_desc(m.n_species, m.n_labels, m.n_rules, m.max_compartments,
                                    m.kind.ctypes.data, m.ctx_label.ctypes.data, m.child_label.ctypes.data,
                                    m.lhs.ctypes.data, m.rhs.ctypes.data,
-                                   ptr(m.grand_label), ptr(m.lhs_ext), ptr(m.rhs_ext))
+                                   ptr(m.grand_label), ptr(m.lhs_ext), ptr(m.rhs_ext),
+                                   ptr(m.rate_law), ptr(m.rate_par))
         self.handle = capi.cwc_model_create(desc)
         self.n_observables = capi.cwc_model_num_observables(self.handle)
         self.flat = m.n_labels == 1 and m.max_compartments == 1
@@ -251,9 +253,12 @@ def mean_observables(rates, cm, init, grid, R, seed, max_events=(1 << 32) - 1):
 def simulate_host(cm: CompiledModel, rates_h: torch.Tensor, init_h: torch.Tensor, grid_h: torch.Tensor, R: int,
                   seed: int, max_events: int = (1 << 32) - 1, *, dev_bufs: Optional[dict] = None,
                   host_out: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None,
-                  **kw) -> torch.Tensor:
+                  direct: bool = True, **kw) -> torch.Tensor:
     """End-to-end call from host (pinned) tensors: copy the inputs to the
-    device, simulate, copy the grid states back into ``host_out``."""
+    device, simulate, and return the grid states in ``host_out`` (page-locked
+    host memory).  With ``direct`` the kernel writes the states into
+    ``host_out`` itself while it runs (over NVLink-C2C on Grace systems);
+    otherwise they go to device memory and are copied back afterwards."""
     st = stream if stream is not None else torch.cuda.current_stream()
     bufs = dev_bufs if dev_bufs is not None else {}
     with torch.cuda.stream(st):
@@ -263,11 +268,18 @@ def simulate_host(cm: CompiledModel, rates_h: torch.Tensor, init_h: torch.Tensor
         d_rates.copy_(rates_h, non_blocking=True)
         d_init.copy_(init_h, non_blocking=True)
         d_grid.copy_(grid_h, non_blocking=True)
-        res = simulate(cm, d_rates, d_init, d_grid, R, seed, max_events, out=bufs.get("out"), stream=st, **kw)
-        bufs["out"] = res
+        P, G = rates_h.shape[0], grid_h.shape[0]
         if host_out is None:
-            host_out = torch.empty(res["states"].shape, dtype=torch.int32, pin_memory=True)
-        host_out.copy_(res["states"], non_blocking=True)
+            host_out = torch.empty((P, R, G, cm.n_observables), dtype=torch.int32, pin_memory=True)
+        out = dict(bufs.get("out") or {})
+        if direct:
+            out["states"] = host_out
+        elif "states" in out and out["states"].device.type != "cuda":
+            del out["states"]
+        res = simulate(cm, d_rates, d_init, d_grid, R, seed, max_events, out=out, stream=st, **kw)
+        bufs["out"] = res
+        if not direct:
+            host_out.copy_(res["states"], non_blocking=True)
     return host_out
 
 

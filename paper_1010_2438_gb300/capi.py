@@ -38,7 +38,7 @@ _u64 = ctypes.c_uint64
 class cwc_model_desc(ctypes.Structure):
     _fields_ = [("n_species", _i32), ("n_labels", _i32), ("n_rules", _i32), ("max_compartments", _i32),
                 ("kind", _vp), ("ctx_label", _vp), ("child_label", _vp), ("lhs", _vp), ("rhs", _vp),
-                ("grand_label", _vp), ("lhs_ext", _vp), ("rhs_ext", _vp)]
+                ("grand_label", _vp), ("lhs_ext", _vp), ("rhs_ext", _vp), ("rate_law", _vp), ("rate_par", _vp)]
 
 
 class cwc_sim_args(ctypes.Structure):

@@ -50,6 +50,7 @@ struct cwc_model {
   // flat compilation
   int B = 1, n_deps = 0;
   int checked_counts = 0;
+  int mm_off = -1;              // Michaelis-Menten tables' word offset in d_tables (-1: none)
   int32_t* d_tables = nullptr;  // [M][RULE_WORDS], [n_deps], [M] descriptors, log tables (cwc_internal.h)
   std::vector<int32_t> h_tables;
   // compartmentalised compilation
@@ -259,8 +260,9 @@ cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
   if (a->log_cap > 0 && a->log_rule == nullptr) return fail(CWC_ERR_INVALID_ARG, "log_cap > 0 needs log_rule");
   if (a->layout < CWC_LAYOUT_AUTO || a->layout > CWC_LAYOUT_TAIL) return fail(CWC_ERR_INVALID_ARG, "bad layout");
   if (a->layout == CWC_LAYOUT_TAIL &&
-      (!m->flat || a->deadline_ns != 0 || a->checkpoint != nullptr || a->resume != 0))
-    return fail(CWC_ERR_INVALID_ARG, "CWC_LAYOUT_TAIL is for flat models without deadline or checkpoints");
+      (!m->flat || m->mm_off >= 0 || a->deadline_ns != 0 || a->checkpoint != nullptr || a->resume != 0))
+    return fail(CWC_ERR_INVALID_ARG,
+                "CWC_LAYOUT_TAIL is for flat mass-action models without deadline or checkpoints");
   if (a->tail_threshold < 0) return fail(CWC_ERR_INVALID_ARG, "tail_threshold must be >= 0");
   if (a->block_threads != 0 && (a->block_threads < 32 || a->block_threads > 256 || a->block_threads % 32 != 0))
     return fail(CWC_ERR_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 256]");
@@ -280,6 +282,35 @@ cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
   return CWC_OK;
 }
 
+// The grid states may be device memory or page-locked host memory
+// (cudaHostAlloc, cudaHostRegister): the latter through its device mapping,
+// so that the kernels store the states across the host link (NVLink-C2C on
+// Grace systems) while they run and no copy follows.  Pageable host memory
+// is refused.  While the stream is being captured into a graph the pointer
+// is taken as it is (no queries during capture; page-locked memory has the
+// same address on the device under unified addressing).
+cwc_status states_ptr(int32_t* p, cudaStream_t st, int32_t** out) {
+  *out = p;
+  if (p == nullptr) return CWC_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return CWC_OK;
+  }
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CWC_ERR_INVALID_ARG, "states: not a device or page-locked host pointer");
+  }
+  if (at.type == cudaMemoryTypeUnregistered)
+    return fail(CWC_ERR_INVALID_ARG, "states: pageable host memory (pass device or page-locked host memory)");
+  if (at.type == cudaMemoryTypeHost) {
+    if (at.devicePointer == nullptr) return fail(CWC_ERR_INVALID_ARG, "states: host memory not mapped on the device");
+    *out = static_cast<int32_t*>(at.devicePointer);
+  }
+  return CWC_OK;
+}
+
 FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
   FlatParams prm;
   std::memset(&prm, 0, sizeof(prm));
@@ -290,6 +321,10 @@ FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
   prm.checked_counts = m->checked_counts;
   prm.rules = m->d_tables;
   prm.deps = m->d_tables + (size_t)m->M * RULE_WORDS;
+  if (m->mm_off >= 0) {
+    prm.mm_K = reinterpret_cast<const double*>(m->d_tables + m->mm_off);
+    prm.mm_desc = reinterpret_cast<const uint32_t*>(m->d_tables + m->mm_off + 2 * m->M);
+  }
   prm.P = a->P;
   prm.R = a->R;
   prm.G = a->G;
@@ -394,6 +429,21 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       return fail(CWC_ERR_INVALID_ARG, rj + ": pattern rows 3-4 belong to FUSION and NESTED rules");
     if (k == CWC_RULE_FUSION && rhs_more)
       return fail(CWC_ERR_INVALID_ARG, rj + ": FUSION writes the merged wrap and content through rhs rows 1-2");
+    const int law = d->rate_law ? d->rate_law[j] : 0;
+    if (law < 0 || law > S) return fail(CWC_ERR_INVALID_ARG, rj + ": rate_law must be 0 or 1 + a species index");
+    if (law != 0) {
+      // Michaelis-Menten: flat model, LOCAL, one or two reactant species of
+      // multiplicity 1 among which the substrate, K > 0 finite
+      const int32_t* l0 = lrow(j, 0);
+      bool ok = L == 1 && C == 1 && k == CWC_RULE_LOCAL && l0[law - 1] == 1 && factors >= 1 && factors <= 2;
+      for (int x = 0; x < S; ++x) ok = ok && l0[x] <= 1;
+      if (!ok)
+        return fail(CWC_ERR_INVALID_ARG, rj + ": Michaelis-Menten rules are LOCAL rules of flat models with one or two "
+                                              "reactant species of multiplicity 1, the substrate among them");
+      const double K = d->rate_par ? d->rate_par[j] : 0.0;
+      if (!(K > 0.0) || !std::isfinite(K))
+        return fail(CWC_ERR_INVALID_ARG, rj + ": Michaelis-Menten rules need rate_par (K) > 0 and finite");
+    }
   }
   cwc_model* m = new cwc_model();
   m->S = S;
@@ -639,6 +689,31 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       tb.push_back((int32_t)(uint32_t)(lct.tj[i] >> 32));
     }
   }
+  // Michaelis-Menten tables (only when some rule has that law), after the
+  // logarithm's tables (16-byte aligned): K_j as doubles [M] (0 = mass
+  // action), then [M] int32 words substrate | (enzyme + 1) << 16 (0: none)
+  bool any_mm = false;
+  for (int j = 0; j < M; ++j) any_mm |= d->rate_law != nullptr && d->rate_law[j] != 0;
+  if (any_mm) {
+    m->mm_off = (int)tb.size();
+    for (int j = 0; j < M; ++j) {
+      const double K = d->rate_law[j] != 0 ? d->rate_par[j] : 0.0;
+      uint64_t kb;
+      std::memcpy(&kb, &K, 8);
+      tb.push_back((int32_t)(uint32_t)kb);
+      tb.push_back((int32_t)(uint32_t)(kb >> 32));
+    }
+    for (int j = 0; j < M; ++j) {
+      uint32_t w = 0;
+      if (d->rate_law[j] != 0) {
+        const int sub = d->rate_law[j] - 1;
+        w = (uint32_t)sub;
+        for (int s : reac[j])
+          if (s != sub) w |= (uint32_t)(s + 1) << 16;
+      }
+      tb.push_back((int32_t)w);
+    }
+  }
   // one trajectory's state must fit: 32 threads per block at least
   {
     FlatParams prm;
@@ -728,7 +803,8 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
   }
   if (!is_sens) {
-    prm.states = a->states;
+    const cwc_status sst = states_ptr(a->states, st, &prm.states);
+    if (sst != CWC_OK) return sst;
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(a->sums);
     if (w.need_sums) sums = reinterpret_cast<unsigned long long*>(ws + w.sums);
     prm.sums = sums;
@@ -885,7 +961,8 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_s
   prm.ckpt = is_sens ? nullptr : a->checkpoint;
   prm.resume = is_sens ? 0 : a->resume;
   if (!is_sens) {
-    prm.states = a->states;
+    const cwc_status sst = states_ptr(a->states, st, &prm.states);
+    if (sst != CWC_OK) return sst;
     prm.traj_status = a->traj_status;
     prm.traj_events = reinterpret_cast<long long*>(a->traj_events);
     prm.traj_hash = reinterpret_cast<unsigned long long*>(a->traj_hash);

@@ -98,6 +98,8 @@ struct FlatParams {
   int checked_counts;       // 1 if some rule has order >= 3 (int64 products may overflow)
   const int32_t* rules;     // [M][RULE_WORDS]
   const int32_t* deps;      // [n_deps]
+  const double* mm_K;       // Michaelis-Menten constants [M] (0: mass action), or null when every rule is mass action
+  const uint32_t* mm_desc;  // [M] substrate | (enzyme + 1) << 16 of the Michaelis-Menten rules
   // batch
   int P, R, G, Pi;
   uint32_t r_offset;        // replica index offset of the random streams

@@ -71,8 +71,10 @@ __host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
 // kTail: the tail layout's variant of the queue kernel, which counts finished
 // trajectories and hands the last ones over (a separate instantiation: the
 // bookkeeping, compiled into the plain queue kernel even behind a runtime
-// flag, measured 2.25x slower on the 32-species network)
-template <bool kQueue, bool kSens, bool kTail>
+// flag, measured 2.25x slower on the 32-species network).
+// kMM: models with Michaelis-Menten rules (a separate instantiation too, so
+// that mass-action networks run the kernel without the rate-law lookups)
+template <bool kQueue, bool kSens, bool kTail, bool kMM>
 __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatParams prm,
                                                        const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -250,10 +252,25 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     }
     return hh;
   };
-  // a_i = k_i H_i; the score replay keeps H_i as doubles in shared memory
-  // (updated for every rule whose count changes), so it reads them there
+  // h_i as a double: the count H_i, or for a Michaelis-Menten rule (kMM)
+  // RN(RN(n_E n_S) / RN(K_i + n_S)), RN(n_S / RN(K_i + n_S)) without an enzyme
+  auto h_of = [&](int i) -> double {
+    if (kMM) {
+      const double Km = prm.mm_K[i];
+      if (dbits(Km) != 0) {
+        const uint32_t md = prm.mm_desc[i];
+        const double ns = (double)CNT(md & 0xffffu);
+        const uint32_t e1 = md >> 16;
+        const double num = e1 != 0u ? __dmul_rn(ns, (double)CNT(e1 - 1u)) : ns;
+        return __ddiv_rn(num, __dadd_rn(Km, ns));
+      }
+    }
+    return u63_to_double_rn(count_h(i));
+  };
+  // a_i = k_i h_i; the score replay keeps h_i as doubles in shared memory
+  // (updated for every rule whose value changes), so it reads them there
   auto prop_of = [&](int i) -> double {
-    return __dmul_rn(kp[i], kSens ? Hd[i * T] : u63_to_double_rn(count_h(i)));
+    return __dmul_rn(kp[i], kSens ? Hd[i * T] : h_of(i));
   };
 
   // leaf l as the blocked sum of its rules (B > 1)
@@ -334,7 +351,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     }
     if (kSens) {
       for (int i = 0; i < M; ++i) {
-        Hd[i * T] = u63_to_double_rn(count_h(i));
+        Hd[i * T] = h_of(i);
         Vv[i] = 0.0;
         Nf[i] = 0.0;
       }
@@ -438,15 +455,19 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       j = -1;
       double s = 0.0;
       for (int jj = j0; jj < j1; ++jj) {
-        // (the score replay has H as a double already: nonzero exactly when H is)
-        const double hdd = kSens ? Hd[jj * T] : u63_to_double_rn(count_h(jj));
-        if (dbits(hdd) != 0) {
+        // (the score replay has h as a double already).  A count H >= 1 gives
+        // a_j >= k_j > 0; a Michaelis-Menten h < 1 can give k_j h = 0, so
+        // kMM tests a_j itself
+        const double hdd = kSens ? Hd[jj * T] : h_of(jj);
+        if (kMM || dbits(hdd) != 0) {
           const double a = __dmul_rn(kp[jj], hdd);
-          s = last < 0 ? a : __dadd_rn(s, a);
-          last = jj;
-          if (dbits(x) < dbits(s)) {
-            j = jj;
-            break;
+          if (!kMM || dbits(a) != 0) {
+            s = last < 0 ? a : __dadd_rn(s, a);
+            last = jj;
+            if (dbits(x) < dbits(s)) {
+              j = jj;
+              break;
+            }
           }
         }
       }
@@ -476,11 +497,11 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       else
         Nf[j] = __dadd_rn(Nf[j], 1.0);
       const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
-      // V_i += (h' - h) t for the rules whose count changed (h, h' < 2^53 in
-      // practice, so h' - h is exact)
+      // V_i += (h' - h) t for the rules whose value changed (for counts
+      // h, h' < 2^53 in practice, so h' - h is exact)
       for (int e = 0; e < dcnt; ++e) {
         const int i = g_deps[doff + e];
-        const double hd = u63_to_double_rn(count_h(i));
+        const double hd = h_of(i);
         Vv[i] = __dadd_rn(Vv[i], __dmul_rn(__dadd_rn(hd, -Hd[i * T]), tn));
         Hd[i * T] = hd;
       }
@@ -580,6 +601,8 @@ __global__ void flat_estimate_kernel(const __grid_constant__ FlatParams prm, dou
       const double n = (double)max(x0[v & 0xffff], 0);
       hh *= (v >> 16) == 1 ? n : 0.5 * n * (n - 1.0);
     }
+    if (prm.mm_K != nullptr && prm.mm_K[j] != 0.0)   // Michaelis-Menten: n_E n_S / (K + n_S)
+      hh /= prm.mm_K[j] + (double)max(x0[prm.mm_desc[j] & 0xffffu], 0);
     a0 += k[j] * hh;
   }
   est[p] = (a0 >= 0.0 && a0 < 1e300) ? a0 : 0.0;
@@ -610,10 +633,10 @@ cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order
 // Host launcher
 // ---------------------------------------------------------------------------
 
-template <bool kQueue, bool kSens, bool kTail = false>
+template <bool kQueue, bool kSens, bool kTail = false, bool kMM = false>
 static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
                             cudaStream_t stream, int* used_blocks) {
-  auto kern = flat_ssa_kernel<kQueue, kSens, kTail>;
+  auto kern = flat_ssa_kernel<kQueue, kSens, kTail, kMM>;
   const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -652,9 +675,9 @@ int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps
 // ceil(blocks / SMs) * T, since that SM sets the time of the launch (ties:
 // the larger block); e.g. 32,768 trajectories at 224 per block fill 147 SMs
 // with one block each instead of doubling up 19 SMs with 192-thread blocks.
-template <bool kQueue, bool kSens>
+template <bool kQueue, bool kSens, bool kMM>
 static int auto_threads_t(const FlatParams& prm) {
-  auto kern = flat_ssa_kernel<kQueue, kSens, false>;
+  auto kern = flat_ssa_kernel<kQueue, kSens, false, kMM>;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       sms < 1)
@@ -688,12 +711,24 @@ static int auto_threads_t(const FlatParams& prm) {
 }
 
 int flat_auto_threads(const FlatParams& prm, bool queue, bool sens) {
-  if (queue) return sens ? auto_threads_t<true, true>(prm) : auto_threads_t<true, false>(prm);
-  return sens ? auto_threads_t<false, true>(prm) : auto_threads_t<false, false>(prm);
+  if (prm.mm_K != nullptr) {
+    if (queue) return sens ? auto_threads_t<true, true, true>(prm) : auto_threads_t<true, false, true>(prm);
+    return sens ? auto_threads_t<false, true, true>(prm) : auto_threads_t<false, false, true>(prm);
+  }
+  if (queue) return sens ? auto_threads_t<true, true, false>(prm) : auto_threads_t<true, false, false>(prm);
+  return sens ? auto_threads_t<false, true, false>(prm) : auto_threads_t<false, false, false>(prm);
 }
 
 cudaError_t launch_flat(const FlatParams& prm, const LogConstants& lc, bool queue, bool sens, int T,
                         int blocks_per_sm_cap, cudaStream_t stream, int* used_blocks) {
+  if (prm.mm_K != nullptr) {   // Michaelis-Menten rules: no tail hand-over
+    if (prm.handoff > 0) return cudaErrorInvalidValue;
+    if (queue)
+      return sens ? launch_t<true, true, false, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks)
+                  : launch_t<true, false, false, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
+    return sens ? launch_t<false, true, false, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks)
+                : launch_t<false, false, false, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
+  }
   if (queue) {
     if (!sens && prm.handoff > 0) return launch_t<true, false, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
     return sens ? launch_t<true, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks)

@@ -693,3 +693,46 @@ def lotka_volterra(n: int, R: int = 65536, G: int = 100, T: float = 1.0, seed: i
     rates = np.array([[10.0] + [0.01] * (n - 1) + [10.0]], np.float64)
     init = np.full((1, n), 1000, np.int32)
     return Batch(model, rates, init, uniform_grid(T, G), R, seed + n, name="lotka_volterra_%d" % n)
+
+
+def mm_cascade_model(stages: int) -> Model:
+    """A kinase cascade with Michaelis-Menten kinetics throughout (the usual
+    enzyme-kinetics shape of signalling models): species 0 is the input
+    kinase E; stage i (1..stages) has an inactive form 2i-1 and an active form
+    2i.  Activation of stage i: X_i + E_i -> X_i* + E_i at k n_E n_X / (K +
+    n_X), the enzyme E_1 = E and E_i = X_{i-1}* after it; deactivation
+    X_i* -> X_i at k n_X* / (K + n_X*) (a saturating phosphatase).  Rule
+    2(i-1) activates stage i, rule 2(i-1)+1 deactivates it."""
+    reactions: List[Reaction] = []
+    mm: Dict[int, Tuple[int, float]] = {}
+    for i in range(1, stages + 1):
+        x, xa = 2 * i - 1, 2 * i
+        enz = 0 if i == 1 else 2 * (i - 1)
+        mm[len(reactions)] = (x, 50.0)
+        reactions.append(({x: 1, enz: 1}, {xa: 1, enz: 1}))
+        mm[len(reactions)] = (xa, 50.0)
+        reactions.append(({xa: 1}, {x: 1}))
+    return flat_model(2 * stages + 1, reactions, "mm_cascade_%d" % stages, michaelis_menten=mm)
+
+
+def mm_cascade(stages: int = 20, R: int = 16384, G: int = 100, T: float = 20.0, P: int = 1,
+               seed: int = 400) -> Batch:
+    """Seeded batch of the cascade: 10 input kinases, 100 molecules of each
+    stage's inactive form; activation k = 1 and deactivation k = 20 (per
+    unit time, the maximal rates of one enzyme and of the phosphatase), K = 50
+    molecules.  P > 1 sweep points scale the activation constants by factors
+    drawn log-uniformly from [0.5, 2] (SplitMix64 from the seed)."""
+    model = mm_cascade_model(stages)
+    M = model.n_rules
+    base = np.tile(np.array([1.0, 20.0]), stages)
+    rates = np.tile(base, (P, 1))
+    if P > 1:
+        rng = SplitMix64(seed)
+        for p in range(P):
+            f = 2.0 ** (2.0 * rng.uniform() - 1.0)
+            rates[p, 0::2] *= f
+    init = np.zeros((1, 2 * stages + 1), np.int32)
+    init[0, 0] = 10
+    init[0, 1::2] = 100
+    assert rates.shape == (P, M)
+    return Batch(model, rates, init, uniform_grid(T, G), R, seed + stages, name="mm_cascade_%d" % stages)

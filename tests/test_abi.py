@@ -1,6 +1,7 @@
 """The C ABI: the library builds for sm_103a, loads, exports every symbol the
 headers declare, and rejects bad arguments on the host (no GPU needed)."""
 import ctypes
+import dataclasses
 import glob
 import os
 import re
@@ -53,9 +54,11 @@ def test_version(lib):
 
 def _desc(model):
     m = model.contiguous()
-    keep = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs)
+    keep = (m.kind, m.ctx_label, m.child_label, m.lhs, m.rhs, m.rate_law, m.rate_par)
     d = capi.cwc_model_desc(m.n_species, m.n_labels, m.n_rules, m.max_compartments,
-                            *(a.ctypes.data for a in keep))
+                            *(a.ctypes.data for a in keep[:5]))
+    d.rate_law = None if m.rate_law is None else m.rate_law.ctypes.data
+    d.rate_par = None if m.rate_par is None else m.rate_par.ctypes.data
     return d, keep
 
 
@@ -133,3 +136,30 @@ def test_ctypes_structs_follow_the_header(name):
     for (nm, is_ptr, typ), (_, ctype) in zip(hdr, py):
         want = 8 if is_ptr else sizes[typ]
         assert ctypes.sizeof(ctype) == want, nm
+
+
+def test_michaelis_menten_validation_on_host(lib):
+    """Michaelis-Menten rules are LOCAL rules of flat models with one or two
+    reactant species of multiplicity 1, the substrate among them, and a
+    finite K > 0; anything else is refused before any device work."""
+    out = ctypes.c_void_p()
+    conv = ({0: 1, 2: 1}, {1: 1, 2: 1})
+    ok = W.flat_model(3, [conv], michaelis_menten={0: (0, 10.0)})
+    cases = [
+        (W.flat_model(3, [conv], michaelis_menten={0: (0, 0.0)}), "K"),
+        (W.flat_model(3, [conv], michaelis_menten={0: (0, float("inf"))}), "K"),
+        (W.flat_model(3, [conv], michaelis_menten={0: (1, 10.0)}), "substrate"),       # product, not a reactant
+        (W.flat_model(3, [({0: 2}, {1: 1})], michaelis_menten={0: (0, 10.0)}), "multiplicity"),
+        (W.flat_model(3, [({}, {1: 1})], michaelis_menten={0: (0, 10.0)}), "substrate"),
+    ]
+    bad = dataclasses.replace(ok.contiguous(), rate_law=np.array([4], np.int32))
+    cases.append((bad, "rate_law"))
+    # a compartment model (two labels) may not use the law
+    comp = dataclasses.replace(ok.contiguous(), n_labels=2, max_compartments=4)
+    cases.append((comp, "flat"))
+    for model, text in cases:
+        d, keep = _desc(model)
+        rc = lib.cwc_model_create(ctypes.byref(d), ctypes.byref(out))
+        assert rc == capi.CWC_ERR_INVALID_ARG, (text, rc, capi.cwc_last_error())
+        assert "Michaelis-Menten" in capi.cwc_last_error() or "rate_law" in capi.cwc_last_error(), text
+        assert out.value is None

@@ -204,3 +204,32 @@ def test_general_pattern_workload_recipe():
     tokens_V = img[:, 3 + W.GEN_V].sum() + img[:, 3 + S + W.GEN_V].sum()
     assert (tokens_M, tokens_V) == (10, 8)
     assert 1 + tokens_M + tokens_V <= m.max_compartments - 5
+
+
+def test_michaelis_menten_cascade_recipe():
+    """20 stages: species 0 the input kinase, stage i's inactive / active forms
+    2i-1 / 2i; rule 2(i-1) activates stage i with enzyme 0 (i = 1) or the
+    previous stage's active form, rule 2(i-1)+1 deactivates it without an
+    enzyme; every rule Michaelis-Menten with K = 50 on its substrate;
+    activation k = 1, deactivation k = 20; each stage conserves its 100
+    molecules; P > 1 scales the activation constants by factors in [0.5, 2]."""
+    b = W.mm_cascade(stages=20, R=8, P=5)
+    m = b.model
+    assert (m.n_species, m.n_rules) == (41, 40)
+    lhs, rhs = m.lhs[:, 0, :], m.rhs[:, 0, :]
+    for i in range(1, 21):
+        x, xa, enz = 2 * i - 1, 2 * i, 0 if i == 1 else 2 * (i - 1)
+        ja, jd = 2 * (i - 1), 2 * (i - 1) + 1
+        assert set(np.nonzero(lhs[ja])[0]) == {x, enz} and m.rate_law[ja] == 1 + x
+        assert rhs[ja, xa] == 1 and rhs[ja, enz] == 1 and rhs[ja, x] == 0
+        assert set(np.nonzero(lhs[jd])[0]) == {xa} and m.rate_law[jd] == 1 + xa and rhs[jd, x] == 1
+        assert (rhs[ja] - lhs[ja]).sum() == 0 and (rhs[jd] - lhs[jd]).sum() == 0
+    assert np.all(m.rate_par == 50.0) and np.all((m.lhs[:, 0, :] <= 1))
+    assert np.all(b.rates[:, 1::2] == 20.0)
+    f = b.rates[:, 0::2]
+    assert np.all(f == f[:, :1]) and np.all((f >= 0.5) & (f <= 2.0)) and len(set(f[:, 0])) == 5
+    assert b.init[0, 0] == 10 and np.all(b.init[0, 1::2] == 100) and np.all(b.init[0, 2::2] == 0)
+    b1 = W.mm_cascade(stages=20, R=8, P=1)
+    assert np.all(b1.rates[0, 0::2] == 1.0)
+    b2 = W.mm_cascade(stages=20, R=8, P=5)
+    assert np.array_equal(b.rates, b2.rates)
