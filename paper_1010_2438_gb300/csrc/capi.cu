@@ -51,6 +51,7 @@ struct cwc_model {
   int B = 1, n_deps = 0;
   int checked_counts = 0;
   int mm_off = -1;              // Michaelis-Menten tables' word offset in d_tables (-1: none)
+  int pool = 0;                 // flat kernel: leaves rebuilt by the warp together
   int32_t* d_tables = nullptr;  // [M][RULE_WORDS], [n_deps], [M] descriptors, log tables (cwc_internal.h)
   std::vector<int32_t> h_tables;
   // compartmentalised compilation
@@ -321,6 +322,7 @@ FlatParams make_flat_params(const cwc_model* m, const cwc_sim_args* a) {
   prm.checked_counts = m->checked_counts;
   prm.rules = m->d_tables;
   prm.deps = m->d_tables + (size_t)m->M * RULE_WORDS;
+  prm.pool = m->pool;
   if (m->mm_off >= 0) {
     prm.mm_K = reinterpret_cast<const double*>(m->d_tables + m->mm_off);
     prm.mm_desc = reinterpret_cast<const uint32_t*>(m->d_tables + m->mm_off + 2 * m->M);
@@ -688,6 +690,17 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       tb.push_back((int32_t)(uint32_t)lct.tj[i]);
       tb.push_back((int32_t)(uint32_t)(lct.tj[i] >> 32));
     }
+  }
+  // The warp rebuilds its lanes' dirty leaves together when a leaf holds more
+  // than one rule and an event dirties three leaves or more on average over
+  // the rules (or the leaves hold Michaelis-Menten divisions); measured +9 %
+  // at 4.5 leaves (64 rules), -11 % at 2 (33 rules).
+  {
+    long long dirty = 0;
+    for (int j = 0; j < M; ++j) dirty += __builtin_popcount((unsigned)tb[(size_t)j * RULE_WORDS + R_LEAFMASK]);
+    bool law = false;
+    for (int j = 0; j < M; ++j) law |= d->rate_law != nullptr && d->rate_law[j] != 0;
+    m->pool = m->B > 1 && (law || dirty >= 3LL * M) ? 1 : 0;
   }
   // Michaelis-Menten tables (only when some rule has that law), after the
   // logarithm's tables (16-byte aligned): K_j as doubles [M] (0 = mass

@@ -100,6 +100,7 @@ struct FlatParams {
   const int32_t* deps;      // [n_deps]
   const double* mm_K;       // Michaelis-Menten constants [M] (0: mass action), or null when every rule is mass action
   const uint32_t* mm_desc;  // [M] substrate | (enzyme + 1) << 16 of the Michaelis-Menten rules
+  int pool;                 // 1: the warp rebuilds its lanes' dirty leaves together (B > 1, see the kernel)
   // batch
   int P, R, G, Pi;
   uint32_t r_offset;        // replica index offset of the random streams

@@ -1274,36 +1274,46 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   };
 
   bool need_new = true;
+  bool done = false;   // no trajectories left for this group (it stays in the loop with its warp)
   for (;;) {
-    if (need_new) {
-      if (kQueue) {
-        if (kL == 1) {
-          q = cwc_grab_next(prm.ws);
+    // every lane group of the warp starts its step together, so that the
+    // groups' common instructions (draw, logarithm, descent) issue once for
+    // the warp (+2 % events/s on 16,384 terms of 48 rules)
+    __syncwarp();
+    if (!done) {
+      if (need_new) {
+        if (kQueue) {
+          if (kL == 1) {
+            q = cwc_grab_next(prm.ws);
+          } else {
+            long long v = 0;
+            if (gl == 0) v = (long long)atomicAdd(&prm.ws->queue_next, 1ull);
+            q = grp.bcast(v, 0);
+          }
         } else {
-          long long v = 0;
-          if (gl == 0) v = (long long)atomicAdd(&prm.ws->queue_next, 1ull);
-          q = grp.bcast(v, 0);
+          q = first ? gslot : q + (long long)gridDim.x * NT;
+          first = false;
+        }
+        if (q >= Q) {
+          done = true;
+        } else {
+          const int st0 = start();
+          if (st0 == 1) finalize();
+          if (st0 == 0) {
+            n_launch = n;
+            need_new = false;
+          }
         }
       } else {
-        q = first ? gslot : q + (long long)gridDim.x * NT;
-        first = false;
+        const int ended = step();
+        if (ended != 0) {
+          if (ended == 1) fill();
+          finalize();
+          need_new = true;
+        }
       }
-      if (q >= Q) break;
-      const int st0 = start();
-      if (st0 == 2) continue;
-      if (st0 == 1) {
-        finalize();
-        continue;
-      }
-      n_launch = n;
-      need_new = false;
     }
-    const int ended = step();
-    if (ended != 0) {
-      if (ended == 1) fill();
-      finalize();
-      need_new = true;
-    }
+    if (__all_sync(0xffffffffu, done)) break;
   }
 #undef LEAF
 #undef NODE

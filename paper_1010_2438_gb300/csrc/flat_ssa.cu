@@ -27,12 +27,14 @@
 // Per event the thread: draws Philox(n, 0, r, p); computes tau with the
 // fixed integer logarithm and one IEEE division; records grid points passed;
 // descends the tree (integer compares of non-negative doubles, one FP64
-// subtraction per level); applies the stoichiometry change; rebuilds only the
+// subtraction per level); applies the stoichiometry change.  Then only the
 // leaves holding a rule whose propensity reads a changed species (Gibson-
-// Bruck dependency graph) and the level-1 nodes above them, then the 15
-// register nodes (a warp's lanes fire different rules, so between them they
-// dirty nearly every upper node anyway).  a0 is always the tree root, never
-// a running sum, so values equal a full rebuild bit for bit.
+// Bruck dependency graph) are rebuilt — with B > 1 by the whole warp at once,
+// every lane's dirty leaves dealt out over the lanes — and the level-1 nodes
+// above them, then the 15 register nodes (a warp's lanes fire different
+// rules, so between them they dirty every upper node anyway: all 15 in every
+// warp-step of the 64-rule network's event logs).  a0 is always the tree
+// root, never a running sum, so values equal a full rebuild bit for bit.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -73,8 +75,11 @@ __host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
 // bookkeeping, compiled into the plain queue kernel even behind a runtime
 // flag, measured 2.25x slower on the 32-species network).
 // kMM: models with Michaelis-Menten rules (a separate instantiation too, so
-// that mass-action networks run the kernel without the rate-law lookups)
-template <bool kQueue, bool kSens, bool kTail, bool kMM>
+// that mass-action networks run the kernel without the rate-law lookups).
+// kPool: B > 1 and events that dirty several leaves (chosen by the host from
+// the model, prm.pool): the warp rebuilds its lanes' dirty leaves together
+// (pooled_leaves); otherwise every lane rebuilds its own.
+template <bool kQueue, bool kSens, bool kTail, bool kMM, bool kPool>
 __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatParams prm,
                                                        const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -232,13 +237,14 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // H_i of rule i at the current counts (Match_Populations: product of
   // binomials).  Models whose rules all have order <= 2 cannot overflow
   // (n*m < 2^62 for counts < 2^31) and take 32x32->64-bit products only.
-  auto count_h = [&](int i) -> unsigned long long {
+  // (of trajectory column cc: the counts of block thread c are ibase + c)
+  auto count_h_at = [&](int i, const int32_t* cc, bool* of) -> unsigned long long {
     if (!checked) {
       // one descriptor load, both count loads in flight together, no branches
       const uint32_t d = g_desc[i];
       const uint32_t kind = d & 3u;
-      const unsigned n0 = (unsigned)CNT((d >> 2) & 0x3fffu);
-      const unsigned n1 = (unsigned)CNT((d >> 16) & 0x3fffu);
+      const unsigned n0 = (unsigned)cc[((d >> 2) & 0x3fffu) * T];
+      const unsigned n1 = (unsigned)cc[((d >> 16) & 0x3fffu) * T];
       const unsigned m = kind == 3u ? n1 : (kind == 2u ? n0 - 1u : 1u);
       const unsigned long long prod = (unsigned long long)(kind == 0u ? 1u : n0) * m;
       return kind == 2u ? prod >> 1 : prod;
@@ -248,25 +254,27 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     unsigned long long hh = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[R_REAC + a];
-      hh = mul_checked(hh, binom12(CNT(v & 0xffff), v >> 16), &ovf);
+      hh = mul_checked(hh, binom12(cc[(v & 0xffff) * T], v >> 16), of);
     }
     return hh;
   };
+  auto count_h = [&](int i) -> unsigned long long { return count_h_at(i, cnt, &ovf); };
   // h_i as a double: the count H_i, or for a Michaelis-Menten rule (kMM)
   // RN(RN(n_E n_S) / RN(K_i + n_S)), RN(n_S / RN(K_i + n_S)) without an enzyme
-  auto h_of = [&](int i) -> double {
+  auto h_of_at = [&](int i, const int32_t* cc, bool* of) -> double {
     if (kMM) {
       const double Km = prm.mm_K[i];
       if (dbits(Km) != 0) {
         const uint32_t md = prm.mm_desc[i];
-        const double ns = (double)CNT(md & 0xffffu);
+        const double ns = (double)cc[(md & 0xffffu) * T];
         const uint32_t e1 = md >> 16;
-        const double num = e1 != 0u ? __dmul_rn(ns, (double)CNT(e1 - 1u)) : ns;
+        const double num = e1 != 0u ? __dmul_rn(ns, (double)cc[(e1 - 1u) * T]) : ns;
         return __ddiv_rn(num, __dadd_rn(Km, ns));
       }
     }
-    return u63_to_double_rn(count_h(i));
+    return u63_to_double_rn(count_h_at(i, cc, of));
   };
+  auto h_of = [&](int i) -> double { return h_of_at(i, cnt, &ovf); };
   // a_i = k_i h_i; the score replay keeps h_i as doubles in shared memory
   // (updated for every rule whose value changes), so it reads them there
   auto prop_of = [&](int i) -> double {
@@ -279,6 +287,19 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     double s = j0 < M ? prop_of(j0) : 0.0;
     for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, prop_of(jj));
     return s;
+  };
+  // the same for the trajectory of block thread c (rates kc, counts ibase + c;
+  // the score replay's h in column c of Hd); +inf when a count product
+  // overflows, which makes that trajectory's a0 infinite, so that its next
+  // step ends it with PROP_OVERFLOW as the overflow flag would
+  auto leaf_sum_at = [&](int l, int c, const double* kc) -> double {
+    const int32_t* cc = ibase + c;
+    const double* hc = dbase + (32 + 16) * T + c;
+    bool of = false;
+    const int j0 = l * B, j1 = min(j0 + B, M);
+    double s = j0 < M ? __dmul_rn(kc[j0], kSens ? hc[j0 * T] : h_of_at(j0, cc, &of)) : 0.0;
+    for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, __dmul_rn(kc[jj], kSens ? hc[jj * T] : h_of_at(jj, cc, &of)));
+    return of ? __longlong_as_double(0x7FF0000000000000ll) : s;
   };
 
   auto finalize = [&]() {
@@ -372,6 +393,9 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     }
   };
 
+  int pend_j = 0;
+  double pend_t = 0.0;
+  unsigned pend_lm = 0u;
   // one event or the end of the trajectory: 0 = running, 1 = ended with grid
   // points left to fill, 2 = ended with the grid complete (or left to a resume)
   auto step = [&]() -> int {
@@ -506,22 +530,36 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
         Hd[i * T] = hd;
       }
     }
-    if (B == 1) {
-      // the leaves are the propensities: recompute the dependents
-      const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
-      for (int e = 0; e < dcnt; ++e) {
-        const int i = g_deps[doff + e];
-        LEAF(i) = prop_of(i);
-      }
-    } else {
-      unsigned lm = (unsigned)rec[R_LEAFMASK];
-      while (lm) {
-        const int ll = __ffs(lm) - 1;
-        lm &= lm - 1u;
-        LEAF(ll) = leaf_sum(ll);
+    // the leaves, nodes and the rest of the event follow in finish_event(),
+    // after the warp has rebuilt every lane's dirty leaves together
+    pend_j = j;
+    pend_t = tn;
+    pend_lm = (unsigned)rec[R_LEAFMASK];
+    return 0;
+  };
+
+  // the rest of an applied event: the lane rebuilds its dirty leaves (with
+  // B = 1 they are the dependents' propensities), unless the warp has
+  // already rebuilt them together (kPool)
+  auto finish_event = [&]() {
+    const int32_t* rec = g_rules + pend_j * RULE_WORDS;
+    if (!kPool) {
+      if (B == 1) {
+        const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
+        for (int e = 0; e < dcnt; ++e) {
+          const int i = g_deps[doff + e];
+          LEAF(i) = prop_of(i);
+        }
+      } else {
+        unsigned lm = (unsigned)rec[R_LEAFMASK];
+        while (lm) {
+          const int ll = __ffs(lm) - 1;
+          lm &= lm - 1u;
+          LEAF(ll) = leaf_sum(ll);
+        }
       }
     }
-    unsigned nm = (unsigned)rec[R_NODEMASK] & 0xFFFFu;    // level-1 nodes above the dirty leaves
+    unsigned nm = (unsigned)rec[R_NODEMASK] & 0xFFFFu;   // level-1 nodes above the dirty leaves
     while (nm) {
       const int kk = __ffs(nm) - 1;
       nm &= nm - 1u;
@@ -530,48 +568,145 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     rebuild_upper();
     if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
       const size_t at = (size_t)q * prm.log_cap + n;
-      prm.log_rule[at] = j;
+      prm.log_rule[at] = pend_j;
       if (prm.log_slot) prm.log_slot[at] = 0;
-      if (prm.log_t) prm.log_t[at] = tn;
+      if (prm.log_t) prm.log_t[at] = pend_t;
     }
-    t = tn;
+    t = pend_t;
     ++n;
-    h = fnv1a_event(h, (uint32_t)j, 0u);
-    return 0;
+    h = fnv1a_event(h, (uint32_t)pend_j, 0u);
+  };
+
+  // Every lane's dirty leaves (kPool), rebuilt by the whole warp: the
+  // (lane, leaf) pairs are numbered lane by lane (a prefix sum of the leaf
+  // counts) and dealt out 32 at a time, so that a warp spends ceil(sum / 32)
+  // rounds instead of max-over-lanes iterations of a per-lane leaf loop.
+  // Each round holds the leaf's B products and B - 1 sums, and an FP64 warp
+  // instruction occupies GB300's FP64 pipe for the same 16 SM cycles however
+  // few lanes execute it; on the 64-rule network (4.5 dirty leaves per event)
+  // a warp-step needs 4.8 rounds against 8.9 iterations of the per-lane loop
+  // (+9 % events/s).  Where an event dirties at most two leaves, or a leaf is
+  // one product (B = 1), the dealing costs more than it saves (-11 % on the
+  // 32-species Lotka-Volterra chain, -5 % on a 24-rule network), unless the
+  // leaves hold Michaelis-Menten divisions (+12 % on the 40-rule cascade).
+  // All 32 lanes of the warp take part.
+  auto pooled_leaves = [&](unsigned lm) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = tid & 31;
+    const int cnt_l = __popc(lm);
+    int incl = cnt_l;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - cnt_l;
+    for (int base = 0; base < total; base += 32) {
+      const int idx = base + lane;
+      // owner: the number of lanes whose inclusive prefix is <= idx
+      int o = 0;
+#pragma unroll
+      for (int s = 16; s >= 1; s >>= 1) {
+        const int v = __shfl_sync(FULL, incl, o + s - 1);
+        if (v <= idx) o += s;
+      }
+      o &= 31;
+      const unsigned lm_o = __shfl_sync(FULL, lm, o);
+      const int ex_o = __shfl_sync(FULL, excl, o);
+      const int p_o = __shfl_sync(FULL, p, o);
+      if (idx < total) {
+        // the (idx - ex_o)-th set bit of the owner's mask
+        unsigned m = lm_o;
+        int k = idx - ex_o, pos = 0, c;
+        c = __popc(m & 0xFFFFu); if (k >= c) { k -= c; m >>= 16; pos += 16; }
+        c = __popc(m & 0xFFu);   if (k >= c) { k -= c; m >>= 8;  pos += 8; }
+        c = __popc(m & 0xFu);    if (k >= c) { k -= c; m >>= 4;  pos += 4; }
+        c = __popc(m & 0x3u);    if (k >= c) { k -= c; m >>= 2;  pos += 2; }
+        if (k >= (int)(m & 1u)) pos += 1;
+        const int col = tid - lane + o;
+        dbase[pos * T + col] = leaf_sum_at(pos, col, prm.rates + (size_t)p_o * M);
+      }
+    }
+    __syncwarp();
   };
 
   bool need_new = true;
   bool had_one = false;   // kTail: this lane has finished a trajectory before taking the next
-  for (;;) {
-    if (need_new) {
-      if (kTail && had_one) {
-        // warp-aggregated count of finished trajectories (ran, or bad input)
-        const unsigned mask = __activemask();
-        if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&prm.ws->finished, (unsigned long long)__popc(mask));
-      }
-      had_one = true;
-      if (kQueue) {
-        q = grab_next(prm.ws);
-        if (prm.order != nullptr && q < Q) {
-          const long long pp = prm.order[q / prm.R];
-          q = pp * prm.R + (q - (q / prm.R) * prm.R);
-        }
-      } else {
-        q = first ? (long long)blockIdx.x * T + tid : q + qstride;
-        first = false;
-      }
-      if (q >= Q) break;
-      const int st0 = start();
-      if (st0 == 1) finalize();
-      if (st0 != 0) continue;
-      n_launch = n;
-      need_new = false;
+  // a lane that finishes a trajectory takes the next one
+  auto next_trajectory = [&]() -> bool {
+    if (kTail && had_one) {
+      // warp-aggregated count of finished trajectories (ran, or bad input)
+      const unsigned mask = __activemask();
+      if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&prm.ws->finished, (unsigned long long)__popc(mask));
     }
-    const int ended = step();
-    if (ended != 0) {
-      if (ended == 1) fill();
-      finalize();
-      need_new = true;
+    had_one = true;
+    if (kQueue) {
+      q = grab_next(prm.ws);
+      if (prm.order != nullptr && q < Q) {
+        const long long pp = prm.order[q / prm.R];
+        q = pp * prm.R + (q - (q / prm.R) * prm.R);
+      }
+    } else {
+      q = first ? (long long)blockIdx.x * T + tid : q + qstride;
+      first = false;
+    }
+    return q < Q;
+  };
+  if (!kPool) {
+    // every lane runs its own trajectories through
+    for (;;) {
+      if (need_new) {
+        if (!next_trajectory()) break;
+        const int st0 = start();
+        if (st0 == 1) finalize();
+        if (st0 != 0) continue;
+        n_launch = n;
+        need_new = false;
+      }
+      const int ended = step();
+      if (ended == 0) {
+        finish_event();
+      } else {
+        if (ended == 1) fill();
+        finalize();
+        need_new = true;
+      }
+    }
+  } else {
+    // the warp rebuilds its lanes' leaves together, so every lane stays in
+    // the loop until all of them are out of trajectories
+    bool done = false;
+    for (;;) {
+      unsigned lm = 0u;     // leaves of this lane's applied event, if any
+      bool applied = false;
+      if (!done) {
+        if (need_new) {
+          if (!next_trajectory()) {
+            done = true;
+          } else {
+            const int st0 = start();
+            if (st0 == 1) finalize();
+            if (st0 == 0) {
+              n_launch = n;
+              need_new = false;
+            }
+          }
+        } else {
+          const int ended = step();
+          if (ended != 0) {
+            if (ended == 1) fill();
+            finalize();
+            need_new = true;
+          } else {
+            lm = pend_lm;
+            applied = true;
+          }
+        }
+      }
+      pooled_leaves(lm);   // ends with __syncwarp(): the warp is reconverged for the rest of the event
+      if (applied) finish_event();
+      if (__all_sync(0xffffffffu, done)) break;
     }
   }
 #undef LEAF
@@ -633,10 +768,10 @@ cudaError_t launch_flat_order(const FlatParams& prm, double* est, int32_t* order
 // Host launcher
 // ---------------------------------------------------------------------------
 
-template <bool kQueue, bool kSens, bool kTail = false, bool kMM = false>
-static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
+template <bool kQueue, bool kSens, bool kTail, bool kMM, bool kPool>
+static cudaError_t launch_k(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
                             cudaStream_t stream, int* used_blocks) {
-  auto kern = flat_ssa_kernel<kQueue, kSens, kTail, kMM>;
+  auto kern = flat_ssa_kernel<kQueue, kSens, kTail, kMM, kPool>;
   const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -662,6 +797,13 @@ static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T
   return cudaGetLastError();
 }
 
+template <bool kQueue, bool kSens, bool kTail = false, bool kMM = false>
+static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
+                            cudaStream_t stream, int* used_blocks) {
+  return prm.pool ? launch_k<kQueue, kSens, kTail, kMM, true>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks)
+                  : launch_k<kQueue, kSens, kTail, kMM, false>(prm, lc, T, blocks_per_sm_cap, stream, used_blocks);
+}
+
 size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens) {
   return (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, sens);
 }
@@ -677,7 +819,7 @@ int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps
 // with one block each instead of doubling up 19 SMs with 192-thread blocks.
 template <bool kQueue, bool kSens, bool kMM>
 static int auto_threads_t(const FlatParams& prm) {
-  auto kern = flat_ssa_kernel<kQueue, kSens, false, kMM>;
+  auto kern = prm.pool ? flat_ssa_kernel<kQueue, kSens, false, kMM, true> : flat_ssa_kernel<kQueue, kSens, false, kMM, false>;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       sms < 1)
