@@ -28,12 +28,13 @@
  *   select_rule     never picks a zero entry; frequencies vs a_j / a0.
  *   propensities    Sec. 2.2 worked example (rate 4k); brute-force counting
  *                   of distinct reactant tuples on small terms, and of
- *                   distinct occurrences of FUSION / NESTED left-hand sides
- *                   (identified atoms and compartments) on random terms.
+ *                   distinct occurrences of FUSION / PAIR / NESTED left-hand
+ *                   sides (identified atoms and compartments) on random terms.
  *   context choice  chi-square laws where the chosen compartment changes the
  *                   outcome; exact recomputation of the integer draw.
  *   simulate        closed-form laws (birth-death Poisson / binomial mixture,
- *                   isomerisation binomial, depth-two transport binomial),
+ *                   isomerisation binomial, depth-two transport binomial,
+ *                   sibling transport as the Ehrenfest model),
  *                   chemical master equation via matrix exponential (incl.
  *                   fusion of empty compartments), conservation invariants.
  *   sensitivities   analytic birth-death gradient; central finite
@@ -67,14 +68,17 @@ enum {
  *   FUSION        l: p X (w1 x1 | q1 Y1)^l' (w2 x2 | q2 Y2)^l'
  *                      -> p' X (w' x1 x2 | q' Y1 Y2)^l'      (two compartments)
  *   NESTED        l: p X (w x | q Y (v z | u Z)^l'')^l'
- *                      -> p' X (w' x | q' Y (v' z | u' Z)^l'')^l'   (depth two) */
-enum { K_LOCAL = 0, K_PARENT_CHILD = 1, K_CREATE = 2, K_DISSOLVE = 3, K_FUSION = 4, K_NESTED = 5 };
+ *                      -> p' X (w' x | q' Y (v' z | u' Z)^l'')^l'   (depth two)
+ *   PAIR          l: p X (w1 x1 | q1 Y1)^l' (w2 x2 | q2 Y2)^l'
+ *                      -> p' X (w1' x1 | q1' Y1)^l' (w2' x2 | q2' Y2)^l'
+ *                                         (two compartments, both kept) */
+enum { K_LOCAL = 0, K_PARENT_CHILD = 1, K_CREATE = 2, K_DISSOLVE = 3, K_FUSION = 4, K_NESTED = 5, K_PAIR = 6 };
 
 /* Pattern rows of lhs / rhs ([M][ROWS][S]):
  *   0  the context's content (the parent's, for rules with a compartment)
  *   1  wrap of the (first) child      2  content of the (first) child
- *   3  FUSION: wrap of the second child, NESTED: wrap of the grandchild
- *   4  FUSION: content of the second child, NESTED: content of the grandchild
+ *   3  FUSION, PAIR: wrap of the second child, NESTED: wrap of the grandchild
+ *   4  FUSION, PAIR: content of the second child, NESTED: content of the grandchild
  * CREATE's rhs rows 1, 2 are the new compartment's wrap and content; FUSION's
  * rhs rows 1, 2 are added to the merged wrap and content. */
 #define ROWS 5
@@ -340,13 +344,13 @@ static int pattern_count(const int32_t* pattern, const int32_t* multiset, int32_
 /* PARENT_CHILD/DISSOLVE: a child slot of label child_label whose parent has  */
 /* the rule's label.                                                          */
 /* NESTED: a grandchild slot of label grand_label whose parent has label     */
-/* child_label and whose grandparent has the rule's label.  FUSION's contexts */
-/* are pairs of slots (is_pair below), never single slots.                    */
+/* child_label and whose grandparent has the rule's label.  FUSION's and     */
+/* PAIR's contexts are pairs of slots (is_pair below), never single slots.   */
 static int is_context(const oracle_model* m, const term_t* t, int j, int c) {
   if (!t->alive[c]) return 0;
   int kind = m->kind[j];
   if (kind == K_LOCAL || kind == K_CREATE) return t->label[c] == m->ctx_label[j];
-  if (kind == K_FUSION) return 0;
+  if (kind == K_FUSION || kind == K_PAIR) return 0;
   if (c == 0) return 0;
   int q = t->parent[c];
   if (kind == K_NESTED) {
@@ -356,16 +360,24 @@ static int is_context(const oracle_model* m, const term_t* t, int j, int c) {
   return t->label[c] == m->child_label[j] && t->label[q] == m->ctx_label[j];
 }
 
-/* FUSION: are the two patterns identical?  Then the occurrences (d1, d2) and */
-/* (d2, d1) are the same subterm and only d1 < d2 counts.                      */
-static int fusion_symmetric(const oracle_model* m, int j) {
-  const int32_t* lhs = m->lhs + (size_t)j * ROWS * m->S;
-  for (int x = 0; x < m->S; x++)
-    if (lhs[m->S + x] != lhs[3 * m->S + x] || lhs[2 * m->S + x] != lhs[4 * m->S + x]) return 0;
+/* FUSION: are the two compartment patterns identical?  Then the occurrences */
+/* (d1, d2) and (d2, d1) are the same subterm and only d1 < d2 counts (the    */
+/* merged result is the same either way).  PAIR: the two compartments keep   */
+/* their own right-hand sides, so (d1, d2) and (d2, d1) are the same rewrite  */
+/* only when the right-hand patterns are identical too.                       */
+static int pair_symmetric(const oracle_model* m, int j) {
+  const int S = m->S;
+  const int32_t* lhs = m->lhs + (size_t)j * ROWS * S;
+  const int32_t* rhs = m->rhs + (size_t)j * ROWS * S;
+  for (int x = 0; x < S; x++)
+    if (lhs[S + x] != lhs[3 * S + x] || lhs[2 * S + x] != lhs[4 * S + x]) return 0;
+  if (m->kind[j] == K_PAIR)
+    for (int x = 0; x < S; x++)
+      if (rhs[S + x] != rhs[3 * S + x] || rhs[2 * S + x] != rhs[4 * S + x]) return 0;
   return 1;
 }
 
-/* Is the ordered pair (d1, d2) an occurrence context of FUSION rule j: two   */
+/* Is the ordered pair (d1, d2) an occurrence context of FUSION / PAIR rule j: two */
 /* distinct alive children of label child_label under the same parent, whose */
 /* label is the rule's?                                                        */
 static int is_pair(const oracle_model* m, const term_t* t, int j, int d1, int d2) {
@@ -373,7 +385,7 @@ static int is_pair(const oracle_model* m, const term_t* t, int j, int d1, int d2
   if (t->label[d1] != m->child_label[j] || t->label[d2] != m->child_label[j]) return 0;
   if (t->parent[d1] != t->parent[d2]) return 0;
   if (t->label[t->parent[d1]] != m->ctx_label[j]) return 0;
-  if (d1 > d2 && fusion_symmetric(m, j)) return 0;
+  if (d1 > d2 && pair_symmetric(m, j)) return 0;
   return 1;
 }
 
@@ -405,7 +417,7 @@ static int match_count(const oracle_model* m, const term_t* t, int j, int c, int
   return 0;
 }
 
-/* FUSION: occurrences at the pair (d1, d2): parent content x first child's   */
+/* FUSION, PAIR: occurrences at the pair (d1, d2): parent content x first child's */
 /* wrap and content x second child's wrap and content.                        */
 static int pair_count(const oracle_model* m, const term_t* t, int j, int d1, int d2, int64_t* h) {
   const int32_t S = m->S;
@@ -424,7 +436,7 @@ static int pair_count(const oracle_model* m, const term_t* t, int j, int d1, int
 /* H_j = sum over contexts of the combinatorial counts (int64, -1 overflow). */
 static int rule_total(const oracle_model* m, const term_t* t, int j, int64_t* H) {
   int64_t total = 0;
-  if (m->kind[j] == K_FUSION) {
+  if (m->kind[j] == K_FUSION || m->kind[j] == K_PAIR) {
     for (int d1 = 0; d1 < t->C; d1++)
       for (int d2 = 0; d2 < t->C; d2++) {
         if (!is_pair(m, t, j, d1, d2)) continue;
@@ -493,6 +505,19 @@ static int apply_rule(const oracle_model* m, term_t* t, int j, int c) {
     int q = t->parent[c], a = t->parent[q];
     int32_t* ms[5] = {t->content + (size_t)a * S, t->wrap + (size_t)q * S, t->content + (size_t)q * S,
                       t->wrap + (size_t)c * S, t->content + (size_t)c * S};
+    for (int row = 0; row < 5; row++)
+      for (int s = 0; s < S; s++)
+        if (!fits((int64_t)ms[row][s] + rhs[row * S + s] - lhs[row * S + s])) return ST_INT_OVERFLOW;
+    for (int row = 0; row < 5; row++)
+      for (int s = 0; s < S; s++) ms[row][s] = ms[row][s] + rhs[row * S + s] - lhs[row * S + s];
+    return ST_OK;
+  }
+  if (kind == K_PAIR) {
+    /* c encodes the pair (d1, d2): the parent content and both compartments' */
+    /* wraps and contents are rewritten in place                              */
+    int d1 = c & 0xffff, d2 = c >> 16, q = t->parent[d1];
+    int32_t* ms[5] = {t->content + (size_t)q * S, t->wrap + (size_t)d1 * S, t->content + (size_t)d1 * S,
+                      t->wrap + (size_t)d2 * S, t->content + (size_t)d2 * S};
     for (int row = 0; row < 5; row++)
       for (int s = 0; s < S; s++)
         if (!fits((int64_t)ms[row][s] + rhs[row * S + s] - lhs[row * S + s])) return ST_INT_OVERFLOW;
@@ -731,7 +756,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
   const int S = m->S, C = m->C, M = m->M, O = num_obs(m);
   if (S < 1 || C < 1 || M < 1 || m->L < 1) return -1;
   for (int j = 0; j < M; j++) {
-    if (m->kind[j] < 0 || m->kind[j] > 5) return -1;
+    if (m->kind[j] < 0 || m->kind[j] > 6) return -1;
     if (m->rate_law != NULL && m->rate_law[j] != 0) {
       /* Michaelis-Menten: flat models, LOCAL, one or two reactant species of
          multiplicity 1 among which the substrate, K > 0 finite */
@@ -863,7 +888,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
       if (m->rate_law != NULL && m->rate_law[j] > 0) xc = 0; /* flat: the root is the only context */
       int ctx = -1;
       uint64_t cum = 0;
-      if (m->kind[j] == K_FUSION) {
+      if (m->kind[j] == K_FUSION || m->kind[j] == K_PAIR) {
         /* pairs in ascending (d1, d2) order; the context id is d1 | d2 << 16 */
         for (int d1 = 0; d1 < C && ctx < 0; d1++)
           for (int d2 = 0; d2 < C; d2++) {
@@ -874,7 +899,7 @@ int oracle_simulate(const oracle_model* m, const double* rates, int32_t P, int32
             if (xc < cum) { ctx = d1 | (d2 << 16); break; }
           }
       }
-      for (int c = 0; c < C && m->kind[j] != K_FUSION; c++) {
+      for (int c = 0; c < C && m->kind[j] != K_FUSION && m->kind[j] != K_PAIR; c++) {
         if (!is_context(m, &t, j, c)) continue;
         int64_t hc;
         match_count(m, &t, j, c, &hc);

@@ -28,12 +28,16 @@ Model representation (the restricted CWC rule language of Sec. 2.1-2.2):
   ``NESTED``       ``l: p X (w x | q Y (v z | u Z)^l'')^l' ->
                    p' X (w' x | q' Y (v' z | u' Z)^l'')^l'`` rewrites a
                    compartment two levels down together with its parent and
-                   grandparent (a pattern of depth two).
+                   grandparent (a pattern of depth two);
+  ``PAIR``         ``l: p X (w1 x1 | q1 Y1)^l' (w2 x2 | q2 Y2)^l' ->
+                   p' X (w1' x1 | q1' Y1)^l' (w2' x2 | q2' Y2)^l'`` rewrites
+                   two sibling compartments, both kept (e.g. transport from
+                   one to the other).
 * ``lhs[j, 0/1/2, :]`` are the multiplicities of the parent (context)
   content, child wrap and child content patterns; ``rhs`` the same for the
   right-hand side.  ``lhs_ext[j, 0/1, :]`` (and ``rhs_ext``) are rows 3 and 4:
-  the second child's wrap and content (FUSION) or the grandchild's wrap and
-  content (NESTED); ``grand_label[j]`` is NESTED's grandchild label.
+  the second child's wrap and content (FUSION, PAIR) or the grandchild's wrap
+  and content (NESTED); ``grand_label[j]`` is NESTED's grandchild label.
 
 Flat mass-action networks are the special case ``L = 1``, ``C = 1`` and only
 ``LOCAL`` rules on label 0.
@@ -48,9 +52,9 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-LOCAL, PARENT_CHILD, CREATE, DISSOLVE, FUSION, NESTED = 0, 1, 2, 3, 4, 5
+LOCAL, PARENT_CHILD, CREATE, DISSOLVE, FUSION, NESTED, PAIR = 0, 1, 2, 3, 4, 5, 6
 KIND_NAMES = {LOCAL: "LOCAL", PARENT_CHILD: "PARENT_CHILD", CREATE: "CREATE", DISSOLVE: "DISSOLVE",
-              FUSION: "FUSION", NESTED: "NESTED"}
+              FUSION: "FUSION", NESTED: "NESTED", PAIR: "PAIR"}
 
 _MASK64 = (1 << 64) - 1
 
@@ -200,7 +204,7 @@ class RuleSpec:
     rhs_ctx: Dict[int, int] = dataclasses.field(default_factory=dict)
     rhs_wrap: Dict[int, int] = dataclasses.field(default_factory=dict)
     rhs_child: Dict[int, int] = dataclasses.field(default_factory=dict)
-    # rows 3 and 4: the second child (FUSION) or the grandchild (NESTED)
+    # rows 3 and 4: the second child (FUSION, PAIR) or the grandchild (NESTED)
     lhs_wrap2: Dict[int, int] = dataclasses.field(default_factory=dict)
     lhs_child2: Dict[int, int] = dataclasses.field(default_factory=dict)
     rhs_wrap2: Dict[int, int] = dataclasses.field(default_factory=dict)
@@ -216,7 +220,7 @@ def cwc_model(n_species: int, n_labels: int, max_compartments: int,
     kind = np.zeros(M, np.int32)
     ctx = np.zeros(M, np.int32)
     child = np.full(M, -1, np.int32)
-    ext = any(r.kind in (FUSION, NESTED) or r.lhs_wrap2 or r.lhs_child2 or r.rhs_wrap2 or r.rhs_child2
+    ext = any(r.kind in (FUSION, NESTED, PAIR) or r.lhs_wrap2 or r.lhs_child2 or r.rhs_wrap2 or r.rhs_child2
               for r in rules)
     lhs_ext = np.zeros((M, 2, n_species), np.int32)
     rhs_ext = np.zeros((M, 2, n_species), np.int32)
@@ -610,16 +614,21 @@ GEN_M, GEN_V = 5, 6   # cell and vesicle tokens (one in every wrap; merged wraps
 
 def cwc_general(R: int = 256, G: int = 50, seed: int = 7) -> Batch:
     """Seven species (A..E = 0..4, the cell token M = 5, the vesicle token
-    V = 6), labels top / cell / vesicle, 19 rules of all six kinds:
+    V = 6), labels top / cell / vesicle, 21 rules of all seven kinds:
     reactions in each compartment type, transport across the cell and the
     vesicle membranes, creation and dissolution of cells (token M) and
     vesicles (token V), fusion of two cells (identical patterns: one M in
     each wrap) and of two vesicles (different patterns: V in the first wrap,
-    E in the second content), and two depth-two rules (E taken out of a
+    E in the second content), two depth-two rules (E taken out of a
     vesicle straight into the top with a B there; vesicle-membrane catalysis
-    of A -> C in the cell).  Tokens are conserved (10 M, 8 V), so at most 18
+    of A -> C in the cell), and two rules on two sibling compartments that
+    keep both (a C passed from one cell to another: ordered pairs; both
+    vesicles of a pair turning a D into an E: unordered pairs).  Tokens are
+    conserved (10 M, 8 V), so at most 18
     compartments exist besides the root (24 slots).  Rates log-uniform over
-    two decades with volume scaling for Omega = 50; initial term: the top with
+    two decades with volume scaling for Omega = 50 (creation, dissolution and
+    the two-compartment rules log-uniform in [10^-1.5, 10^-0.5] without
+    scaling); initial term: the top with
     U{20..80} of A..E and 6 free M, 4 cells each with one M in the wrap,
     U{5..40} of A..E, one free V and one vesicle (one V in its wrap, U{2..10}
     of A..E)."""
@@ -646,13 +655,15 @@ def cwc_general(R: int = 256, G: int = 50, seed: int = 7) -> Batch:
         RuleSpec(NESTED, 0, 1, grand_label=2, lhs_ctx={B: 1}, lhs_child2={E: 1}, rhs_ctx={C_: 1}),
         RuleSpec(NESTED, 0, 1, grand_label=2, lhs_child={A: 1}, lhs_wrap2={V: 1},
                  rhs_child={C_: 1}, rhs_wrap2={V: 1}),
+        RuleSpec(PAIR, 0, 1, lhs_child={C_: 1}, rhs_child2={C_: 1}),
+        RuleSpec(PAIR, 1, 2, lhs_child={D: 1}, lhs_child2={D: 1}, rhs_child={E: 1}, rhs_child2={E: 1}),
     ]
     model = cwc_model(S, L, Cmax, rules, "cwc_general")
     rng = SplitMix64(seed)
     omega = 50.0
     rates = np.empty(model.n_rules, np.float64)
     for j in range(model.n_rules):
-        if model.kind[j] in (CREATE, DISSOLVE, FUSION):
+        if model.kind[j] in (CREATE, DISSOLVE, FUSION, PAIR):
             rates[j] = rng.log_uniform(-1.5, -0.5)
         else:
             lhs5, _, _ = model.rows5()

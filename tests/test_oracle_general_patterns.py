@@ -1,5 +1,6 @@
 """Pins of the oracle's general CWC patterns: two compartments in one
-left-hand side (FUSION) and a pattern of depth two (NESTED).
+left-hand side, merged (FUSION) or both kept (PAIR), and a pattern of depth
+two (NESTED).
 
 Sec. 2.1 lets a pattern be any term with variables, so a left-hand side may
 hold several compartments, themselves holding compartments; Sec. 2.2 counts
@@ -12,12 +13,21 @@ rule.  The pins check the oracle against that definition and against laws:
   rule's combinatorial count.  This fixes, among others, that a FUSION whose
   two compartment patterns are identical counts unordered pairs and one
   whose patterns differ counts ordered pairs (the oracle's rule), and that
-  NESTED matches only grandchildren under the right labels.
+  NESTED matches only grandchildren under the right labels.  A PAIR keeps
+  both compartments, each with its own right-hand side, so a match and its
+  swap are one application only when both the left- and the right-hand
+  patterns of the two compartments are identical (same consumed items, same
+  resulting term); the brute force then keys an application by its consumed
+  items plus, when the right-hand patterns differ, which compartment played
+  the first role.
 * laws: fusion of m empty compartments at rate k per pair is a pure-death
   chain with rate k C(n, 2) (Kingman's coalescent), checked against the
   chemical master equation; content is conserved by fusion; transport from a
   grandchild to its grandparent at rate k per atom leaves Bin(N, 1 - e^-kt)
-  atoms at the top.
+  atoms at the top; PAIR transport of one atom at a time between two sibling
+  compartments at rate k per atom is the Ehrenfest model: every atom flips
+  independently at rate k, so N atoms started in the first compartment leave
+  Bin(N, (1 + e^-2kt) / 2) there.
 """
 import itertools
 import math
@@ -65,7 +75,10 @@ def brute_force_count(model, img, j):
     cont = {c: img[c, 3 + S:3 + 2 * S] for c in alive}
     kind, lab, ch = int(model.kind[j]), int(model.ctx_label[j]), int(model.child_label[j])
     occ = set()
-    if kind == W.FUSION:
+    if kind in (W.FUSION, W.PAIR):
+        _, rhs5, _ = model.rows5()
+        role = kind == W.PAIR and not (np.array_equal(rhs5[j][1], rhs5[j][3]) and
+                                       np.array_equal(rhs5[j][2], rhs5[j][4]))
         for d1 in alive:
             for d2 in alive:
                 if d1 == d2 or d1 == 0 or d2 == 0 or label[d1] != ch or label[d2] != ch:
@@ -78,7 +91,8 @@ def brute_force_count(model, img, j):
                                                _choices((d1, "c"), cont[d1], lhs[2]),
                                                _choices((d2, "w"), wrap[d2], lhs[3]),
                                                _choices((d2, "c"), cont[d2], lhs[4])):
-                    occ.add(frozenset().union(*parts) | {("comp", d1), ("comp", d2)})
+                    key = frozenset().union(*parts) | {("comp", d1), ("comp", d2)}
+                    occ.add(key | {("first", d1)} if role else key)
     elif kind == W.NESTED:
         for g in alive:
             if g == 0 or label[g] != grand[j]:
@@ -94,13 +108,19 @@ def brute_force_count(model, img, j):
                                            _choices((g, "c"), cont[g], lhs[4])):
                 occ.add(frozenset().union(*parts) | {("comp", q), ("comp", g)})
     else:
-        raise ValueError("brute force covers FUSION and NESTED")
+        raise ValueError("brute force covers FUSION, PAIR and NESTED")
     return len(occ)
 
 
 def _general_rules():
-    F, N = W.FUSION, W.NESTED
+    F, N, P = W.FUSION, W.NESTED, W.PAIR
     return [
+        W.RuleSpec(P, 0, 1, lhs_child={0: 1}, rhs_child2={0: 1}),                # transport d1 -> d2
+        W.RuleSpec(P, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={0: 1},
+                   rhs_wrap={1: 1}, rhs_wrap2={1: 1}),                           # symmetric rewrite
+        W.RuleSpec(P, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={0: 1},
+                   rhs_wrap={1: 1}, rhs_wrap2={0: 1}),                           # same lhs, one-sided rhs
+        W.RuleSpec(P, 1, 2, lhs_ctx={1: 1}, lhs_child={0: 1}, lhs_child2={1: 1}, rhs_ctx={0: 1}),
         W.RuleSpec(F, 0, 1),                                                     # empty patterns
         W.RuleSpec(F, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={0: 1}),                  # identical patterns
         W.RuleSpec(F, 0, 1, lhs_wrap={0: 1}, lhs_child2={1: 1}),                 # different patterns
@@ -128,7 +148,7 @@ def _random_term(rng, model, n_comp):
     return img
 
 
-def test_brute_force_counts_fusion_and_nested():
+def test_brute_force_counts_fusion_pair_and_nested():
     model = W.cwc_model(2, 3, 8, _general_rules())
     rng = np.random.default_rng(2024)
     nonzero = np.zeros(model.n_rules, int)
@@ -277,3 +297,93 @@ def test_nested_transport_from_grandchildren_is_binomial():
         pmf = stats.binom.pmf(np.arange(41), 40, 1 - math.exp(-k * t))
         assert _chi2(st[:, g, 0], pmf) > P_MIN
     assert np.all(st[:, -1, 2] >= 9)                            # the decoy is never drained
+
+
+def test_pair_counts_unordered_pairs_only_for_fully_symmetric_rules():
+    """Three label-1 children of the top with wraps (a, b) = (1,0), (1,1), (2,1):
+    identical left- and right-hand patterns count unordered pairs; identical
+    left-hand but different right-hand patterns count ordered pairs (the two
+    roles give different terms); different left-hand patterns count ordered
+    pairs."""
+    rules = [W.RuleSpec(W.PAIR, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={0: 1}, rhs_wrap={1: 1}, rhs_wrap2={1: 1}),
+             W.RuleSpec(W.PAIR, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={0: 1}, rhs_wrap={1: 1}, rhs_wrap2={0: 1}),
+             W.RuleSpec(W.PAIR, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={1: 1})]
+    model = W.cwc_model(2, 2, 4, rules)
+    img = W.empty_slot_image(model)
+    wraps = {1: (1, 0), 2: (1, 1), 3: (2, 1)}
+    for c, (a, b) in wraps.items():
+        img[c, :3] = [1, 1, 0]
+        img[c, 3:5] = [a, b]
+    H = oracle.rule_totals(model, img)
+    a = {c: v[0] for c, v in wraps.items()}
+    b = {c: v[1] for c, v in wraps.items()}
+    pairs = [(x, y) for x in wraps for y in wraps if x != y]
+    assert H[0] == sum(a[x] * a[y] for x, y in pairs) // 2       # unordered
+    assert H[1] == sum(a[x] * a[y] for x, y in pairs)            # ordered
+    assert H[2] == sum(a[x] * b[y] for x, y in pairs)            # ordered
+    assert [H[j] for j in range(3)] == [brute_force_count(model, img, j) for j in range(3)]
+
+
+def test_pair_rewrites_both_compartments_in_place():
+    """One event of a PAIR rule: the chosen (d1, d2) loses the matched atoms,
+    gains its own right-hand atoms, and both compartments stay alive with
+    their labels and parents; the parent content changes by row 0."""
+    rules = [W.RuleSpec(W.PAIR, 0, 1, lhs_ctx={2: 1}, lhs_child={0: 1}, lhs_wrap2={1: 1},
+                        rhs_child={1: 1}, rhs_wrap2={0: 2}, rhs_child2={2: 1})]
+    model = W.cwc_model(3, 2, 4, rules)
+    S = 3
+    img = W.empty_slot_image(model)
+    img[0, 3 + S + 2] = 5
+    img[1, :3] = [1, 1, 0]
+    img[1, 3 + S + 0] = 1          # content a of slot 1
+    img[2, :3] = [1, 1, 0]
+    img[2, 3 + 1] = 1              # wrap b of slot 2
+    # the only occurrence: first = slot 1 (has a), second = slot 2 (wrap b)
+    assert oracle.rule_totals(model, img)[0] == 5
+    res = _run(model, img, [1.0], np.array([0.0, 50.0]), 1, 3, log_cap=4)
+    assert res["log_rule"][0, 0] == 0 and res["log_slot"][0, 0] == 1 | (2 << 16)
+    st = res["states"][0, 1]                      # observables after the only event
+    L = 2
+    cont = st[:L * S].reshape(L, S)
+    wr = st[L * S:L * S + (L - 1) * S].reshape(L - 1, S)
+    alive = st[L * S + (L - 1) * S:]
+    assert cont[0].tolist() == [0, 0, 4]          # root lost one c
+    assert cont[1].tolist() == [0, 1, 1]          # slot 1: a -> b; slot 2 gained c
+    assert wr[0].tolist() == [2, 0, 0]            # slot 2's wrap b -> 2 a
+    assert alive.tolist() == [1, 2]
+
+
+def test_pair_transport_between_siblings_is_the_ehrenfest_model():
+    """Two label-1 compartments, N atoms a in the first; PAIR (a X)(Y) -> (X)(a Y)
+    at rate k per atom, in both directions (ordered pairs): each atom flips
+    independently at rate k, so the first compartment holds
+    Bin(N, (1 + e^-2kt) / 2)."""
+    N, k = 12, 0.7
+    model = W.cwc_model(1, 2, 3, [W.RuleSpec(W.PAIR, 0, 1, lhs_child={0: 1}, rhs_child2={0: 1})])
+    img = W.empty_slot_image(model)
+    img[1, :3] = [1, 1, 0]
+    img[2, :3] = [1, 1, 0]
+    img[1, 3 + 1] = N
+    grid = np.array([0.0, 0.2, 0.6, 1.5, 4.0])
+    R = 20000
+    b = W.Batch(model, np.array([[k]]), img[None].astype(np.int32), grid, R, 41)
+    res = oracle.simulate(b, threads=8, log_cap=128)
+    ls = res["log_slot"][res["log_rule"] >= 0]
+    assert set(np.unique(ls).tolist()) == {1 | (2 << 16), 2 | (1 << 16)}
+    # the observables hold label totals only (always N at label 1), so slot
+    # 1's count is rebuilt from the event log: each event moves one atom
+    lt, ev = res["log_t"], res["events"]
+    assert np.all(ev < 128)
+    n1 = np.full((R, len(grid)), N)
+    for r in range(R):
+        cnt = N
+        e = 0
+        for g, t in enumerate(grid):
+            while e < ev[r] and lt[r, e] < t:
+                cnt += -1 if res["log_slot"][r, e] == (1 | (2 << 16)) else 1
+                e += 1
+            n1[r, g] = cnt
+    for g, t in enumerate(grid):
+        p = (1 + math.exp(-2 * k * t)) / 2
+        pmf = stats.binom.pmf(np.arange(N + 1), N, p)
+        assert _chi2(n1[:, g], pmf) > P_MIN, (t, n1[:, g].mean(), N * p)

@@ -175,7 +175,8 @@ def test_lotka_volterra_chain(n):
 
 def test_general_pattern_workload_recipe():
     """cwc_general: every rule kind present, FUSION with identical (cells) and
-    different (vesicles) patterns, NESTED with its grandchild label; tokens
+    different (vesicles) patterns, PAIR with ordered (cells) and unordered
+    (vesicles) pairs, NESTED with its grandchild label; tokens
     M (cells) and V (vesicles): one in every wrap, conserved by every rule,
     so at most 18 compartments besides the root exist (24 slots)."""
     b = W.cwc_general()
@@ -197,6 +198,9 @@ def test_general_pattern_workload_recipe():
             assert grand[j] == 2 and m.child_label[j] == 1 and m.ctx_label[j] == 0
     fus = np.nonzero(m.kind == W.FUSION)[0]
     sym = [np.array_equal(lhs5[j, 1:3], lhs5[j, 3:5]) for j in fus]
+    assert sorted(sym) == [False, True]
+    pair = np.nonzero(m.kind == W.PAIR)[0]
+    sym = [np.array_equal(lhs5[j, 1:3], lhs5[j, 3:5]) and np.array_equal(rhs5[j, 1:3], rhs5[j, 3:5]) for j in pair]
     assert sorted(sym) == [False, True]
     img = b.init[0]
     S = m.n_species
