@@ -77,11 +77,20 @@ enum {
                                 are identical); the lower slot keeps the merged
                                 compartment, the other is freed and its
                                 children move to the survivor                */
-  CWC_RULE_NESTED = 5        /* a pattern of depth two:
+  CWC_RULE_NESTED = 5,       /* a pattern of depth two:
                                 l: p X (w x | q Y (v z | u Z)^l'')^l'
                                    -> p' X (w' x | q' Y (v' z | u' Z)^l'')^l'
                                 contexts: grandchild slots of label l'' under
                                 a slot of label l' under one of label l     */
+  CWC_RULE_PAIR = 6          /* two compartments in one left-hand side, both
+                                kept, each with its own right-hand side:
+                                l: p X (w1 x1 | q1 Y1)^l' (w2 x2 | q2 Y2)^l'
+                                   -> p' X (w1' x1 | q1' Y1)^l' (w2' x2 | q2' Y2)^l'
+                                contexts: ordered pairs of sibling l' slots,
+                                unordered when both the left- and the right-
+                                hand patterns of the two compartments are
+                                identical (a match and its swap then give the
+                                same term)                                   */
 };
 
 /*
@@ -97,13 +106,14 @@ enum {
  *   uses lhs row 0 and rhs rows 0..2 (rows 1, 2 = the new compartment's wrap
  *   and content); DISSOLVE uses lhs rows 0..2 and rhs row 0.  At most four
  *   species with a nonzero left-hand multiplicity per rule.
- *   FUSION and NESTED rules need two more pattern rows and a third label
- *   (all three pointers may be NULL when no rule is of those kinds):
- *   grand_label[M] in [1, L) for NESTED (ignored otherwise);
+ *   FUSION, NESTED and PAIR rules need two more pattern rows and NESTED a
+ *   third label (all three pointers may be NULL when no rule is of those
+ *   kinds): grand_label[M] in [1, L) for NESTED (ignored otherwise);
  *   lhs_ext[M][2][S] (in {0, 1, 2}) and rhs_ext[M][2][S] (<= 1000): rows 3
  *   and 4, the second child's wrap and content (FUSION, whose rhs rows 3, 4
- *   must be 0; its rhs rows 1, 2 are added to the merged wrap and content)
- *   or the grandchild's wrap and content (NESTED).
+ *   must be 0; its rhs rows 1, 2 are added to the merged wrap and content;
+ *   PAIR, whose rhs rows 1, 2 and 3, 4 are the two compartments' new wrap
+ *   and content patterns) or the grandchild's wrap and content (NESTED).
  * Flat mass-action networks are L = 1, C = 1, all rules LOCAL on label 0.
  *   Rate laws (Sec. 2.2 takes mass action as the usual rate and allows other
  *   kinetics; both pointers may be NULL, meaning mass action throughout):

@@ -397,12 +397,13 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
   for (int j = 0; j < M; ++j) {
     const int k = d->kind[j];
     const std::string rj = "rule " + std::to_string(j);
-    if (k < CWC_RULE_LOCAL || k > CWC_RULE_NESTED) return fail(CWC_ERR_INVALID_ARG, rj + ": bad kind");
+    if (k < CWC_RULE_LOCAL || k > CWC_RULE_PAIR) return fail(CWC_ERR_INVALID_ARG, rj + ": bad kind");
     if (d->ctx_label[j] < 0 || d->ctx_label[j] >= L) return fail(CWC_ERR_INVALID_ARG, rj + ": ctx_label out of range");
     if (k != CWC_RULE_LOCAL && (d->child_label[j] < 1 || d->child_label[j] >= L))
       return fail(CWC_ERR_INVALID_ARG, rj + ": child_label out of [1, L)");
-    if ((k == CWC_RULE_FUSION || k == CWC_RULE_NESTED) && (d->lhs_ext == nullptr || d->rhs_ext == nullptr))
-      return fail(CWC_ERR_INVALID_ARG, rj + ": FUSION and NESTED rules need lhs_ext and rhs_ext");
+    if ((k == CWC_RULE_FUSION || k == CWC_RULE_NESTED || k == CWC_RULE_PAIR) &&
+        (d->lhs_ext == nullptr || d->rhs_ext == nullptr))
+      return fail(CWC_ERR_INVALID_ARG, rj + ": FUSION, NESTED and PAIR rules need lhs_ext and rhs_ext");
     if (k == CWC_RULE_NESTED && (d->grand_label == nullptr || d->grand_label[j] < 1 || d->grand_label[j] >= L))
       return fail(CWC_ERR_INVALID_ARG, rj + ": NESTED needs grand_label in [1, L)");
     int factors = 0;
@@ -428,7 +429,7 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
     if (k == CWC_RULE_DISSOLVE && rhs_child)
       return fail(CWC_ERR_INVALID_ARG, rj + ": DISSOLVE writes the parent content only");
     if (k <= CWC_RULE_DISSOLVE && (lhs_more || rhs_more))
-      return fail(CWC_ERR_INVALID_ARG, rj + ": pattern rows 3-4 belong to FUSION and NESTED rules");
+      return fail(CWC_ERR_INVALID_ARG, rj + ": pattern rows 3-4 belong to FUSION, NESTED and PAIR rules");
     if (k == CWC_RULE_FUSION && rhs_more)
       return fail(CWC_ERR_INVALID_ARG, rj + ": FUSION writes the merged wrap and content through rhs rows 1-2");
     const int law = d->rate_law ? d->rate_law[j] : 0;
@@ -475,7 +476,7 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
     for (int j = 0; j < M; ++j) {
       const int kind = d->kind[j], ctx = d->ctx_label[j], ch = d->child_label[j];
       const int gr = kind == CWC_RULE_NESTED ? d->grand_label[j] : 0;
-      m->general |= kind == CWC_RULE_FUSION || kind == CWC_RULE_NESTED;
+      m->general |= kind == CWC_RULE_FUSION || kind == CWC_RULE_NESTED || kind == CWC_RULE_PAIR;
       int32_t* rec = tb.data() + (size_t)j * CWC_RULE_WORDS;
       rec[CR_KIND] = kind;
       rec[CR_CTX] = ctx;
@@ -509,15 +510,29 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
         return true;
       };
       bool ok = put(rec, CR_ND0, CR_D0, lrow(j, 0), rrow(j, 0), false);
-      if (kind == CWC_RULE_PARENT_CHILD || kind == CWC_RULE_NESTED) {
+      if (kind == CWC_RULE_PARENT_CHILD || kind == CWC_RULE_NESTED || kind == CWC_RULE_PAIR) {
         ok = ok && put(rec, CR_ND1, CR_D1, lrow(j, 1), rrow(j, 1), false) &&
              put(rec, CR_ND2, CR_D2, lrow(j, 2), rrow(j, 2), false);
       } else if (kind == CWC_RULE_CREATE || kind == CWC_RULE_FUSION) {
         ok = ok && put(rec, CR_ND1, CR_D1, nullptr, rrow(j, 1), true) && put(rec, CR_ND2, CR_D2, nullptr, rrow(j, 2), true);
       }
-      if (kind == CWC_RULE_NESTED) {
-        // rows 3-4 of NESTED go to an extension record after the dependency
-        // list; its offset is known once the list is, so keep it aside
+      if (kind == CWC_RULE_NESTED || kind == CWC_RULE_PAIR) {
+        // rows 3-4 of NESTED and PAIR go to an extension record after the
+        // dependency list; its offset is known once the list is, so keep it
+        // aside.  PAIR's low byte says whether the two compartments' right-
+        // hand patterns are identical (with identical left-hand patterns the
+        // pairs are then unordered)
+        if (kind == CWC_RULE_PAIR) {
+          bool rsym = true;
+          for (int x = 0; x < S; ++x) {
+            const int32_t* r1 = rrow(j, 1);
+            const int32_t* r2 = rrow(j, 2);
+            const int32_t* r3 = rrow(j, 3);
+            const int32_t* r4 = rrow(j, 4);
+            rsym = rsym && r1[x] == r3[x] && r2[x] == r4[x];
+          }
+          rec[CR_GRAND] = rsym ? 1 : 0;
+        }
         nested_ext.emplace_back(j, std::vector<int32_t>(XR_WORDS, 0));
         int32_t* xr = nested_ext.back().second.data();
         ok = ok && put(xr, XR_ND3, XR_D3, lrow(j, 3), rrow(j, 3), false) &&
@@ -534,7 +549,7 @@ cwc_status cwc_model_create(const cwc_model_desc* d, cwc_model** out) {
       }
     }
     std::vector<int32_t> deps_all;
-    auto general = [&](int kind) { return kind == CWC_RULE_FUSION || kind == CWC_RULE_NESTED; };
+    auto general = [&](int kind) { return kind == CWC_RULE_FUSION || kind == CWC_RULE_NESTED || kind == CWC_RULE_PAIR; };
     for (int j = 0; j < M; ++j) {
       int32_t* rec = tb.data() + (size_t)j * CWC_RULE_WORDS;
       rec[CR_DEPOFF] = (int32_t)deps_all.size();

@@ -43,26 +43,29 @@ constexpr int TREE_ROOT = 30;
 //            child's (FUSION) or the grandchild's (NESTED) wrap / content),
 //            rows then species ascending
 //   [8]  n0, [9..16]   changes of the context (parent) content: species | delta << 16
-//   [17] n1, [18..25]  PARENT_CHILD / NESTED: changes of the child wrap; CREATE:
-//                      the new wrap; FUSION: atoms added to the merged wrap
+//   [17] n1, [18..25]  PARENT_CHILD / NESTED / PAIR: changes of the (first)
+//                      child wrap; CREATE: the new wrap; FUSION: atoms added
+//                      to the merged wrap
 //   [26] n2, [27..34]  the same for the child content / new content / merged content
 //   [35] offset and [36] number of dependents (rules whose counts the event
-//        can change; every rule after a FUSION or NESTED event)
+//        can change; every rule after a FUSION, NESTED or PAIR event)
 //   [37] dirty-leaf mask, [38] dirty-node mask of those dependents
-//   [39] NESTED: grandchild label | (word offset of its extension record in
-//        the table) << 8; the extension, after the dependency list, holds
-//        n3, [8] changes of the grandchild wrap, n4, [8] changes of the
-//        grandchild content (species | delta << 16)
+//   [39] NESTED: grandchild label, PAIR: 1 if the two compartments' right-
+//        hand patterns are identical (else 0), | (word offset of the rule's
+//        extension record in the table) << 8; the extension, after the
+//        dependency list, holds n3, [8] changes of the grandchild's (second
+//        child's) wrap, n4, [8] changes of its content (species | delta << 16)
 // The 40-word stride keeps the records of different rules in different
 // shared-memory banks when the lanes of a warp read different rules.
 constexpr int CWC_RULE_WORDS = 40;
 constexpr int CR_KIND = 0, CR_CTX = 1, CR_CHILD = 2, CR_NREAC = 3, CR_REAC = 4, CR_ND0 = 8, CR_D0 = 9, CR_ND1 = 17,
               CR_D1 = 18, CR_ND2 = 26, CR_D2 = 27, CR_DEPOFF = 35, CR_DEPCNT = 36, CR_LEAFMASK = 37, CR_NODEMASK = 38,
               CR_GRAND = 39;
-// the NESTED extension record: XR_ND3 / XR_D3 / XR_ND4 / XR_D4 words
+// the NESTED / PAIR extension record: XR_ND3 / XR_D3 / XR_ND4 / XR_D4 words
 constexpr int XR_ND3 = 0, XR_D3 = 1, XR_ND4 = 9, XR_D4 = 10, XR_WORDS = 18;
 // rule kinds (values of the C header's CWC_RULE_*)
-constexpr int RK_LOCAL = 0, RK_PARENT_CHILD = 1, RK_CREATE = 2, RK_DISSOLVE = 3, RK_FUSION = 4, RK_NESTED = 5;
+constexpr int RK_LOCAL = 0, RK_PARENT_CHILD = 1, RK_CREATE = 2, RK_DISSOLVE = 3, RK_FUSION = 4, RK_NESTED = 5,
+              RK_PAIR = 6;
 constexpr int CWC_MAX_SLOTS = 64;
 
 // Checkpoint record of a flat trajectory (int32 words): time (double, words

@@ -223,6 +223,9 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
     }
     sym = sym && found;
   }
+  // PAIR: the two compartments keep their own right-hand sides, so a pair
+  // and its swap are one application only if those are identical too
+  if (rec[CR_KIND] == RK_PAIR && (rec[CR_GRAND] & 0xff) == 0) sym = false;
   bool of = false;
   unsigned long long tot = 0ull;
   unsigned long long last = 0ull;
@@ -262,17 +265,23 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
   return of ? (tot | (1ull << 63)) : tot;
 }
 
-// The overflow check and the rewrite of the two-compartment (FUSION) and
+// The overflow check and the rewrite of the two-compartment (FUSION, PAIR) and
 // depth-two (NESTED) rules, out of line (rare events; one copy shared by every
 // lane-group width).  ctx is the grandchild slot (NESTED) or d1 | d2 << 16
 // (FUSION: the lower slot keeps the merged compartment, the higher is freed
-// and its children move to the survivor).
+// and its children move to the survivor; PAIR: d1 takes the first
+// compartment pattern's changes, d2 the second's, both stay).
 __device__ __noinline__ int cwc_general_check(const int32_t* content, const int32_t* wrap, const int32_t* meta, int S,
                                               int C, const int32_t* table, const int32_t* rec, int ctx) {
   auto fits = [](long long v) { return v >= 0 && v <= 0x7FFFFFFFll; };
   const int nr = rec[CR_NREAC];
-  if (rec[CR_KIND] == RK_NESTED) {
-    const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
+  if (rec[CR_KIND] == RK_NESTED || rec[CR_KIND] == RK_PAIR) {
+    // five multisets rewritten in place: NESTED's grandparent content, child
+    // wrap and content, grandchild wrap and content; PAIR's parent content
+    // and both children's wraps and contents
+    const bool pair = rec[CR_KIND] == RK_PAIR;
+    const int g = pair ? (ctx >> 16) : ctx, qq = pair ? (ctx & 0xffff) : (meta[g] >> 8) - 1,
+              aa = (meta[qq] >> 8) - 1;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
     const int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
                             wrap + (size_t)g * S, content + (size_t)g * S};
@@ -318,8 +327,11 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
   auto OC = [&](int l, int x) { return l * S + x; };
   auto OW = [&](int l, int x) { return L * S + (l - 1) * S + x; };
   auto OA = [&](int l) { return L * S + (L - 1) * S + l; };
-  if (rec[CR_KIND] == RK_NESTED) {
-    const int g = ctx, qq = (meta[g] >> 8) - 1, aa = (meta[qq] >> 8) - 1;
+  if (rec[CR_KIND] == RK_NESTED || rec[CR_KIND] == RK_PAIR) {
+    // (PAIR: qq = the first child, g = the second, aa = their parent)
+    const bool pair = rec[CR_KIND] == RK_PAIR;
+    const int g = pair ? (ctx >> 16) : ctx, qq = pair ? (ctx & 0xffff) : (meta[g] >> 8) - 1,
+              aa = (meta[qq] >> 8) - 1;
     const int la = meta[aa] & 0xff, lq = meta[qq] & 0xff, lg = meta[g] & 0xff;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
     int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
@@ -575,8 +587,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     return acc;
   };
-  // candidate contexts of rule i, in ascending slot order (FUSION: the slots
-  // its pairs are drawn from)
+  // candidate contexts of rule i, in ascending slot order (FUSION, PAIR: the
+  // slots its pairs are drawn from)
   auto ctx_mask = [&](const int32_t* rec) -> unsigned long long {
     const int kind = rec[CR_KIND];
     if (kGen && kind == RK_NESTED) return labmask[rec[CR_GRAND] & 0xff];
@@ -611,7 +623,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // H_i from scratch: sum over all its contexts
   auto total_h = [&](int i) -> unsigned long long {
     const int32_t* rec = s_rules + i * CWC_RULE_WORDS;
-    if (kGen && rec[CR_KIND] == RK_FUSION) {
+    if (kGen && (rec[CR_KIND] == RK_FUSION || rec[CR_KIND] == RK_PAIR)) {
       const unsigned long long r = cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), false, 0ull);
       if (r >> 63) ovf = true;
       return r & ~(1ull << 63);
@@ -1185,7 +1197,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const uint4 w1 = philox4x32_10(make_uint4(n, 1u, rr, (uint32_t)p), prm.key0, prm.key1);
     const unsigned long long Wd = (unsigned long long)w1.x | ((unsigned long long)w1.y << 32);
     const unsigned long long xc = __umul64hi(Wd, HV(j));
-    const int ctx = (kGen && rec[CR_KIND] == RK_FUSION)
+    const int ctx = (kGen && (rec[CR_KIND] == RK_FUSION || rec[CR_KIND] == RK_PAIR))
                         ? (int)cwc_fusion_scan(content, wrap, meta, S, rec, ctx_mask(rec), true, xc)
                         : choose_context(rec, xc);
     // 3. update.  Only contexts in `touched` can change their counts: the
@@ -1193,7 +1205,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     // and the free slots (one of which CREATE fills).  Each dependent rule
     // drops the old counts of its touched contexts and adds the new ones; a
     // rule whose contexts all lie in `touched` is summed afresh.
-    const bool general_j = kGen && (rec[CR_KIND] == RK_FUSION || rec[CR_KIND] == RK_NESTED);
+    const bool general_j = kGen && (rec[CR_KIND] == RK_FUSION || rec[CR_KIND] == RK_NESTED || rec[CR_KIND] == RK_PAIR);
     const int ast = general_j ? cwc_general_check(content, wrap, meta, S, C, s_rules, rec, ctx)
                     : kL > 1  ? cwc_apply_check(content, wrap, meta, *alive_p, S, C, rec, ctx)
                               : apply_check(rec, ctx);
@@ -1202,7 +1214,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       return 1;
     }
     const int kind_j = rec[CR_KIND];
-    // FUSION and NESTED events touch every slot (every dependent is recounted)
+    // FUSION, NESTED and PAIR events touch every slot (every dependent is recounted)
     unsigned long long touched = general_j ? ~0ull : chmask[ctx];
     if (kind_j == RK_LOCAL || kind_j == RK_CREATE) {
       touched |= 1ull << ctx;
@@ -1213,9 +1225,12 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     if (kSens && gl == 0) Nf[j] += 1;
     const int doff = rec[CR_DEPOFF], dcnt = rec[CR_DEPCNT];
-    // FUSION and NESTED dependents, whose contexts are pairs or grandchildren
-    // rather than the touched slots, are recounted in full after the rewrite
-    auto general_rule = [&](const int32_t* ri) { return kGen && (ri[CR_KIND] == RK_FUSION || ri[CR_KIND] == RK_NESTED); };
+    // FUSION, NESTED and PAIR dependents, whose contexts are pairs or
+    // grandchildren rather than the touched slots, are recounted in full
+    // after the rewrite
+    auto general_rule = [&](const int32_t* ri) {
+      return kGen && (ri[CR_KIND] == RK_FUSION || ri[CR_KIND] == RK_NESTED || ri[CR_KIND] == RK_PAIR);
+    };
     for (int e = gl; e < dcnt; e += kL) {
       const int i = s_deps[doff + e];
       const int32_t* ri = s_rules + i * CWC_RULE_WORDS;

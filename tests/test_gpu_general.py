@@ -1,5 +1,6 @@
 """GPU parity for the general CWC patterns: two compartments in one left-hand
-side (FUSION) and patterns of depth two (NESTED), mixed with every other
+side, merged (FUSION) or both kept (PAIR), and patterns of depth two (NESTED),
+mixed with every other
 rule kind, against the oracle bit for bit (observables, statuses, event
 counts, (rule, context) hashes, final times, event logs); score partials
 within the FP64 tolerance of the other compartment tests."""
@@ -28,14 +29,15 @@ def built():
 @pytest.mark.parametrize("layout,lanes", [(capi.CWC_LAYOUT_STATIC, 1), (capi.CWC_LAYOUT_QUEUE, 1),
                                           (capi.CWC_LAYOUT_QUEUE, 4), (capi.CWC_LAYOUT_STATIC, 8)])
 def test_general_model_bit_exact_with_event_log(layout, lanes):
-    """19 rules of all six kinds, 256 replicas x ~1.2e3 events; every rule
-    kind fires (checked on the oracle's log)."""
+    """21 rules of all seven kinds, 256 replicas x ~1.2e3 events; every rule
+    kind fires (checked on the oracle's log), the symmetric vesicle PAIR too."""
     b = W.cwc_general(R=256)
     g, o = check(b, log_cap=2048, layout=layout, lanes=lanes)
     fired = np.unique(o["log_rule"][o["log_rule"] >= 0])
     assert set(W.KIND_NAMES) == set(b.model.kind[fired].tolist())
-    pairs = o["log_slot"][np.isin(o["log_rule"], np.nonzero(b.model.kind == W.FUSION)[0])]
+    pairs = o["log_slot"][np.isin(o["log_rule"], np.nonzero(np.isin(b.model.kind, (W.FUSION, W.PAIR)))[0])]
     assert pairs.size > 0 and np.all(pairs >> 16 > 0)          # pair contexts were logged
+    assert np.isin(np.nonzero(b.model.kind == W.PAIR)[0], fired).all()
 
 
 def test_general_model_ragged_batch_and_sweep_points():
@@ -149,3 +151,44 @@ def test_checkpoint_records_of_odd_length():
     torch.cuda.synchronize()
     for k in ("states", "status", "events", "hash", "final_t"):
         assert torch.equal(one[k], sl[k]), k
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 8])
+def test_pair_rules_bit_exact(lanes):
+    """The pinned PAIR scenarios: sibling transport (the Ehrenfest model, both
+    directions as ordered pairs) among three compartments, a symmetric rule
+    (unordered pairs), a one-sided rule with identical left-hand patterns
+    (ordered pairs) and a rewrite of the parent content with both children,
+    and a PAIR whose second compartment would overflow: INT_OVERFLOW."""
+    m = W.cwc_model(1, 2, 4, [W.RuleSpec(W.PAIR, 0, 1, lhs_child={0: 1}, rhs_child2={0: 1})])
+    img = W.empty_slot_image(m)
+    for c, n in ((1, 12), (2, 3), (3, 0)):
+        img[c, :3] = [1, 1, 0]
+        img[c, 4] = n
+    g, o = check(W.Batch(m, np.array([[0.7]]), img[None], np.array([0.0, 0.2, 0.6, 1.5, 4.0]), 300, 41),
+                 log_cap=64, lanes=lanes)
+    assert len(set(o["log_slot"][o["log_rule"] >= 0].tolist())) == 6     # all six ordered pairs
+
+    rules = [W.RuleSpec(W.PAIR, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={0: 1}, rhs_wrap={1: 1}, rhs_wrap2={1: 1}),
+             W.RuleSpec(W.PAIR, 0, 1, lhs_wrap={0: 1}, lhs_wrap2={0: 1}, rhs_wrap={1: 1}, rhs_wrap2={0: 1}),
+             W.RuleSpec(W.PAIR, 0, 1, lhs_ctx={2: 1}, lhs_child={0: 1}, lhs_wrap2={1: 1},
+                        rhs_child={1: 1}, rhs_wrap2={0: 2}, rhs_child2={2: 1}),
+             W.RuleSpec(W.PARENT_CHILD, 0, 1, lhs_child={1: 1}, rhs_child={0: 1})]
+    m = W.cwc_model(3, 2, 6, rules)
+    img = W.empty_slot_image(m)
+    img[0, 3 + 3 + 2] = 40
+    for c in range(1, 5):
+        img[c, :3] = [1, 1, 0]
+        img[c, 3:6] = [3, 1, 0]
+        img[c, 6:9] = [2, 2, 0]
+    check(W.Batch(m, np.array([[0.3, 0.2, 0.05, 0.4]]), img[None], np.array([0.0, 0.5, 2.0, 6.0]), 200, 17),
+          log_cap=256, lanes=lanes)
+
+    m = W.cwc_model(1, 2, 3, [W.RuleSpec(W.PAIR, 0, 1, lhs_child={0: 1}, rhs_child={0: 1}, rhs_child2={0: 3})])
+    img = W.empty_slot_image(m)
+    img[1, :4] = [1, 1, 0, 0]
+    img[1, 4] = 5
+    img[2, :3] = [1, 1, 0]
+    img[2, 4] = 2 ** 31 - 2
+    g, o = check(W.Batch(m, np.array([[1.0]]), img[None], np.array([0.0, 10.0]), 8, 5), lanes=lanes)
+    assert np.all(g["status"] == oracle.ST_INT_OVERFLOW)
