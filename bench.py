@@ -237,11 +237,26 @@ def measure_extras(dev):
             "issue_active_frac": None if cap is None else cap.get("issue_active_frac"),
             "warps_per_sm": None if cap is None else cap.get("warps_per_sm"),
             "source": "ncu capture of the profiling case on the same kernel sources (hash-checked); null if stale"}
+    # the same with 16-bit term counts (term_bits = 16): half the slab bytes
+    keep16 = {}
+
+    def run_cwc16():
+        keep16["o"] = api.simulate(cm, rates, init, grid, b.R, b.seed, states=True, out=keep16.get("o"), term_bits=16)
+        return keep16["o"]
+
+    out16, sec16 = _timed(run_cwc16, "cwc3x24_16bit")
+    same16 = bool(torch.equal(out16["hash"], out["hash"]) and torch.equal(out16["states"], out["states"]))
+    cap16 = capture_record("cwc_ssa_kernel16_cwc3x24", "cwc3x24", CWC_KERNEL_SOURCES)
     extras["cwc3x24"] = {"events_per_s": ev / sec, "events": ev, "seconds": sec, "layout": lay, "block_threads": thr,
                          "lanes_per_trajectory": lanes, "roofline": roof,
+                         "term_bits_16": {"events_per_s": ev / sec16, "seconds": sec16, "identical": same16,
+                                          "dram_bytes_per_event": None if cap16 is None
+                                          else cap16.get("dram_bytes_per_event"),
+                                          "issue_active_frac": None if cap16 is None
+                                          else cap16.get("issue_active_frac")},
                          "workload": "3 labels below the top, 24 species, 48 rules (transport, wrap binding, create, "
                                      "dissolve), <=64 compartments, 16384 replicas, 500-point grid"}
-    del out, keep
+    del out, keep, out16, keep16
     # uneven sweep: 256 rate vectors x 256 replicas of flat32x64's network, CUDA
     # graph; the autotuned queue / static layout, then the tail layout (the last
     # trajectories handed over to a warp each), which must agree bit for bit
@@ -375,6 +390,7 @@ def main():
     ap.add_argument("--layout", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory (compartment workload; 0 = automatic)")
+    ap.add_argument("--term-bits", type=int, default=0, help="compartment workload: 16 for 16-bit term counts")
     ap.add_argument("--replicas", type=int, default=0, help="smaller case for profiling (default: 65536)")
     ap.add_argument("--horizon-scale", type=float, default=1.0, help="scale the time grid (profiling only)")
     ap.add_argument("--grid-points", type=int, default=0, help="grid points (profiling only; default 1000)")
@@ -416,6 +432,7 @@ def main():
     def step(o):
         return api.simulate(cm, rates, init, grid, R, batch.seed, batch.max_events, states=True, traj=True,
                             layout=args.layout, block_threads=args.threads, lanes=args.lanes, replica_offset=r_off,
+                            term_bits=args.term_bits,
                             out=o)
 
     for _ in range(args.warmup):

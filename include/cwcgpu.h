@@ -312,6 +312,17 @@ typedef struct {
   size_t workspace_bytes;
   int32_t tail_threshold;    /* CWC_LAYOUT_TAIL: hand over when at most this many
                                 trajectories run (0 = 108 per SM) */
+  int32_t term_bits;         /* compartment models: 0 or 32 = 32-bit term counts;
+                                16 = 16-bit counts (half the term slab bytes, so
+                                a full GPU's terms stay in L2) for forward calls
+                                without FUSION / NESTED / PAIR rules, deadline or
+                                checkpoints: a trajectory whose count would leave
+                                int16's range is saved and finished by a 32-bit
+                                launch that redraws the same event, so results
+                                are identical; the workspace then also holds
+                                4 * P * R * (8 + C * (3 + 2S)) bytes of those
+                                hand-over records.  Ignored for flat models;
+                                other values are CWC_ERR_INVALID_ARG */
 } cwc_sim_args;
 
 /*
@@ -324,10 +335,11 @@ typedef struct {
  * The scratch it needs lives in one statically sized device array of
  * CWC_NOALLOC_SCRATCH_BYTES inside the library; every GPU that loads the
  * library holds that array until the process exits.  args->workspace and
- * args->workspace_bytes are ignored.  The scratch is exactly what
- * cwc_simulate_workspace_size reports for the same arguments, so a call fits
- * when that size is <= CWC_NOALLOC_SCRATCH_BYTES.  Its parts, each rounded up
- * to 256 bytes:
+ * args->workspace_bytes are ignored.  The scratch is what
+ * cwc_simulate_workspace_size reports for the same arguments, less the
+ * hand-over records of 16-bit terms (term_bits = 16): this entry point runs
+ * 32-bit terms throughout.  A call fits when that is <=
+ * CWC_NOALLOC_SCRATCH_BYTES.  Its parts, each rounded up to 256 bytes:
  *   - 256 bytes: work-queue ticket and deadline timestamp;
  *   - 8 * P * G * O: int64 replica sums, when means, variance or ci90 are
  *     requested without sums;

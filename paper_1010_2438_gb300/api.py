@@ -105,7 +105,7 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
              sumsq: bool = False, variance: bool = False, ci90: bool = False,
              traj: bool = True, log_cap: int = 0, layout: int = capi.CWC_LAYOUT_AUTO, block_threads: int = 0,
              lanes: int = 0, deadline_ns: int = 0, replica_offset: int = 0, checkpoint: bool = False,
-             resume: bool = False, tail_threshold: int = 0,
+             resume: bool = False, tail_threshold: int = 0, term_bits: int = 0,
              stream: Optional[torch.cuda.Stream] = None,
              out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
     """Run P x R trajectories (cwc_simulate) and return the requested outputs.
@@ -127,6 +127,7 @@ def simulate(cm: CompiledModel, rates: torch.Tensor, init: torch.Tensor, grid: t
 
     a = _sim_args(cm, rates, init, grid, R, seed, max_events, layout, block_threads, deadline_ns, replica_offset, lanes)
     a.tail_threshold = tail_threshold
+    a.term_bits = term_bits
     if states:
         a.states = _p(get("states", (P, R, G, O), torch.int32))
     if sums:

@@ -49,7 +49,8 @@ class cwc_sim_args(ctypes.Structure):
                 ("log_cap", _i32), ("log_rule", _vp), ("log_slot", _vp), ("log_t", _vp),
                 ("checkpoint", _vp), ("resume", _i32),
                 ("layout", _i32), ("block_threads", _i32), ("lanes", _i32), ("deadline_ns", _i64),
-                ("workspace", _vp), ("workspace_bytes", ctypes.c_size_t), ("tail_threshold", _i32)]
+                ("workspace", _vp), ("workspace_bytes", ctypes.c_size_t), ("tail_threshold", _i32),
+                ("term_bits", _i32)]
 
 
 class cwc_sens_args(ctypes.Structure):

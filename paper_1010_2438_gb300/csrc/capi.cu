@@ -115,6 +115,8 @@ struct WsLayout {
   bool need_header = false, need_sums = false, need_partials = false;
   int T = 0, blocks = 0, lanes = 1;   // compartmentalised launch shape (its slabs are per lane group)
   long long slab_words = 0;
+  bool narrow = false;            // compartment forward: a 16-bit launch, then a 32-bit one resuming
+  size_t narrow_ckpt = 0;         // the trajectories handed over: [Q][CKPT_HEADER_WORDS + C(3 + 2S)] int32
 };
 
 CwcParams cwc_shape_params(const cwc_model* m, const cwc_sim_args* a, bool sens) {
@@ -190,7 +192,10 @@ int cover_sms(int T, long long Q) {
   return T;
 }
 
-WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool sens_partials_given) {
+// allow_narrow: compartment forwards may run as a 16-bit launch followed by a
+// 32-bit one (which needs the hand-over records in the workspace)
+WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool sens_partials_given,
+                   bool allow_narrow = true) {
   WsLayout w;
   const int O = m->flat ? m->S : (m->L * m->S + (m->L - 1) * m->S + m->L);
   w.need_header = queue_layout(a) || a->deadline_ns > 0;
@@ -242,6 +247,21 @@ WsLayout ws_layout(const cwc_model* m, const cwc_sim_args* a, bool sens, bool se
     w.slab_words = prm.slab_words;
     w.slabs = off;
     off = align256(off + (size_t)w.blocks * (size_t)(w.T / w.lanes) * (size_t)prm.slab_words * sizeof(int32_t));
+    // Terms with 16-bit counts (term_bits = 16) halve the slab bytes a
+    // trajectory touches, so that the slabs of a full GPU's terms stay in L2
+    // (DRAM 238 -> 82 B per event on 16,384 terms of 24 species), but the
+    // 16-bit kernel ran 2 % slower there (more instruction-fetch stalls), so
+    // 32-bit terms stay the default.  A trajectory whose count would leave
+    // int16's range is handed to a 32-bit launch through a checkpoint
+    // record.  Forward calls without FUSION / NESTED / PAIR rules, deadline
+    // or caller checkpoints only (others run 32-bit terms).
+    w.narrow = allow_narrow && a->term_bits == 16 && !sens && !m->general && a->deadline_ns == 0 &&
+               a->checkpoint == nullptr && a->resume == 0;
+    if (w.narrow) {
+      w.narrow_ckpt = off;
+      const size_t words = (size_t)CKPT_HEADER_WORDS + (size_t)m->C * (3 + 2 * (size_t)m->S);
+      off = align256(off + (size_t)a->P * a->R * words * sizeof(int32_t));
+    }
   }
   w.total = off;
   return w;
@@ -265,6 +285,8 @@ cwc_status check_sim_args(const cwc_model* m, const cwc_sim_args* a) {
     return fail(CWC_ERR_INVALID_ARG,
                 "CWC_LAYOUT_TAIL is for flat mass-action models without deadline or checkpoints");
   if (a->tail_threshold < 0) return fail(CWC_ERR_INVALID_ARG, "tail_threshold must be >= 0");
+  if (a->term_bits != 0 && a->term_bits != 16 && a->term_bits != 32)
+    return fail(CWC_ERR_INVALID_ARG, "term_bits must be 0, 16 or 32");
   if (a->block_threads != 0 && (a->block_threads < 32 || a->block_threads > 256 || a->block_threads % 32 != 0))
     return fail(CWC_ERR_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 256]");
   if (a->lanes != 0 && !(m->flat ? a->lanes == 1 : cwc_lanes_supported(a->lanes)))
@@ -919,7 +941,8 @@ static cwc_status run_flat(const cwc_model* m, const cwc_sim_args* a, const cwc_
   return CWC_OK;
 }
 
-static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* sens, cudaStream_t st);
+static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* sens, cudaStream_t st,
+                          bool allow_narrow = true);
 
 // Scratch of cwc_simulate_noalloc: one statically sized array per device that
 // loads the library.  In host code its name is only a stand-in; the device
@@ -947,7 +970,7 @@ cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void*
   cwc_status st = check_sim_args(m, a);  // also checks that m's device is the current one
   if (st != CWC_OK) return st;
   const cwc_sim_args ra = resolve_auto(m, a);
-  const WsLayout w = ws_layout(m, &ra, false, false);
+  const WsLayout w = ws_layout(m, &ra, false, false, false);
   if (w.total > CWC_NOALLOC_SCRATCH_BYTES)
     return fail(CWC_ERR_INVALID_ARG, "this call needs " + std::to_string(w.total) +
                                          " bytes of scratch; cwc_simulate_noalloc holds " +
@@ -959,13 +982,14 @@ cwc_status cwc_simulate_noalloc(const cwc_model* m, const cwc_sim_args* a, void*
   cwc_sim_args b = ra;
   b.workspace = scratch;
   b.workspace_bytes = CWC_NOALLOC_SCRATCH_BYTES;
-  if (!m->flat) return run_cwc(m, &b, nullptr, static_cast<cudaStream_t>(stream));
+  if (!m->flat) return run_cwc(m, &b, nullptr, static_cast<cudaStream_t>(stream), false);
   return run_flat(m, &b, nullptr, static_cast<cudaStream_t>(stream));
 }
 
-static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* sens, cudaStream_t st) {
+static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_sens_args* sens, cudaStream_t st,
+                          bool allow_narrow) {
   const bool is_sens = sens != nullptr;
-  const WsLayout w = ws_layout(m, a, is_sens, is_sens && sens->partials != nullptr);
+  const WsLayout w = ws_layout(m, a, is_sens, is_sens && sens->partials != nullptr, allow_narrow);
   if (w.blocks < 1) return fail(CWC_ERR_CUDA, "could not size the compartmentalised launch");
   if (a->workspace == nullptr || a->workspace_bytes < w.total)
     return fail(CWC_ERR_WORKSPACE, "workspace of " + std::to_string(w.total) + " bytes required");
@@ -1027,6 +1051,22 @@ static cwc_status run_cwc(const cwc_model* m, const cwc_sim_args* a, const cwc_s
   }
   const LogConstants lc = make_log_constants();
   const bool queue = chosen_layout(a) == CWC_LAYOUT_QUEUE;
+  if (w.narrow) {
+    // 16-bit terms first; then the 32-bit launch resumes the trajectories it
+    // handed over (every other record carries its final status and is
+    // skipped), adding to the same sums
+    prm.narrow = 1;
+    prm.ckpt = reinterpret_cast<int32_t*>(ws + w.narrow_ckpt);
+    prm.resume = 0;
+    e = launch_cwc(prm, lc, queue, w.lanes, w.T, w.blocks, st);
+    if (e != cudaSuccess) return cuda_fail(e, "CWC SSA kernel launch (16-bit terms)");
+    if (w.need_header) {
+      e = cudaMemsetAsync(prm.ws, 0, sizeof(WorkspaceHeader), st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
+    }
+    prm.narrow = 0;
+    prm.resume = 1;
+  }
   e = launch_cwc(prm, lc, queue, w.lanes, w.T, w.blocks, st);
   if (e != cudaSuccess) return cuda_fail(e, "CWC SSA kernel launch");
   if (is_sens) {

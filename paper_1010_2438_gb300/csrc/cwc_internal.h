@@ -76,7 +76,10 @@ constexpr int CKPT_HEADER_WORDS = 8;
 // Trajectory status codes (same values as CWC_TRAJ_* in the C header).
 enum : int32_t {
   TS_OK = 0, TS_ABSORBED = 1, TS_INT_OVERFLOW = 2, TS_PROP_OVERFLOW = 3, TS_CAPACITY = 4,
-  TS_EVENT_LIMIT = 5, TS_BAD_INPUT = 6, TS_TIMEOUT = 7
+  TS_EVENT_LIMIT = 5, TS_BAD_INPUT = 6, TS_TIMEOUT = 7,
+  // internal, never an output: a count of a 16-bit term would leave int16's
+  // range; the trajectory is saved for the 32-bit launch that follows
+  TS_WIDEN = 100
 };
 
 // Workspace header (first 256 bytes when used): work-queue ticket, the
@@ -175,6 +178,9 @@ struct CwcParams {
   long long slab_words;
   int32_t* ckpt;                   // [Q][CKPT_HEADER_WORDS + C * (3 + 2S)] checkpoints (or null)
   int resume;                      // 1: continue the TIMEOUT trajectories of ckpt
+  int narrow;                      // 1: 16-bit term counts; a trajectory whose count would leave
+                                   // int16's range is saved in ckpt as TIMEOUT for the 32-bit
+                                   // resume launch that follows (every record's status is written)
   WorkspaceHeader* ws;
   long long deadline_ns;
   int smem_table_bytes;

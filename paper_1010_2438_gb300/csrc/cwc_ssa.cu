@@ -122,12 +122,27 @@ __host__ __device__ inline long long cwc_slab_words(int S, int L, int C, int M, 
   return (w + 31) / 32 * 32;
 }
 
+// Term counts are stored as CT: int32_t, or int16_t in the narrow launch,
+// whose trajectories leave for a 32-bit launch (TS_WIDEN, below) as soon as
+// a count would exceed 32767.
+template <class CT>
+__device__ __forceinline__ long long count_max() {
+  return sizeof(CT) == 2 ? 0x7FFFll : 0x7FFFFFFFll;
+}
+// the status of a count that would leave CT's range: a 16-bit term hands the
+// trajectory over to the 32-bit launch, a 32-bit one stops with INT_OVERFLOW
+template <class CT>
+__device__ __forceinline__ int count_overflow_status() {
+  return sizeof(CT) == 2 ? TS_WIDEN : TS_INT_OVERFLOW;
+}
+
 // Sum of the counts of rule `rec` over the contexts in m (the child slots of
 // a parent-child rule count only under a parent of the rule's context label);
 // bit 63 of the result flags an int64 overflow of a count or of the sum.
 // Out of line for lane groups (see below).
-__device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restrict__ content,
-                                                        const int32_t* __restrict__ wrap,
+template <class CT>
+__device__ __noinline__ unsigned long long cwc_count_sum(const CT* __restrict__ content,
+                                                        const CT* __restrict__ wrap,
                                                         const int32_t* __restrict__ meta, int S,
                                                         const int32_t* rec, unsigned long long m) {
   const int kind = rec[CR_KIND];
@@ -145,14 +160,14 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
       if ((meta[qq] & 0xff) != ctx) continue;
       x0c = qq;
     }
-    const int32_t* x0 = content + (size_t)x0c * S;
-    const int32_t* x1 = wrap + (size_t)c * S;
-    const int32_t* x2 = content + (size_t)c * S;
+    const CT* x0 = content + (size_t)x0c * S;
+    const CT* x1 = wrap + (size_t)c * S;
+    const CT* x2 = content + (size_t)c * S;
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
       const int row = (v >> 24) & 3;
-      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
+      const CT* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
       acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &of);
     }
     const unsigned long long s2 = tot + acc;
@@ -166,8 +181,9 @@ __device__ __noinline__ unsigned long long cwc_count_sum(const int32_t* __restri
 // must carry the child label and their grandparent the rule's label (the
 // root's label 0 is never a child label); rows 0 / 1-2 / 3-4 read the
 // grandparent's content, the parent's wrap and content, c's wrap and content.
-__device__ __noinline__ unsigned long long cwc_count_sum_nested(const int32_t* __restrict__ content,
-                                                               const int32_t* __restrict__ wrap,
+template <class CT>
+__device__ __noinline__ unsigned long long cwc_count_sum_nested(const CT* __restrict__ content,
+                                                               const CT* __restrict__ wrap,
                                                                const int32_t* __restrict__ meta, int S,
                                                                const int32_t* rec, unsigned long long m) {
   const int nr = rec[CR_NREAC];
@@ -181,7 +197,7 @@ __device__ __noinline__ unsigned long long cwc_count_sum_nested(const int32_t* _
     if ((meta[qq] & 0xff) != rec[CR_CHILD]) continue;
     const int aa = (meta[qq] >> 8) - 1;
     if ((meta[aa] & 0xff) != ctx) continue;
-    const int32_t* rows[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S, wrap + (size_t)c * S, content + (size_t)c * S};
+    const CT* rows[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S, wrap + (size_t)c * S, content + (size_t)c * S};
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
@@ -202,8 +218,9 @@ __device__ __noinline__ unsigned long long cwc_count_sum_nested(const int32_t* _
 // pair in ascending (d1, d2) order whose running sum exceeds xc, as
 // d1 | d2 << 16 (the last positive pair if none does); otherwise the sum,
 // bit 63 flagging an overflow of a product or of the sum.
-__device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __restrict__ content,
-                                                          const int32_t* __restrict__ wrap,
+template <class CT>
+__device__ __noinline__ unsigned long long cwc_fusion_scan(const CT* __restrict__ content,
+                                                          const CT* __restrict__ wrap,
                                                           const int32_t* __restrict__ meta, int S,
                                                           const int32_t* rec, unsigned long long kids,
                                                           bool want_pick, unsigned long long xc) {
@@ -235,7 +252,7 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
     m1 &= m1 - 1ull;
     const int qq = (meta[d1] >> 8) - 1;
     if ((meta[qq] & 0xff) != ctx) continue;
-    const int32_t* x0 = content + (size_t)qq * S;
+    const CT* x0 = content + (size_t)qq * S;
     unsigned long long m2 = kids & ~(1ull << d1);
     if (sym) m2 &= ~((2ull << d1) - 1ull);   // d2 > d1 only
     while (m2) {
@@ -246,7 +263,7 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
       for (int a = 0; a < nr; ++a) {
         const int v = rec[CR_REAC + a];
         const int row = (v >> 24) & 7;
-        const int32_t* x = row == 0 ? x0
+        const CT* x = row == 0 ? x0
                            : row == 1 ? wrap + (size_t)d1 * S
                            : row == 2 ? content + (size_t)d1 * S
                            : row == 3 ? wrap + (size_t)d2 * S : content + (size_t)d2 * S;
@@ -271,9 +288,10 @@ __device__ __noinline__ unsigned long long cwc_fusion_scan(const int32_t* __rest
 // (FUSION: the lower slot keeps the merged compartment, the higher is freed
 // and its children move to the survivor; PAIR: d1 takes the first
 // compartment pattern's changes, d2 the second's, both stay).
-__device__ __noinline__ int cwc_general_check(const int32_t* content, const int32_t* wrap, const int32_t* meta, int S,
+template <class CT>
+__device__ __noinline__ int cwc_general_check(const CT* content, const CT* wrap, const int32_t* meta, int S,
                                               int C, const int32_t* table, const int32_t* rec, int ctx) {
-  auto fits = [](long long v) { return v >= 0 && v <= 0x7FFFFFFFll; };
+  auto fits = [](long long v) { return v >= 0 && v <= count_max<CT>(); };
   const int nr = rec[CR_NREAC];
   if (rec[CR_KIND] == RK_NESTED || rec[CR_KIND] == RK_PAIR) {
     // five multisets rewritten in place: NESTED's grandparent content, child
@@ -283,14 +301,14 @@ __device__ __noinline__ int cwc_general_check(const int32_t* content, const int3
     const int g = pair ? (ctx >> 16) : ctx, qq = pair ? (ctx & 0xffff) : (meta[g] >> 8) - 1,
               aa = (meta[qq] >> 8) - 1;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
-    const int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
-                            wrap + (size_t)g * S, content + (size_t)g * S};
+    const CT* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
+                       wrap + (size_t)g * S, content + (size_t)g * S};
     const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
     const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
     for (int row = 0; row < 5; ++row)
       for (int d = 0; d < nd[row]; ++d) {
         const int v = dd[row][d];
-        if (!fits((long long)ms[row][v & 0xffff] + (v >> 16))) return TS_INT_OVERFLOW;
+        if (!fits((long long)ms[row][v & 0xffff] + (v >> 16))) return count_overflow_status<CT>();
       }
     return TS_OK;
   }
@@ -298,7 +316,7 @@ __device__ __noinline__ int cwc_general_check(const int32_t* content, const int3
   const int qq = (meta[d1] >> 8) - 1;
   for (int d = 0; d < rec[CR_ND0]; ++d) {
     const int v = rec[CR_D0 + d];
-    if (!fits((long long)content[(size_t)qq * S + (v & 0xffff)] + (v >> 16))) return TS_INT_OVERFLOW;
+    if (!fits((long long)content[(size_t)qq * S + (v & 0xffff)] + (v >> 16))) return count_overflow_status<CT>();
   }
   for (int x = 0; x < S; ++x) {
     long long wv = (long long)wrap[(size_t)d1 * S + x] + wrap[(size_t)d2 * S + x];
@@ -314,13 +332,14 @@ __device__ __noinline__ int cwc_general_check(const int32_t* content, const int3
       if ((rec[CR_D1 + d] & 0xffff) == x) wv += rec[CR_D1 + d] >> 16;
     for (int d = 0; d < rec[CR_ND2]; ++d)
       if ((rec[CR_D2 + d] & 0xffff) == x) cv += rec[CR_D2 + d] >> 16;
-    if (!fits(wv) || !fits(cv)) return TS_INT_OVERFLOW;
+    if (!fits(wv) || !fits(cv)) return count_overflow_status<CT>();
   }
   return TS_OK;
 }
 
 // O = L*S content totals, (L-1)*S wrap totals, L alive counts (see kernel)
-__device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, int32_t* meta,
+template <class CT>
+__device__ __noinline__ void cwc_general_apply(CT* content, CT* wrap, int32_t* meta,
                                                unsigned long long* chmask, unsigned long long* labmask,
                                                unsigned long long* alive_p, long long* tot, int S, int L, int C,
                                                const int32_t* table, const int32_t* rec, int ctx) {
@@ -334,8 +353,8 @@ __device__ __noinline__ void cwc_general_apply(int32_t* content, int32_t* wrap, 
               aa = (meta[qq] >> 8) - 1;
     const int la = meta[aa] & 0xff, lq = meta[qq] & 0xff, lg = meta[g] & 0xff;
     const int32_t* xr = table + (rec[CR_GRAND] >> 8);
-    int32_t* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
-                      wrap + (size_t)g * S, content + (size_t)g * S};
+    CT* ms[5] = {content + (size_t)aa * S, wrap + (size_t)qq * S, content + (size_t)qq * S,
+                 wrap + (size_t)g * S, content + (size_t)g * S};
     const int nd[5] = {rec[CR_ND0], rec[CR_ND1], rec[CR_ND2], xr[XR_ND3], xr[XR_ND4]};
     const int32_t* dd[5] = {rec + CR_D0, rec + CR_D1, rec + CR_D2, xr + XR_D3, xr + XR_D4};
     for (int row = 0; row < 5; ++row)
@@ -416,14 +435,16 @@ __device__ __noinline__ void cwc_record_rows(const long long* tot, int32_t* dst,
 
 // Whether the rewrite of rule `rec` at context c fits (TS_OK), else its
 // status; reads only (the in-line version is apply_check in the kernel).
-__device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_t* wrap, const int32_t* meta,
+template <class CT>
+__device__ __noinline__ int cwc_apply_check(const CT* content, const CT* wrap, const int32_t* meta,
                                             unsigned long long alive, int S, int C, const int32_t* rec, int c) {
   const unsigned long long* alive_p = &alive;
   auto PARENT = [&](int cc) -> int { return (meta[cc] >> 8) - 1; };
-  auto fits_add = [](int32_t v, int d) -> bool {
+  auto fits_add = [](int v, int d) -> bool {
     const long long s = (long long)v + d;
-    return s >= 0 && s <= 0x7FFFFFFFll;
+    return s >= 0 && s <= count_max<CT>();
   };
+  const int OVF = count_overflow_status<CT>();
     const int kind = rec[CR_KIND];
     const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
     if (kind == 0 || kind == 2) {
@@ -431,29 +452,29 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
         const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
         if (freeslots == 0ull) return TS_CAPACITY;
       }
-      const int32_t* x = content + (size_t)c * S;
+      const CT* x = content + (size_t)c * S;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(x[v & 0xffff], v >> 16)) return OVF;
       }
       return TS_OK;
     }
     const int qq = PARENT(c);
-    const int32_t* xp = content + (size_t)qq * S;
-    const int32_t* w = wrap + (size_t)c * S;
-    const int32_t* xc = content + (size_t)c * S;
+    const CT* xp = content + (size_t)qq * S;
+    const CT* w = wrap + (size_t)c * S;
+    const CT* xc = content + (size_t)c * S;
     if (kind == 1) {
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xp[v & 0xffff], v >> 16)) return OVF;
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(w[v & 0xffff], v >> 16)) return OVF;
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xc[v & 0xffff], v >> 16)) return OVF;
       }
       return TS_OK;
     }
@@ -470,14 +491,14 @@ __device__ __noinline__ int cwc_apply_check(const int32_t* content, const int32_
         if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
       const long long nv = (long long)xp[s] + dv;
-      if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
+      if (nv < 0 || nv > count_max<CT>()) return OVF;
     }
     return TS_OK;
 }
 
 // kGen: the model has FUSION or NESTED rules (a separate instantiation, so
 // that the code of those kinds costs the other models no registers)
-template <int kL, bool kQueue, bool kSens, bool kGen>
+template <int kL, bool kQueue, bool kSens, bool kGen, class CT>
 __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ CwcParams prm,
                                                       const __grid_constant__ LogConstants lc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -546,8 +567,8 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   double* part = tl + (kSens ? M : 0);                                            // [M]
   int32_t* Nf = reinterpret_cast<int32_t*>(part + (kSens ? M : 0));               // [M]
   int32_t* meta = Nf + (kSens ? M : 0);                                           // [C]
-  int32_t* wrap = meta + C;                                                       // [C][S]
-  int32_t* content = wrap + (size_t)C * S;                                        // [C][S]
+  CT* wrap = reinterpret_cast<CT*>(meta + C);                                                       // [C][S]
+  CT* content = wrap + (size_t)C * S;                                        // [C][S]
 
   auto LABEL = [&](int c) -> int { return meta[c] & 0xff; };
   auto PARENT = [&](int c) -> int { return (meta[c] >> 8) - 1; };
@@ -574,15 +595,15 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
   // (kinds LOCAL .. DISSOLVE; NESTED counts go through cwc_count_sum)
   auto count_at = [&](const int32_t* rec, int c) -> unsigned long long {
     const int kind = rec[CR_KIND];
-    const int32_t* x0 = content + (size_t)((kind == RK_LOCAL || kind == RK_CREATE) ? c : PARENT(c)) * S;
-    const int32_t* x1 = wrap + (size_t)c * S;
-    const int32_t* x2 = content + (size_t)c * S;
+    const CT* x0 = content + (size_t)((kind == RK_LOCAL || kind == RK_CREATE) ? c : PARENT(c)) * S;
+    const CT* x1 = wrap + (size_t)c * S;
+    const CT* x2 = content + (size_t)c * S;
     const int nr = rec[CR_NREAC];
     unsigned long long acc = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[CR_REAC + a];
       const int row = (v >> 24) & 3;
-      const int32_t* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
+      const CT* x = row == 0 ? x0 : (row == 1 ? x1 : x2);
       acc = mul_checked(acc, binom12(x[v & 0xffff], (v >> 16) & 0xff), &ovf);
     }
     return acc;
@@ -695,7 +716,11 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
 
   const int W = 3 + 2 * S;   // slot image row: alive, label, parent, wrap[S], content[S]
   auto finalize = [&]() {
-    if (prm.ckpt != nullptr) {
+    // (a 16-bit launch saves only the trajectories handed to the 32-bit one;
+    // every other record gets its status, which the 32-bit launch reads)
+    if (prm.ckpt != nullptr && sizeof(CT) == 2 && status != TS_TIMEOUT) {
+      if (gl == 0) prm.ckpt[(size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W) + 6] = status;
+    } else if (prm.ckpt != nullptr) {
       int32_t* rec = prm.ckpt + (size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W);
       if (gl == 0) {
         put_f64(rec, t);
@@ -736,7 +761,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
 
   // load and validate the initial term (slot image; on resume the saved one),
   // build masks, H and tree.  0 = running, 1 = ended at once (bad input),
-  // 2 = nothing to do (resuming, and this trajectory did not stop on the deadline)
+  // 2 = nothing to do (resuming, and this trajectory did not stop on the deadline),
+  // 3 = a count of the initial term does not fit a 16-bit term: the image is
+  // saved for the 32-bit launch as a trajectory that has not started
   auto start = [&]() -> int {
     p = (int)(q / prm.R);
     r = (int)(q - (long long)p * prm.R);
@@ -774,6 +801,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       img = rec + CKPT_HEADER_WORDS;
     }
     unsigned long long alive = 0ull;
+    bool wide = false;   // a count above count_max<CT>() (16-bit terms only)
     for (int c = gl; c < C; c += kL) {
       chmask[c] = 0ull;
       const int32_t* row = img + (size_t)c * W;
@@ -787,8 +815,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
           const int wv = row[3 + x], cv = row[3 + S + x];
           if (wv < 0 || cv < 0) bad = true;
           if (c == 0 && wv != 0) bad = true;
-          wrap[(size_t)c * S + x] = wv;
-          content[(size_t)c * S + x] = cv;
+          if (wv > count_max<CT>() || cv > count_max<CT>()) wide = true;
+          wrap[(size_t)c * S + x] = (CT)wv;
+          content[(size_t)c * S + x] = (CT)cv;
         }
         alive |= 1ull << c;
         meta[c] = (lab & 0xff) | ((par + 1) << 8);
@@ -829,6 +858,21 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       grp.sync();
       return 1;
     }
+    if (sizeof(CT) == 2 && grp.any(wide)) {
+      int32_t* rec = prm.ckpt + (size_t)q * (CKPT_HEADER_WORDS + (size_t)C * W);
+      if (gl == 0) {
+        put_f64(rec, 0.0);
+        put_u64(rec + 2, FNV_OFFSET);
+        rec[4] = 0;
+        rec[5] = 0;
+        rec[6] = TS_TIMEOUT;
+        rec[7] = 0;
+        *alive_p = 0ull;
+      }
+      for (long long e = gl; e < (long long)C * W; e += kL) rec[CKPT_HEADER_WORDS + e] = img[e];
+      grp.sync();
+      return 3;
+    }
     if (gl == 0) {
       *alive_p = alive;
       for (int l = 0; l < L; ++l) labmask[l] = 0ull;
@@ -859,13 +903,14 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     return 0;
   };
 
-  auto fits_add = [](int32_t v, int d) -> bool {
+  auto fits_add = [](int v, int d) -> bool {
     const long long s = (long long)v + d;
-    return s >= 0 && s <= 0x7FFFFFFFll;
+    return s >= 0 && s <= count_max<CT>();
   };
 
-  // whether the rewrite of rule j at context c fits (TS_OK), else its status;
-  // nothing is changed
+  // whether the rewrite of rule j at context c fits (TS_OK), else its status
+  // (a count leaving CT's range: INT_OVERFLOW, or TS_WIDEN for 16-bit
+  // terms); nothing is changed
   auto apply_check = [&](const int32_t* rec, int c) -> int {
     const int kind = rec[CR_KIND];
     const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
@@ -874,29 +919,29 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         const unsigned long long freeslots = ~*alive_p & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
         if (freeslots == 0ull) return TS_CAPACITY;
       }
-      const int32_t* x = content + (size_t)c * S;
+      const CT* x = content + (size_t)c * S;
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(x[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(x[v & 0xffff], v >> 16)) return count_overflow_status<CT>();
       }
       return TS_OK;
     }
     const int qq = PARENT(c);
-    const int32_t* xp = content + (size_t)qq * S;
-    const int32_t* w = wrap + (size_t)c * S;
-    const int32_t* xc = content + (size_t)c * S;
+    const CT* xp = content + (size_t)qq * S;
+    const CT* w = wrap + (size_t)c * S;
+    const CT* xc = content + (size_t)c * S;
     if (kind == 1) {
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
-        if (!fits_add(xp[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xp[v & 0xffff], v >> 16)) return count_overflow_status<CT>();
       }
       for (int d = 0; d < nd1; ++d) {
         const int v = rec[CR_D1 + d];
-        if (!fits_add(w[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(w[v & 0xffff], v >> 16)) return count_overflow_status<CT>();
       }
       for (int d = 0; d < nd2; ++d) {
         const int v = rec[CR_D2 + d];
-        if (!fits_add(xc[v & 0xffff], v >> 16)) return TS_INT_OVERFLOW;
+        if (!fits_add(xc[v & 0xffff], v >> 16)) return count_overflow_status<CT>();
       }
       return TS_OK;
     }
@@ -913,7 +958,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
         if (((v >> 24) & 7) != 0 && (v & 0xffff) == s) dv -= (v >> 16) & 0xff;
       }
       const long long nv = (long long)xp[s] + dv;
-      if (nv < 0 || nv > 0x7FFFFFFFll) return TS_INT_OVERFLOW;
+      if (nv < 0 || nv > count_max<CT>()) return count_overflow_status<CT>();
     }
     return TS_OK;
   };
@@ -923,7 +968,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     const int kind = rec[CR_KIND];
     const int nd0 = rec[CR_ND0], nd1 = rec[CR_ND1], nd2 = rec[CR_ND2];
     if (kind == 0) {
-      int32_t* x = content + (size_t)c * S;
+      CT* x = content + (size_t)c * S;
       const int l = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
@@ -934,9 +979,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     }
     if (kind == 1) {
       const int qq = PARENT(c);
-      int32_t* xp = content + (size_t)qq * S;
-      int32_t* w = wrap + (size_t)c * S;
-      int32_t* xc = content + (size_t)c * S;
+      CT* xp = content + (size_t)qq * S;
+      CT* w = wrap + (size_t)c * S;
+      CT* xc = content + (size_t)c * S;
       const int lq = LABEL(qq), lc = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
@@ -959,15 +1004,15 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const unsigned long long alive = *alive_p;
       const unsigned long long freeslots = ~alive & ~1ull & (C >= 64 ? ~0ull : ((1ull << C) - 1ull));
       const int e = __ffsll((long long)freeslots) - 1;
-      int32_t* x = content + (size_t)c * S;
+      CT* x = content + (size_t)c * S;
       const int lctx = LABEL(c);
       for (int d = 0; d < nd0; ++d) {
         const int v = rec[CR_D0 + d];
         x[v & 0xffff] += v >> 16;
         tot[OC(lctx, v & 0xffff)] += v >> 16;
       }
-      int32_t* we = wrap + (size_t)e * S;
-      int32_t* xe = content + (size_t)e * S;
+      CT* we = wrap + (size_t)e * S;
+      CT* xe = content + (size_t)e * S;
       for (int s = 0; s < S; ++s) {
         we[s] = 0;
         xe[s] = 0;
@@ -1001,9 +1046,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
     // to the parent, children are reparented, the slot is freed
     {
       const int qq = PARENT(c);
-      int32_t* xp = content + (size_t)qq * S;
-      int32_t* w = wrap + (size_t)c * S;
-      int32_t* xc = content + (size_t)c * S;
+      CT* xp = content + (size_t)qq * S;
+      CT* w = wrap + (size_t)c * S;
+      CT* xc = content + (size_t)c * S;
       // per-species change of the parent content: (rhs0 - lhs0) + (w - lhs1) + (xc - lhs2)
       auto delta_at = [&](int s) -> long long {
         long long dv = (long long)w[s] + xc[s];
@@ -1022,7 +1067,7 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
       const int lq = LABEL(qq), ld = LABEL(c);
       for (int s = 0; s < S; ++s) {
         const long long dv = delta_at(s);
-        xp[s] = (int32_t)((long long)xp[s] + dv);
+        xp[s] = (CT)((long long)xp[s] + dv);
         tot[OC(lq, s)] += dv;
         tot[OC(ld, s)] -= xc[s];
         tot[OW(ld, s)] -= w[s];
@@ -1210,6 +1255,13 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
                     : kL > 1  ? cwc_apply_check(content, wrap, meta, *alive_p, S, C, rec, ctx)
                               : apply_check(rec, ctx);
     if (ast != TS_OK) {
+      if (ast == TS_WIDEN) {
+        // a 16-bit count would leave its range: the event is not applied
+        // here; the trajectory is saved as it stands (grid points recorded so
+        // far included) and the 32-bit launch redraws this same event
+        status = TS_TIMEOUT;
+        return 2;
+      }
       status = ast;
       return 1;
     }
@@ -1337,9 +1389,9 @@ __global__ void __launch_bounds__(256) cwc_ssa_kernel(const __grid_constant__ Cw
 
 // ---------------------------------------------------------------------------
 
-template <int kL, bool kQueue, bool kSens, bool kGen>
+template <int kL, bool kQueue, bool kSens, bool kGen, class CT>
 static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, size_t* smem_out) {
-  auto kern = cwc_ssa_kernel<kL, kQueue, kSens, kGen>;
+  auto kern = cwc_ssa_kernel<kL, kQueue, kSens, kGen, CT>;
   const size_t smem = (size_t)prm.smem_table_bytes + (size_t)(T / kL) * cwc_thread_bytes(prm.M);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1359,14 +1411,21 @@ static cudaError_t cwc_config_t(const CwcParams& prm, int T, int* blocks_out, si
   return cudaSuccess;
 }
 
+// 16-bit terms (prm.narrow) exist for the forward of models without
+// FUSION / NESTED / PAIR rules only
 template <int kL, bool kGen>
 static cudaError_t cwc_config_g(const CwcParams& prm, bool queue, int T, int* blocks, size_t* smem) {
   const bool sens = prm.sens != 0;
+  if constexpr (!kGen) {
+    if (prm.narrow && !sens)
+      return queue ? cwc_config_t<kL, true, false, false, int16_t>(prm, T, blocks, smem)
+                   : cwc_config_t<kL, false, false, false, int16_t>(prm, T, blocks, smem);
+  }
   if (queue)
-    return sens ? cwc_config_t<kL, true, true, kGen>(prm, T, blocks, smem)
-                : cwc_config_t<kL, true, false, kGen>(prm, T, blocks, smem);
-  return sens ? cwc_config_t<kL, false, true, kGen>(prm, T, blocks, smem)
-              : cwc_config_t<kL, false, false, kGen>(prm, T, blocks, smem);
+    return sens ? cwc_config_t<kL, true, true, kGen, int32_t>(prm, T, blocks, smem)
+                : cwc_config_t<kL, true, false, kGen, int32_t>(prm, T, blocks, smem);
+  return sens ? cwc_config_t<kL, false, true, kGen, int32_t>(prm, T, blocks, smem)
+              : cwc_config_t<kL, false, false, kGen, int32_t>(prm, T, blocks, smem);
 }
 
 template <int kL>
@@ -1423,16 +1482,25 @@ template <int kL, bool kGen>
 static void cwc_launch_g(const CwcParams& prm, const LogConstants& lc, bool queue, int T, int blocks, size_t smem,
                          cudaStream_t stream) {
   const bool sens = prm.sens != 0;
+  if constexpr (!kGen) {
+    if (prm.narrow && !sens) {
+      if (queue)
+        cwc_ssa_kernel<kL, true, false, false, int16_t><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      else
+        cwc_ssa_kernel<kL, false, false, false, int16_t><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      return;
+    }
+  }
   if (queue) {
     if (sens)
-      cwc_ssa_kernel<kL, true, true, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, true, true, kGen, int32_t><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
     else
-      cwc_ssa_kernel<kL, true, false, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, true, false, kGen, int32_t><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
   } else {
     if (sens)
-      cwc_ssa_kernel<kL, false, true, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, false, true, kGen, int32_t><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
     else
-      cwc_ssa_kernel<kL, false, false, kGen><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
+      cwc_ssa_kernel<kL, false, false, kGen, int32_t><<<(unsigned)blocks, T, smem, stream>>>(prm, lc);
   }
 }
 
