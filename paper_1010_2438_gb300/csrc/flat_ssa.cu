@@ -11,7 +11,9 @@
 //                        l is a_l itself (l >= M: +0); with B > 1 it is the
 //                        block sum and the a_j are recomputed from the counts
 //                        when needed instead of being stored
-//   node[16][T]  double  level-1 tree nodes (children: leaves 2n, 2n+1)
+//   node[16][T]  double  level-1 tree nodes (children: leaves 2n, 2n+1); not
+//                        kept by the Michaelis-Menten kernel, which sums them
+//                        from the leaves where they are read
 //   cnt[S][T]    int32   species counts
 // and, in registers, the 15 upper nodes (levels 2-5, root = a0), which the
 // descent selects among without a shared-memory round trip.  For the score
@@ -64,8 +66,9 @@ __host__ __device__ inline int flat_table_bytes(int M, int n_deps) {
   return 0;
 }
 
-__host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens) {
-  int doubles = 32 + 16 + (sens ? M : 0);
+// (mm: the Michaelis-Menten kernel keeps no level-1 nodes, see the kernel)
+__host__ __device__ inline int flat_thread_bytes(int S, int M, bool sens, bool mm) {
+  int doubles = 32 + (mm ? 0 : 16) + (sens ? M : 0);
   int ints = S;
   return doubles * 8 + ints * 4;
 }
@@ -96,10 +99,18 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // Per-thread arrays [index][T]: each pointer below already points at this
   // thread's column, so element i of the array is ptr[i * T].
   double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
-  const int n_dbl_rows = 32 + 16 + (kSens ? M : 0);
+  // The Michaelis-Menten kernel stores no level-1 nodes: it sums them from
+  // their two leaves where they are read (the descent, the register nodes),
+  // which costs FP64 additions but 128 bytes of shared memory per
+  // trajectory, so that 16 instead of 14 warps fit an SM; its leaves, with
+  // their divisions, are dear enough that the residency wins (+13 % events/s
+  // on the 40-rule cascade, against -7 % on the 64-rule mass-action network)
+  constexpr bool kNodes = !kMM;
+  constexpr int kNodeRows = kNodes ? 16 : 0;
+  const int n_dbl_rows = 32 + kNodeRows + (kSens ? M : 0);
   double* leaf = dbase + tid;                                   // [32][T]
-  double* node = dbase + 32 * T + tid;                          // [16][T] level-1 nodes
-  double* Hd = dbase + (32 + 16) * T + tid;                     // score replay only: [M][T]
+  double* node = dbase + 32 * T + tid;                          // [16][T] level-1 nodes (kNodes)
+  double* Hd = dbase + (32 + kNodeRows) * T + tid;              // score replay only: [M][T]
   // score replay, per trajectory in global memory (set by start()):
   // V_i = N_i / k_i - I_i(t_i) + H_i t_i (t_i: the last change of rule i's
   // count or firings), so that the score at grid time t_g is S_i(g) =
@@ -114,7 +125,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   int32_t* cnt = ibase + tid;                                   // [S][T]
 
 #define LEAF(l) leaf[(l) * T]
-#define NODE(i) node[(i) * T]
+#define NODE(i) (kNodes ? node[(i) * T] : __dadd_rn(LEAF(2 * (i)), LEAF(2 * (i) + 1)))
 #define CNT(s) cnt[(s) * T]
 
   const unsigned long long* __restrict__ g_rj =
@@ -294,7 +305,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // step ends it with PROP_OVERFLOW as the overflow flag would
   auto leaf_sum_at = [&](int l, int c, const double* kc) -> double {
     const int32_t* cc = ibase + c;
-    const double* hc = dbase + (32 + 16) * T + c;
+    const double* hc = dbase + (32 + kNodeRows) * T + c;
     bool of = false;
     const int j0 = l * B, j1 = min(j0 + B, M);
     double s = j0 < M ? __dmul_rn(kc[j0], kSens ? hc[j0 * T] : h_of_at(j0, cc, &of)) : 0.0;
@@ -378,7 +389,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       }
     }
     for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
-    for (int nd = 0; nd < 16; ++nd) NODE(nd) = __dadd_rn(LEAF(2 * nd), LEAF(2 * nd + 1));
+    if (kNodes)
+      for (int nd = 0; nd < 16; ++nd) node[nd * T] = __dadd_rn(LEAF(2 * nd), LEAF(2 * nd + 1));
     rebuild_upper();
     return 0;
   };
@@ -559,11 +571,11 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
         }
       }
     }
-    unsigned nm = (unsigned)rec[R_NODEMASK] & 0xFFFFu;   // level-1 nodes above the dirty leaves
+    unsigned nm = kNodes ? (unsigned)rec[R_NODEMASK] & 0xFFFFu : 0u;   // level-1 nodes above the dirty leaves
     while (nm) {
       const int kk = __ffs(nm) - 1;
       nm &= nm - 1u;
-      NODE(kk) = __dadd_rn(LEAF(2 * kk), LEAF(2 * kk + 1));
+      node[kk * T] = __dadd_rn(LEAF(2 * kk), LEAF(2 * kk + 1));
     }
     rebuild_upper();
     if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
@@ -772,7 +784,7 @@ template <bool kQueue, bool kSens, bool kTail, bool kMM, bool kPool>
 static cudaError_t launch_k(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
                             cudaStream_t stream, int* used_blocks) {
   auto kern = flat_ssa_kernel<kQueue, kSens, kTail, kMM, kPool>;
-  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
+  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens, kMM);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   long long blocks;
@@ -805,7 +817,7 @@ static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T
 }
 
 size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens) {
-  return (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, sens);
+  return (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, sens, prm.mm_K != nullptr);
 }
 
 int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps); }
@@ -827,7 +839,7 @@ static int auto_threads_t(const FlatParams& prm) {
   int per_sm[9] = {0};                  // per_sm[T / 32], T = 32..256
   int best_T = 32, best_warps = -1;
   for (int T = 32; T <= 256; T += 32) {
-    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens);
+    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens, kMM);
     if (smem > 227 * 1024) break;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[T / 32], kern, T, smem) != cudaSuccess) break;
