@@ -553,29 +553,54 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // the rest of an applied event: the lane rebuilds its dirty leaves (with
   // B = 1 they are the dependents' propensities), unless the warp has
   // already rebuilt them together (kPool)
+  // The level-1 node above a dirty leaf is written by whoever rebuilds the
+  // last dirty leaf of its pair (the dirty leaves are rebuilt in ascending
+  // order, so the pair's other value, when dirty too, was the one just
+  // before it), in the same pass as the leaves: no second, max-over-lanes
+  // loop over the dirty nodes.  Returns whether leaf l's node is written
+  // here; mate_dirty says whether the node's other leaf was rebuilt too.
+  auto pair_last = [](int l, unsigned lmask, bool* mate_dirty) -> bool {
+    *mate_dirty = (lmask >> (l ^ 1)) & 1u;
+    return (l & 1) || !*mate_dirty;
+  };
   auto finish_event = [&]() {
     const int32_t* rec = g_rules + pend_j * RULE_WORDS;
     if (!kPool) {
+      const unsigned lmask = (unsigned)rec[R_LEAFMASK];
+      double prev = 0.0;   // the previous dirty leaf's new value
+      auto leaf_done = [&](int ll, double v) {
+        LEAF(ll) = v;
+        if (kNodes) {
+          bool md;
+          if (pair_last(ll, lmask, &md)) node[(ll >> 1) * T] = __dadd_rn(v, md ? prev : LEAF(ll ^ 1));
+          prev = v;
+        }
+      };
       if (B == 1) {
+        // (the dependents are listed in ascending order: leaf i is rule i)
         const int doff = rec[R_DEPOFF], dcnt = rec[R_DEPCNT];
         for (int e = 0; e < dcnt; ++e) {
           const int i = g_deps[doff + e];
-          LEAF(i) = prop_of(i);
+          leaf_done(i, prop_of(i));
         }
       } else {
-        unsigned lm = (unsigned)rec[R_LEAFMASK];
+        unsigned lm = lmask;
         while (lm) {
           const int ll = __ffs(lm) - 1;
           lm &= lm - 1u;
-          LEAF(ll) = leaf_sum(ll);
+          leaf_done(ll, leaf_sum(ll));
         }
       }
-    }
-    unsigned nm = kNodes ? (unsigned)rec[R_NODEMASK] & 0xFFFFu : 0u;   // level-1 nodes above the dirty leaves
-    while (nm) {
-      const int kk = __ffs(nm) - 1;
-      nm &= nm - 1u;
-      node[kk * T] = __dadd_rn(LEAF(2 * kk), LEAF(2 * kk + 1));
+    } else {
+      // the warp has rebuilt the leaves; the level-1 nodes above them follow
+      // per lane (writing them in the pooled rounds instead, by the pair's
+      // last dirty leaf, measured 0.6 % slower on the 64-rule network)
+      unsigned nm = kNodes ? (unsigned)rec[R_NODEMASK] & 0xFFFFu : 0u;
+      while (nm) {
+        const int kk = __ffs(nm) - 1;
+        nm &= nm - 1u;
+        node[kk * T] = __dadd_rn(LEAF(2 * kk), LEAF(2 * kk + 1));
+      }
     }
     rebuild_upper();
     if (prm.log_cap > 0 && n < (unsigned)prm.log_cap) {
