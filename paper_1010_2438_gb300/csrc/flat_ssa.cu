@@ -4,20 +4,20 @@
 //
 // Layout.  The compiled rule tables stay in global memory, read through L1
 // (a few KB shared by every block, always resident there).  Shared memory
-// holds only per-thread arrays stored [index][thread], so that every thread
-// reading "its" element i touches bank (2*tid) mod 32 whatever i is: data-
-// dependent indices never conflict.
-//   leaf[32][T]  double  leaves of the 32-lane blocked tree.  With B = 1 leaf
+// holds only per-thread arrays stored [index][thread] with rows of T + 1
+// elements, so that a warp's lanes reading their own elements, or several
+// lanes reading rows of one column (the pooled leaf rounds), spread over banks.
+//   leaf[32][Ts] double  leaves of the 32-lane blocked tree.  With B = 1 leaf
 //                        l is a_l itself (l >= M: +0); with B > 1 it is the
 //                        block sum and the a_j are recomputed from the counts
 //                        when needed instead of being stored
-//   node[16][T]  double  level-1 tree nodes (children: leaves 2n, 2n+1); not
+//   node[16][Ts] double  level-1 tree nodes (children: leaves 2n, 2n+1); not
 //                        kept by the Michaelis-Menten kernel, which sums them
 //                        from the leaves where they are read
-//   cnt[S][T]    int32   species counts
+//   cnt[S][Ts]   int32   species counts
 // and, in registers, the 15 upper nodes (levels 2-5, root = a0), which the
 // descent selects among without a shared-memory round trip.  For the score
-// replay H_i as doubles [M][T] joins shared memory.  The replay's integrals,
+// replay H_i as doubles [M][Ts] joins shared memory.  The replay's integrals,
 // their times, the firing counts and the partials, touched a few at a time
 // per event, live in global memory per trajectory, so that the replay keeps
 // almost the forward pass's residency.
@@ -96,8 +96,14 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   const int32_t* __restrict__ g_deps = g_rules + M * RULE_WORDS;
   const uint32_t* __restrict__ g_desc = reinterpret_cast<const uint32_t*>(g_deps + prm.n_deps);
   const int tbl_words = M * RULE_WORDS + prm.n_deps + M;
-  // Per-thread arrays [index][T]: each pointer below already points at this
-  // thread's column, so element i of the array is ptr[i * T].
+  // Per-thread arrays [index][T + 1]: each pointer below already points at
+  // this thread's column, so element i of the array is ptr[i * Ts].  The
+  // padded row (Ts = T + 1 elements; T is a multiple of 32) keeps a warp's
+  // own-column accesses conflict-free and puts the rows of one column in
+  // different banks, which the pooled leaf rounds need: there several lanes
+  // read and write one owner's counts and leaves at once (with a row of T
+  // elements they all hit the owner's bank).
+  const int Ts = T + 1;
   double* dbase = reinterpret_cast<double*>(smem + prm.smem_table_bytes);
   // The Michaelis-Menten kernel stores no level-1 nodes: it sums them from
   // their two leaves where they are read (the descent, the register nodes),
@@ -108,9 +114,9 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   constexpr bool kNodes = !kMM;
   constexpr int kNodeRows = kNodes ? 16 : 0;
   const int n_dbl_rows = 32 + kNodeRows + (kSens ? M : 0);
-  double* leaf = dbase + tid;                                   // [32][T]
-  double* node = dbase + 32 * T + tid;                          // [16][T] level-1 nodes (kNodes)
-  double* Hd = dbase + (32 + kNodeRows) * T + tid;              // score replay only: [M][T]
+  double* leaf = dbase + tid;                                   // [32][Ts]
+  double* node = dbase + 32 * Ts + tid;                         // [16][Ts] level-1 nodes (kNodes)
+  double* Hd = dbase + (32 + kNodeRows) * Ts + tid;             // score replay only: [M][Ts]
   // score replay, per trajectory in global memory (set by start()):
   // V_i = N_i / k_i - I_i(t_i) + H_i t_i (t_i: the last change of rule i's
   // count or firings), so that the score at grid time t_g is S_i(g) =
@@ -121,12 +127,12 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   double* Nf = nullptr;     // [M] firings of rules whose 1 / k_i overflows
   double* part = nullptr;   // [M] the trajectory's partials
   const double* ik = nullptr;   // [M] 1 / k_i of this sweep point
-  int32_t* ibase = reinterpret_cast<int32_t*>(dbase + (size_t)n_dbl_rows * T);
-  int32_t* cnt = ibase + tid;                                   // [S][T]
+  int32_t* ibase = reinterpret_cast<int32_t*>(dbase + (size_t)n_dbl_rows * Ts);
+  int32_t* cnt = ibase + tid;                                   // [S][Ts]
 
-#define LEAF(l) leaf[(l) * T]
-#define NODE(i) (kNodes ? node[(i) * T] : __dadd_rn(LEAF(2 * (i)), LEAF(2 * (i) + 1)))
-#define CNT(s) cnt[(s) * T]
+#define LEAF(l) leaf[(l) * Ts]
+#define NODE(i) (kNodes ? node[(i) * Ts] : __dadd_rn(LEAF(2 * (i)), LEAF(2 * (i) + 1)))
+#define CNT(s) cnt[(s) * Ts]
 
   const unsigned long long* __restrict__ g_rj =
       reinterpret_cast<const unsigned long long*>(g_rules + ((tbl_words + 3) & ~3));
@@ -233,11 +239,11 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       for (; i + 1 < M; i += 2) {
         const double v0 = Vv[i], v1 = Vv[i + 1], k0 = ik[i], k1 = ik[i + 1];
         const double p0 = part[i], p1 = part[i + 1];
-        const double h0 = Hd[i * T], h1 = Hd[(i + 1) * T];
+        const double h0 = Hd[i * Ts], h1 = Hd[(i + 1) * Ts];
         part[i] = __dadd_rn(p0, term(v0, h0, k0, i));
         part[i + 1] = __dadd_rn(p1, term(v1, h1, k1, i + 1));
       }
-      if (i < M) part[i] = __dadd_rn(part[i], term(Vv[i], Hd[i * T], ik[i], i));
+      if (i < M) part[i] = __dadd_rn(part[i], term(Vv[i], Hd[i * Ts], ik[i], i));
     }
   };
 
@@ -254,8 +260,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       // one descriptor load, both count loads in flight together, no branches
       const uint32_t d = g_desc[i];
       const uint32_t kind = d & 3u;
-      const unsigned n0 = (unsigned)cc[((d >> 2) & 0x3fffu) * T];
-      const unsigned n1 = (unsigned)cc[((d >> 16) & 0x3fffu) * T];
+      const unsigned n0 = (unsigned)cc[((d >> 2) & 0x3fffu) * Ts];
+      const unsigned n1 = (unsigned)cc[((d >> 16) & 0x3fffu) * Ts];
       const unsigned m = kind == 3u ? n1 : (kind == 2u ? n0 - 1u : 1u);
       const unsigned long long prod = (unsigned long long)(kind == 0u ? 1u : n0) * m;
       return kind == 2u ? prod >> 1 : prod;
@@ -265,7 +271,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     unsigned long long hh = 1ull;
     for (int a = 0; a < nr; ++a) {
       const int v = rec[R_REAC + a];
-      hh = mul_checked(hh, binom12(cc[(v & 0xffff) * T], v >> 16), of);
+      hh = mul_checked(hh, binom12(cc[(v & 0xffff) * Ts], v >> 16), of);
     }
     return hh;
   };
@@ -277,9 +283,9 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       const double Km = prm.mm_K[i];
       if (dbits(Km) != 0) {
         const uint32_t md = prm.mm_desc[i];
-        const double ns = (double)cc[(md & 0xffffu) * T];
+        const double ns = (double)cc[(md & 0xffffu) * Ts];
         const uint32_t e1 = md >> 16;
-        const double num = e1 != 0u ? __dmul_rn(ns, (double)cc[(e1 - 1u) * T]) : ns;
+        const double num = e1 != 0u ? __dmul_rn(ns, (double)cc[(e1 - 1u) * Ts]) : ns;
         return __ddiv_rn(num, __dadd_rn(Km, ns));
       }
     }
@@ -289,7 +295,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // a_i = k_i h_i; the score replay keeps h_i as doubles in shared memory
   // (updated for every rule whose value changes), so it reads them there
   auto prop_of = [&](int i) -> double {
-    return __dmul_rn(kp[i], kSens ? Hd[i * T] : h_of(i));
+    return __dmul_rn(kp[i], kSens ? Hd[i * Ts] : h_of(i));
   };
 
   // leaf l as the blocked sum of its rules (B > 1)
@@ -305,11 +311,11 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // step ends it with PROP_OVERFLOW as the overflow flag would
   auto leaf_sum_at = [&](int l, int c, const double* kc) -> double {
     const int32_t* cc = ibase + c;
-    const double* hc = dbase + (32 + kNodeRows) * T + c;
+    const double* hc = dbase + (32 + kNodeRows) * Ts + c;
     bool of = false;
     const int j0 = l * B, j1 = min(j0 + B, M);
-    double s = j0 < M ? __dmul_rn(kc[j0], kSens ? hc[j0 * T] : h_of_at(j0, cc, &of)) : 0.0;
-    for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, __dmul_rn(kc[jj], kSens ? hc[jj * T] : h_of_at(jj, cc, &of)));
+    double s = j0 < M ? __dmul_rn(kc[j0], kSens ? hc[j0 * Ts] : h_of_at(j0, cc, &of)) : 0.0;
+    for (int jj = j0 + 1; jj < j1; ++jj) s = __dadd_rn(s, __dmul_rn(kc[jj], kSens ? hc[jj * Ts] : h_of_at(jj, cc, &of)));
     return of ? __longlong_as_double(0x7FF0000000000000ll) : s;
   };
 
@@ -383,14 +389,14 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
     }
     if (kSens) {
       for (int i = 0; i < M; ++i) {
-        Hd[i * T] = h_of(i);
+        Hd[i * Ts] = h_of(i);
         Vv[i] = 0.0;
         Nf[i] = 0.0;
       }
     }
     for (int l = 0; l < 32; ++l) LEAF(l) = B == 1 ? (l < M ? prop_of(l) : 0.0) : leaf_sum(l);
     if (kNodes)
-      for (int nd = 0; nd < 16; ++nd) node[nd * T] = __dadd_rn(LEAF(2 * nd), LEAF(2 * nd + 1));
+      for (int nd = 0; nd < 16; ++nd) node[nd * Ts] = __dadd_rn(LEAF(2 * nd), LEAF(2 * nd + 1));
     rebuild_upper();
     return 0;
   };
@@ -400,8 +406,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
   // after it; the lazily kept integrals are first brought up to t
   auto freeze_h = [&]() {
     for (int i = 0; i < M; ++i) {
-      Vv[i] = __dadd_rn(Vv[i], __dmul_rn(-Hd[i * T], t));   // H_i drops to 0 at t
-      Hd[i * T] = 0.0;
+      Vv[i] = __dadd_rn(Vv[i], __dmul_rn(-Hd[i * Ts], t));   // H_i drops to 0 at t
+      Hd[i * Ts] = 0.0;
     }
   };
 
@@ -494,7 +500,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
         // (the score replay has h as a double already).  A count H >= 1 gives
         // a_j >= k_j > 0; a Michaelis-Menten h < 1 can give k_j h = 0, so
         // kMM tests a_j itself
-        const double hdd = kSens ? Hd[jj * T] : h_of(jj);
+        const double hdd = kSens ? Hd[jj * Ts] : h_of(jj);
         if (kMM || dbits(hdd) != 0) {
           const double a = __dmul_rn(kp[jj], hdd);
           if (!kMM || dbits(a) != 0) {
@@ -538,8 +544,8 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       for (int e = 0; e < dcnt; ++e) {
         const int i = g_deps[doff + e];
         const double hd = h_of(i);
-        Vv[i] = __dadd_rn(Vv[i], __dmul_rn(__dadd_rn(hd, -Hd[i * T]), tn));
-        Hd[i * T] = hd;
+        Vv[i] = __dadd_rn(Vv[i], __dmul_rn(__dadd_rn(hd, -Hd[i * Ts]), tn));
+        Hd[i * Ts] = hd;
       }
     }
     // the leaves, nodes and the rest of the event follow in finish_event(),
@@ -572,7 +578,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
         LEAF(ll) = v;
         if (kNodes) {
           bool md;
-          if (pair_last(ll, lmask, &md)) node[(ll >> 1) * T] = __dadd_rn(v, md ? prev : LEAF(ll ^ 1));
+          if (pair_last(ll, lmask, &md)) node[(ll >> 1) * Ts] = __dadd_rn(v, md ? prev : LEAF(ll ^ 1));
           prev = v;
         }
       };
@@ -599,7 +605,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
       while (nm) {
         const int kk = __ffs(nm) - 1;
         nm &= nm - 1u;
-        node[kk * T] = __dadd_rn(LEAF(2 * kk), LEAF(2 * kk + 1));
+        node[kk * Ts] = __dadd_rn(LEAF(2 * kk), LEAF(2 * kk + 1));
       }
     }
     rebuild_upper();
@@ -662,7 +668,7 @@ __global__ void __maxnreg__(168) flat_ssa_kernel(const __grid_constant__ FlatPar
         c = __popc(m & 0x3u);    if (k >= c) { k -= c; m >>= 2;  pos += 2; }
         if (k >= (int)(m & 1u)) pos += 1;
         const int col = tid - lane + o;
-        dbase[pos * T + col] = leaf_sum_at(pos, col, prm.rates + (size_t)p_o * M);
+        dbase[pos * Ts + col] = leaf_sum_at(pos, col, prm.rates + (size_t)p_o * M);
       }
     }
     __syncwarp();
@@ -809,7 +815,7 @@ template <bool kQueue, bool kSens, bool kTail, bool kMM, bool kPool>
 static cudaError_t launch_k(const FlatParams& prm, const LogConstants& lc, int T, int blocks_per_sm_cap,
                             cudaStream_t stream, int* used_blocks) {
   auto kern = flat_ssa_kernel<kQueue, kSens, kTail, kMM, kPool>;
-  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens, kMM);
+  const size_t smem = (size_t)prm.smem_table_bytes + (size_t)(T + 1) * flat_thread_bytes(prm.S, prm.M, kSens, kMM);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   long long blocks;
@@ -842,7 +848,7 @@ static cudaError_t launch_t(const FlatParams& prm, const LogConstants& lc, int T
 }
 
 size_t flat_smem_bytes(const FlatParams& prm, int T, bool sens) {
-  return (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, sens, prm.mm_K != nullptr);
+  return (size_t)prm.smem_table_bytes + (size_t)(T + 1) * flat_thread_bytes(prm.S, prm.M, sens, prm.mm_K != nullptr);
 }
 
 int flat_table_bytes_host(int M, int n_deps) { return flat_table_bytes(M, n_deps); }
@@ -864,7 +870,7 @@ static int auto_threads_t(const FlatParams& prm) {
   int per_sm[9] = {0};                  // per_sm[T / 32], T = 32..256
   int best_T = 32, best_warps = -1;
   for (int T = 32; T <= 256; T += 32) {
-    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)T * flat_thread_bytes(prm.S, prm.M, kSens, kMM);
+    const size_t smem = (size_t)prm.smem_table_bytes + (size_t)(T + 1) * flat_thread_bytes(prm.S, prm.M, kSens, kMM);
     if (smem > 227 * 1024) break;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) break;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[T / 32], kern, T, smem) != cudaSuccess) break;
