@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "flat32x64"
 WORKLOAD_DESC = ("flat mass-action network, 32 species, 64 reactions (8 inflow/outflow pairs, 32 conversions, "
                  "16 bimolecular), 65536 replicas x ~1e5 events, 1000-point grid, int32 states, FP64 propensities/time")
+SWEEP_DESC = ("flat32x64's network under 256 rate vectors (two decades of scale, trajectory lengths ~65x apart) "
+              "x 256 replicas, 1000-point grid, tail layout (the last trajectories handed to 16-lane groups)")
 CWC_DESC = ("compartmentalised CWC, 3 labels below the top, 24 species, 48 rules (transport, wrap binding, create, "
             "dissolve), <=64 compartments per term, 16384 replicas x ~1e4 events, 500-point grid, 172 observables")
 METRIC = "SSA events/sec"
@@ -394,8 +396,9 @@ def main():
     ap.add_argument("--replicas", type=int, default=0, help="smaller case for profiling (default: 65536)")
     ap.add_argument("--horizon-scale", type=float, default=1.0, help="scale the time grid (profiling only)")
     ap.add_argument("--grid-points", type=int, default=0, help="grid points (profiling only; default 1000)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "cwc3x24"],
-                    help="profiling only: run the compartment workload as the timed step")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "cwc3x24", "sweep256x256"],
+                    help="profiling only: run the compartment workload, or the uneven sweep in the tail "
+                         "layout, as the timed step")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -414,14 +417,22 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.device("cuda", torch.cuda.current_device())
     lib_build.build()
+    layout = args.layout
     if args.workload == "cwc3x24":
         batch = W.cwc3x24(R=args.replicas or 16384, G=args.grid_points or 500)
+    elif args.workload == "sweep256x256":
+        batch = W.sweep256x256(R=args.replicas or 256, G=args.grid_points or 1000)
+        layout = layout or capi.CWC_LAYOUT_TAIL
     else:
         batch = W.flat32x64(R=args.replicas or 65536, G=args.grid_points or 1000)
     if args.horizon_scale != 1.0:
         batch = W.Batch(batch.model, batch.rates, batch.init, batch.grid * args.horizon_scale, batch.R, batch.seed,
                         name=batch.name)
     R = batch.R
+    # kernels of this library per step: the SSA kernel; for the sweep in the
+    # tail layout also the queue order (estimate, rank) and the hand-over
+    # (collect, rank, lane-group kernel)
+    launches_per_step = 6 if args.workload == "sweep256x256" else 1
     r_off, _ = shard.weak_shard(R, rank)
     cm = api.CompiledModel(batch.model)
     rates, init, grid = api.device_inputs(batch, dev)
@@ -431,7 +442,7 @@ def main():
 
     def step(o):
         return api.simulate(cm, rates, init, grid, R, batch.seed, batch.max_events, states=True, traj=True,
-                            layout=args.layout, block_threads=args.threads, lanes=args.lanes, replica_offset=r_off,
+                            layout=layout, block_threads=args.threads, lanes=args.lanes, replica_offset=r_off,
                             term_bits=args.term_bits,
                             out=o)
 
@@ -470,7 +481,7 @@ def main():
     achieved = f_evt * events / kernel_s
     traffic = None
     issue = None
-    tj = capture_record("flat_ssa_kernel_flat32x64", WORKLOAD, KERNEL_SOURCES)
+    tj = capture_record("flat_ssa_kernel_flat32x64", args.workload, KERNEL_SOURCES)
     if tj is not None:
         traffic = tj.get("dram_bytes_per_launch")
         # issue-rate roofline of the same kernel (warp instructions issued per
@@ -541,13 +552,14 @@ def main():
                                                     or args.workload != WORKLOAD)
                        else "%s (profiling case: R=%d, G=%d, horizon x%g)" % (args.workload, R, batch.G,
                                                                                args.horizon_scale),
-                       "description": WORKLOAD_DESC if args.workload == WORKLOAD else CWC_DESC, "P": batch.P, "R": R,
+                       "description": {WORKLOAD: WORKLOAD_DESC, "cwc3x24": CWC_DESC}.get(args.workload, SWEEP_DESC),
+                           "P": batch.P, "R": R,
                            "G": batch.G, "S": batch.model.n_species, "M": batch.model.n_rules,
                            "events_per_step_per_gpu": events, "statuses": statuses,
-                           "layout": ["auto(queue)", "static", "queue"][args.layout],
+                           "layout": ["auto(queue)", "static", "queue", "tail"][layout],
                            "l2": "256 MiB buffer written between timed steps; outputs 8.4 GB per step",
                            "parallelism": "replica shards, %d GPU(s)" % world},
-                "gpu_launches": args.steps, "clocks": clk, "roofline": roofline,
+                "gpu_launches": args.steps * launches_per_step, "clocks": clk, "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": cpu, "extras": extras,
                 "step_ms": [round(x, 3) for x in step_ms]}
         print(json.dumps(line), flush=True)
