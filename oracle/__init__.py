@@ -44,9 +44,16 @@ def lib():
         return _lib if _lib is not None else _load()
 
 
+# A patched copy of the oracle, loaded instead of the built one when this
+# variable names it: tests/test_oracle_mutants.py plants one mistake per copy
+# (in the C source, on the CPU) to show that the pins catch it.  Unset
+# otherwise.
+LIBRARY_ENV = "CWC_ORACLE_LIBRARY"
+
+
 def _load():
     global _lib
-    path = _build.build()
+    path = os.environ.get(LIBRARY_ENV) or _build.build()
     L = ctypes.CDLL(path)
     vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
     L.oracle_philox4x32_10.argtypes = [vp, vp, vp]

@@ -1,11 +1,15 @@
 """Pins of the oracle's building blocks against mathematics and library routines.
 
-Philox4x32-10 (Salmon et al., SC'11) is pinned on the CPU by statistical
-tests; the GPU test-suite additionally checks it word for word against
-cuRAND's Philox4_32_10 (tests/test_gpu_philox.py).
+Philox4x32-10 (Salmon et al., SC'11) is pinned on the CPU by the algorithm's
+published known-answer vectors (tests/golden/philox4x32_10_kat.json) and by
+statistical tests; the GPU test-suite additionally checks it word for word
+against cuRAND's Philox4_32_10 (test_oracle_philox_matches_curand in
+tests/test_gpu_flat.py).
 """
 import decimal
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -19,6 +23,21 @@ EPS = 2.0 ** -52
 # ----------------------------------------------------------------------------
 # Philox4x32-10
 # ----------------------------------------------------------------------------
+
+def test_philox_known_answer_vectors():
+    """The published known-answer vectors: a wrong round multiplier, Weyl
+    increment, word order or key schedule changes every output word, which
+    the statistical tests below cannot see."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")
+    with open(path) as f:
+        kat = json.load(f)
+    assert len(kat["vectors"]) == 3
+    for v in kat["vectors"]:
+        ctr = np.array([[int(x, 16) for x in v["ctr"]]], np.uint32)
+        key = tuple(int(x, 16) for x in v["key"])
+        out = oracle.philox(ctr, key)
+        assert [int(x) for x in out[0]] == [int(x, 16) for x in v["out"]]
+
 
 def _stream(n, purpose=0, r=3, p=5, key=(0x01234567, 0x89ABCDEF)):
     ctr = np.zeros((n, 4), np.uint32)
