@@ -34,6 +34,7 @@ LAWS = "tests/test_oracle_laws.py::"
 GEN = "tests/test_oracle_general_patterns.py::"
 SENS = "tests/test_oracle_sensitivity.py::"
 RATE = "tests/test_oracle_rate_laws.py::"
+HASH = "tests/test_oracle_hash.py::"
 CTX_LAWS = [CTX + "test_dissolution_releases_the_content_of_a_child_chosen_with_probability_h",
             CTX + "test_local_rule_context_law_with_binomial_weights",
             CTX + "test_parent_child_context_law_over_children_of_different_parents"]
@@ -113,6 +114,19 @@ CASES = {
         "    if (x < SL || SR == 0.0) {",
         "    if (x < SL || SR != SR) {",
         [PRIM + "test_select_never_picks_zero"], []),
+    # the event hash compared by parity
+    "hash: the slot's bytes before the rule's": (
+        "  for (int i = 0; i < 4; i++) bytes[i] = (uint8_t)(rule >> (8 * i));\n"
+        "  for (int i = 0; i < 4; i++) bytes[4 + i] = (uint8_t)(slot >> (8 * i));",
+        "  for (int i = 0; i < 4; i++) bytes[4 + i] = (uint8_t)(rule >> (8 * i));\n"
+        "  for (int i = 0; i < 4; i++) bytes[i] = (uint8_t)(slot >> (8 * i));",
+        [HASH + "test_flat_hash_is_fnv1a_of_the_event_log",
+         HASH + "test_compartment_hash_is_fnv1a_of_the_event_log"], [HASH + "test_fnv1a64_published_values"]),
+    "hash: a wrong FNV prime": (
+        "    h *= 0x100000001b3ull;",
+        "    h *= 0x100000001b5ull;",
+        [HASH + "test_flat_hash_is_fnv1a_of_the_event_log",
+         HASH + "test_compartment_hash_is_fnv1a_of_the_event_log"], []),
     # the likelihood-ratio score
     "score: the integral of h dropped": (
         "for (int i = 0; i < M; i++) x.I[i] = x.I[i] + x.Hs[i] * (tnext - tnow);",
