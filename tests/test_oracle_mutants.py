@@ -114,6 +114,43 @@ CASES = {
         "    if (x < SL || SR == 0.0) {",
         "    if (x < SL || SR != SR) {",
         [PRIM + "test_select_never_picks_zero"], []),
+    # Update step, the rewrite of the matched multisets (Sec. 2.1)
+    "update: a dissolved compartment's children not re-parented": (
+        "if (t->alive[d] && d != c && t->parent[d] == c) t->parent[d] = q;",
+        "if (t->alive[d] && d != c && t->parent[d] == c) t->parent[d] = t->parent[d];",
+        [LAWS + "test_cwc_dissolve_reparents_children"], []),
+    "update: a dissolved compartment's wrap lost": (
+        "      xp[s] = xp[s] + rhs[s] - lhs[s] + (w[s] - lhs[S + s]) + (xc[s] - lhs[2 * S + s]);",
+        "      xp[s] = xp[s] + rhs[s] - lhs[s] + (xc[s] - lhs[2 * S + s]);",
+        [LAWS + "test_cwc_create_dissolve_token_law"], []),
+    "update: transport applied in the other direction": (
+        "      xp[s] = xp[s] + rhs[s] - lhs[s];\n      w[s] = w[s] + rhs[S + s] - lhs[S + s];\n"
+        "      xc[s] = xc[s] + rhs[2 * S + s] - lhs[2 * S + s];",
+        "      xp[s] = xp[s] + rhs[2 * S + s] - lhs[2 * S + s];\n      w[s] = w[s] + rhs[S + s] - lhs[S + s];\n"
+        "      xc[s] = xc[s] + rhs[s] - lhs[s];",
+        [LAWS + "test_cwc_transport_two_children_binomial"], []),
+    "update: a created compartment takes the context's label": (
+        "    t->label[e] = m->child_label[j];",
+        "    t->label[e] = m->ctx_label[j];",
+        [LAWS + "test_cwc_create_dissolve_token_law"], []),
+    "update: FUSION drops the second compartment's content": (
+        "      int32_t xm = x1[s] - lhs[2 * S + s] + x2[s] - lhs[4 * S + s] + rhs[2 * S + s];",
+        "      int32_t xm = x1[s] - lhs[2 * S + s] + rhs[2 * S + s];",
+        [GEN + "test_fusion_merges_wraps_and_contents_and_moves_children"], []),
+    "update: PAIR rewrites the first compartment twice": (
+        "    int32_t* ms[5] = {t->content + (size_t)q * S, t->wrap + (size_t)d1 * S, t->content + (size_t)d1 * S,\n"
+        "                      t->wrap + (size_t)d2 * S, t->content + (size_t)d2 * S};",
+        "    int32_t* ms[5] = {t->content + (size_t)q * S, t->wrap + (size_t)d1 * S, t->content + (size_t)d1 * S,\n"
+        "                      t->wrap + (size_t)d1 * S, t->content + (size_t)d1 * S};",
+        [GEN + "test_pair_rewrites_both_compartments_in_place"], []),
+    "update: NESTED rewrites the child's content for the grandparent's": (
+        "    int32_t* ms[5] = {t->content + (size_t)a * S, t->wrap + (size_t)q * S, t->content + (size_t)q * S,",
+        "    int32_t* ms[5] = {t->content + (size_t)q * S, t->wrap + (size_t)q * S, t->content + (size_t)q * S,",
+        [GEN + "test_nested_transport_from_grandchildren_is_binomial"], []),
+    "update: no int32 overflow check": (
+        "static int fits(int64_t v) { return v >= 0 && v <= 2147483647LL; }",
+        "static int fits(int64_t v) { return v >= 0; }",
+        [LAWS + "test_bad_input_and_overflow_statuses"], []),
     # the event hash compared by parity
     "hash: the slot's bytes before the rule's": (
         "  for (int i = 0; i < 4; i++) bytes[i] = (uint8_t)(rule >> (8 * i));\n"
