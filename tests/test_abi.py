@@ -6,6 +6,7 @@ import glob
 import os
 import re
 import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -136,6 +137,28 @@ def test_ctypes_structs_follow_the_header(name):
     for (nm, is_ptr, typ), (_, ctype) in zip(hdr, py):
         want = 8 if is_ptr else sizes[typ]
         assert ctypes.sizeof(ctype) == want, nm
+
+
+@pytest.mark.parametrize("name", ["cwc_sim_args", "cwc_sens_args", "cwc_model_desc"])
+def test_ctypes_struct_offsets_equal_the_compiled_header(name, tmp_path):
+    """Every field's offset and the struct's size, as a C compiler lays out
+    the header's declaration, equal the ctypes mirror's (padding included)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    fields = [f[0] for f in _header_struct_fields(name)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cwcgpu.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(' + name + '));']
+    lines += ['  printf("%zu\\n", offsetof(' + name + ', ' + f + '));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    exe = tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c11", "-I" + os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True,
+                   capture_output=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    py = getattr(capi, name)
+    assert got[0] == ctypes.sizeof(py)
+    assert got[1:] == [getattr(py, f).offset for f in fields]
 
 
 def test_michaelis_menten_validation_on_host(lib):
